@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the polynomial-diagram objective+gradient hot path.
+
+Workload: a 1024 x 1024 pixel grid on [-1,1]^2 labelled by a seeded
+degree-4 polynomial diagram with N = 500 grains (Legendre coefficients of
+degree >= 2 standard normal, degree <= 1 terms from uniform sites), 2%
+boundary label noise, fitted at degree 4 (K = 15) with eps = 1e-3.  One
+step is one objective + gradient evaluation (features, logits, log-sum-exp,
+objective and gradient reductions) at the generating parameters.
+
+Metric: pixel x grain objective+gradient evaluations per second
+(P * N_eff per step).  ``value`` is timed on the device with CUDA events
+with inputs resident in HBM and L2 flushed between steps (a 256 MiB write,
+not timed); ``e2e`` is the same metric through the public API with the
+step's inputs copied from pinned host memory and its outputs copied back
+inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+method has) on a bounded band of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_20816_gb300 import synth  # noqa: E402
+
+SHAPE = (1024, 1024)
+N_GRAINS = 500
+DEG = 4
+EPS = 1e-3
+NOISE = 0.02
+SEED = synth.SEED_BASE + 1
+WORKLOAD = ("2D 1024x1024, N=500 degree-4 polynomial diagram, 2% boundary noise, "
+            "fit degree 4 (K=15), eps=1e-3")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target duration of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sel = [r for r in rows if self.t0 and self.t1 and self.t0 - 0.2 <= r[0] <= self.t1 + 0.2] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in sel for q in range(4) if r[3][q].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
+                "reasons": reasons, "samples": len(sel)}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+def make_workload_gpu(pd, torch):
+    """Rasterise the generating diagram with the library's own assignment."""
+    y, z = synth.poly_params(SEED, N_GRAINS, 2, pd.pd_K(2, DEG))
+    th = pd.pd_theta_from_apd(2, DEG, y, np.zeros(N_GRAINS)).numpy()
+    th[:, 3:] = z[:, 3:]
+    grid = pd.Grid(SHAPE)
+    lab, _, _ = pd.pd_assign(grid, N_GRAINS, DEG, torch.from_numpy(th).cuda())
+    lab = synth.boundary_noise(lab.cpu().numpy(), SHAPE, NOISE, SEED + 7)
+    lab, n_eff, used = synth.compact(lab)
+    return grid, lab.astype(np.int32), n_eff, np.ascontiguousarray(th[used])
+
+
+def oracle_band(rows: int):
+    """A band of `rows` grid rows of the same workload, as an explicit point
+    list, labelled by the oracle (only the CPU legs call this)."""
+    import oracle as O
+    n1, n2 = SHAPE
+    r0 = (n2 - rows) // 2
+    xs = -1.0 + (2.0 * np.arange(n1) + 1.0) / n1
+    ys = -1.0 + (2.0 * np.arange(r0, r0 + rows) + 1.0) / n2
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    g = O.Grid(coords=np.stack([X.reshape(-1), Y.reshape(-1)], 1))
+    y, z = synth.poly_params(SEED, N_GRAINS, 2, O.K(2, DEG))
+    th = O.theta_from_apd(2, DEG, y, np.zeros(N_GRAINS))
+    th[:, 3:] = z[:, 3:]
+    lab, _ = O.assign(g, N_GRAINS, DEG, th)
+    lab = synth.boundary_noise(lab, (n1, rows), NOISE, SEED + 7)
+    lab, n_eff, used = synth.compact(lab)
+    return O, g, lab.astype(np.int32), n_eff, np.ascontiguousarray(th[used])
+
+
+def cpu_oracle_rate(target_s: float):
+    """Time the oracle's objective+gradient on a band sized for ~target_s."""
+    O, g, lab, n, th = oracle_band(8)
+    t = time.perf_counter()
+    O.objective_grad(g, lab, n, DEG, EPS, th)
+    per_px = (time.perf_counter() - t) / g.P
+    rows = int(max(8, min(SHAPE[1], target_s / (per_px * SHAPE[0]))))
+    O, g, lab, n, th = oracle_band(rows)
+    t = time.perf_counter()
+    O.objective_grad(g, lab, n, DEG, EPS, th)
+    dt = time.perf_counter() - t
+    return {"value": g.P * n / dt, "unit": "pixel*grain/s", "cores": 1, "kind": "oracle",
+            "sample": "objective+gradient of the FP64 C oracle (single thread) on a %d-row band "
+                      "(%d pixels x %d grains) of the same workload, %.1f s" % (rows, g.P, n, dt)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    per_step = max(0.5, min(3.0, 120.0 / (steps + warm)))
+    O, g, lab, n, th = oracle_band(8)
+    t = time.perf_counter()
+    O.objective_grad(g, lab, n, DEG, EPS, th)
+    per_px = (time.perf_counter() - t) / g.P
+    rows = int(max(2, min(SHAPE[1], per_step / (per_px * SHAPE[0]))))
+    O, g, lab, n, th = oracle_band(rows)
+    for _ in range(warm):
+        O.objective_grad(g, lab, n, DEG, EPS, th)
+    t = time.perf_counter()
+    for _ in range(steps):
+        O.objective_grad(g, lab, n, DEG, EPS, th)
+    dt = time.perf_counter() - t
+    value = g.P * n * steps / dt
+    line = {
+        "impl": "reference", "metric": "pixel*grain objective+gradient evaluations per second",
+        "value": value, "unit": "pixel*grain/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+        "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_rows": rows, "sample_pixels": g.P, "grains": n},
+        "cpu_baseline": {"value": value, "unit": "pixel*grain/s", "cores": 1, "kind": "oracle",
+                         "sample": "FP64 C oracle, single thread, %d-row band (%d pixels) of the workload "
+                                   "per step" % (rows, g.P)},
+        "e2e": {"value": value, "unit": "pixel*grain/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_20816_gb300 import pd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    prec = pd.PREC[args.prec]
+
+    grid, lab_np, N, th_np = make_workload_gpu(pd, torch)
+    P = grid.P
+    K = pd.pd_K(2, DEG)
+    lab = torch.from_numpy(lab_np).cuda()
+    th = torch.from_numpy(th_np).cuda()
+    obj = torch.empty((), dtype=torch.float64, device="cuda")
+    grad = torch.empty((N, K), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pd.pd_objective_grad(grid, lab, N, th, DEG, EPS, prec=prec, obj_out=obj, grad_out=grad)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark(True)
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)           # evict the previous step's data from L2 (not timed)
+        ev[s][0].record(stream)
+        step()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = sampler.stop() if not args.no_clocks else None
+    ms_step = ms / args.steps
+    value = world * P * N / (ms_step * 1e-3)
+
+    # traced pass: per-kernel device time of the same steps
+    pd.pd_prof_enable(True)
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    prof = pd.pd_prof_read()
+    pd.pd_prof_enable(False)
+    launches = sum(c for c, _ in prof.values()) // args.steps
+
+    # end to end through the public API from pinned host buffers
+    h_lab = torch.from_numpy(lab_np).pin_memory()
+    h_th = torch.from_numpy(th_np).pin_memory()
+    h_obj = torch.empty((), dtype=torch.float64).pin_memory()
+    h_grad = torch.empty((N, K), dtype=torch.float64).pin_memory()
+    d_lab = torch.empty_like(lab)
+    d_th = torch.empty_like(th)
+    e2e_steps = max(5, args.steps // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_lab.copy_(h_lab, non_blocking=True)
+        d_th.copy_(h_th, non_blocking=True)
+        o, g = pd.pd_objective_grad(grid, d_lab, N, d_th, DEG, EPS, prec=prec, obj_out=obj, grad_out=grad)
+        h_obj.copy_(o, non_blocking=True)
+        h_grad.copy_(g, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    assert math.isfinite(float(h_obj.item()))
+
+    if rank != 0:
+        return 0
+    pk = peaks()
+    # dominant kernel and its roofline: the CUDA-core path is bound by FP32
+    # FMA issue (2K flop per pixel-grain pair per contraction)
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (cnt, tot_ms) = top
+    avg_s = tot_ms / cnt * 1e-3
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if args.prec in ("fp32", "fp64"):
+        flop_per_pg = 2 * K
+        algo = P * N * flop_per_pg
+        if args.prec == "fp32":
+            peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        else:
+            peak = sms * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # 2 DFMA/clk/SM (GB300 FP64)
+        achieved = algo / avg_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "%d SMs x %s lanes x 2 flop x %.0f MHz (max SM clock, %s)" % (
+                    sms, "128 FP32" if args.prec == "fp32" else "2 FP64", pk.get("sm_max_mhz", 2070.0),
+                    pk["source"])}
+    else:
+        flop_per_pg = 4 * K
+        algo = P * N * flop_per_pg
+        peak = pk.get("bf16_tflops_sustained", 1683.3)
+        achieved = algo / avg_s / 1e12
+        roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None}
+    cpu = cpu_oracle_rate(args.cpu_seconds) if world == 1 or rank == 0 else None
+    line = {
+        "metric": "pixel*grain objective+gradient evaluations per second",
+        "value": value, "unit": "pixel*grain/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels": P, "grains": N, "K": K, "eps": EPS,
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "clocks": clocks,
+        "e2e": {"value": world * P * N / (e2e_ms * 1e-3), "unit": "pixel*grain/s",
+                "h2d_bytes_per_step": 4 * P + 8 * N * K, "d2h_bytes_per_step": 8 + 8 * N * K},
+        "gpu_launches": launches * args.steps,
+        "kernels_per_step": {k: {"launches": c // args.steps, "ms": t / args.steps} for k, (c, t) in prof.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,243 @@
+/*
+ * pd.h -- C ABI of libpd, a GB300 (sm_103a) implementation of the hot path
+ * of polynomial-diagram fitting from "Polynomial diagrams for microstructure
+ * modelling" (Bourne, Buze, Gallouet, Merigot).
+ *
+ * Notation follows the paper:
+ *   Omega      the pixel (or voxel) set, |Omega| = P points in [-1,1]^dim;
+ *   G          the grain map Omega -> {0..N-1} (0-based here; 1-based in
+ *              the paper), given as int32 labels[P];
+ *   eta(x)     the tensor-product Legendre design function of degree d
+ *              (Sec. 3.3), K = K_d entries;
+ *   theta      the parameters, theta[N][K] row-major (grain-major), double;
+ *   h_i(x)     = theta_i . eta(x); the diagram is F(x) = argmin_i h_i(x);
+ *   Phi        the objective Phi_eps^G of eq. (Phi), always <= 0, which the
+ *              fit maximises.
+ *
+ * Layout conventions
+ *   Pixels of a structured grid of extents n[0] x n[1] (x n[2]) have centres
+ *   x_a = -1 + (2 k_a + 1) / n[a] (Sec. 2.1 with n = 2M, each axis scaled to
+ *   [-1,1] on its own) and linear index j = k_0 + n[0] (k_1 + n[1] k_2).
+ *   The multi-indices alpha of A_d are ordered by ascending total degree,
+ *   then descending alpha_1, then descending alpha_2 (the paper fixes "an
+ *   ordering" without choosing one, Sec. 3.1).  Entries 0..dim of every
+ *   theta_i are therefore the constant and the linear terms.
+ *
+ * Ownership and execution
+ *   The caller owns every buffer.  Pointers documented "device" must be
+ *   device memory of the current CUDA device; "host" pointers host memory.
+ *   Entry points taking a stream enqueue their work on that stream
+ *   (a cudaStream_t passed as void*; NULL = the legacy default stream) and
+ *   return without synchronising, except where documented "synchronous".
+ *   Scratch memory is drawn from the device's stream-ordered memory pool on
+ *   the given stream and returned to it on the same stream before the call
+ *   returns, so calls on different streams never share scratch.
+ *
+ * Errors
+ *   Every entry point returns PD_OK (0) or a negative PD_E* code and never
+ *   aborts or exits.  Arguments are checked on the host before anything is
+ *   enqueued; an error return means nothing was enqueued.  Asynchronous
+ *   device errors surface at the caller's next synchronisation, as for any
+ *   CUDA call.
+ */
+#ifndef PD_H_
+#define PD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PD_OK 0
+#define PD_EINVAL (-1)   /* bad argument: N<2, eps<=0, bad dim/d, NULL, P   */
+#define PD_ELABEL (-2)   /* a label outside 0..N-1 (checked where stated)    */
+#define PD_ENAN (-3)     /* a non-finite objective or parameter was met      */
+#define PD_ENOMEM (-4)   /* scratch allocation failed                        */
+#define PD_ECUDA (-5)    /* a CUDA runtime call or kernel launch failed      */
+#define PD_ETIMEOUT (-6) /* a bounded device wait gave up                    */
+#define PD_ENOTSUP (-7)  /* valid but unsupported combination (e.g. degree)  */
+
+/* ---- precisions of an evaluation --------------------------------------- */
+#define PD_FP64 0  /* all arithmetic in double                              */
+#define PD_FP32 1  /* logits, exp and per-tile sums in float; log-sum-exp in
+                      float; cross-tile and final reductions in double       */
+#define PD_BF16 2  /* logits and gradient contraction on tcgen05 tensor cores
+                      with bf16 operands and fp32 accumulation; float
+                      log-sum-exp; double final reduction                    */
+#define PD_BF16X3 3 /* as PD_BF16 with every operand split into three bf16
+                      terms (hi+mid+lo), which recovers float-level accuracy
+                      on the tensor cores                                     */
+
+/* ---- supported sizes --------------------------------------------------- */
+#define PD_MAX_DEGREE_2D 7
+#define PD_MAX_DEGREE_3D 4
+
+/* Pixel set Omega (Sec. 2.1).  coords == NULL: structured grid n[0..dim-1]
+ * with P = n[0]*n[1](*n[2]).  coords != NULL: an explicit device point list
+ * [P][dim] of doubles in [-1,1]^dim (the paper's "any finite set of sample
+ * points"); n is then ignored. */
+typedef struct pd_grid {
+  int dim;              /* 2 or 3 */
+  int64_t n[3];
+  const double* coords; /* device, or NULL */
+  int64_t P;
+} pd_grid;
+
+/* Options of one evaluation. */
+typedef struct pd_eval_opts {
+  int d;       /* polynomial degree, 1..PD_MAX_DEGREE_{2D,3D}            */
+  double eps;  /* regularisation eps > 0 of eq. (p-e)                     */
+  int prec;    /* PD_FP64, PD_FP32, PD_BF16, PD_BF16X3                     */
+} pd_eval_opts;
+
+/* K_d = |A_d| for dimension dim (Sec. 3.1: (d+1)(d+2)/2 in 2-D; the 3-D
+ * tensor product gives (d+1)(d+2)(d+3)/6).  Returns -1 for bad arguments. */
+int pd_K(int dim, int d);
+
+/* Writes the exponents of A_d in library order to alpha_out (host,
+ * [K][dim] ints).  Returns K, or a negative code. */
+int pd_alpha(int dim, int d, int* alpha_out);
+
+/* Human-readable text of a status code (static storage). */
+const char* pd_strerror(int code);
+
+/* Design matrix eta(Omega) (Sec. 3.3, eq. h-degree-d-legendre): writes
+ * eta_out[j][k] = psi_{alpha_k}(x_j), pixel-major, as double (prec ==
+ * PD_FP64) or float (PD_FP32).  eta_out: device, P*K elements.  Used to
+ * check the in-register features of the other kernels; those never write
+ * eta to memory.  P == 0 is a no-op. */
+int pd_features(const pd_grid* grid, int d, int prec, void* eta_out,
+                void* stream);
+
+/* Objective and gradient, one fused evaluation (eqs. Phi and grad):
+ *   Phi       = (1/P) sum_x log p_{G(x)}(x),
+ *   grad_i    = -(1/(eps P)) sum_x (delta_{i G(x)} - p_i(x)) eta(x),
+ * with p_i(x) = exp(-h_i(x)/eps) / sum_j exp(-h_j(x)/eps) (eq. p-e).
+ * labels: device int32[P], each in 0..N-1 (not checked here; see
+ * pd_check_labels).  theta: device double[N][K].  obj_out: device double
+ * scalar.  grad_out: device double[N][K], or NULL to skip the gradient.
+ * Results are bitwise reproducible run to run (fixed-order reductions). */
+int pd_objective_grad(const pd_grid* grid, const int32_t* labels, int N,
+                      const double* theta, const pd_eval_opts* opts,
+                      double* obj_out, double* grad_out, void* stream);
+
+/* Hessian-vector product from eq. (hess):
+ *   (H v)_i = -(1/(eps^2 P)) sum_x p_i(x) (u_i(x) - sum_k p_k(x) u_k(x)) eta(x),
+ * u_i(x) = v_i . eta(x).  v, hv_out: device double[N][K].  labels are not
+ * used by the Hessian but keep the call shape of pd_objective_grad (may be
+ * NULL).  prec: PD_FP64 or PD_FP32. */
+int pd_hvp(const pd_grid* grid, const int32_t* labels, int N,
+           const double* theta, const double* v, const pd_eval_opts* opts,
+           double* hv_out, void* stream);
+
+/* Arg-min assignment F_theta (Sec. 2.1, eq. Li_def), computed in double:
+ * labels_out[j] = the smallest i attaining min_i theta_i . eta(x_j).
+ * gap_out (device double[P] or NULL): second-smallest minus smallest h.
+ * ref_labels (device int32[P] or NULL) with mismatch_out (device int64
+ * scalar): the number of pixels with labels_out != ref_labels, i.e.
+ * Err^G * P (Sec. 4); mismatch_out is overwritten, not accumulated.
+ * P == 0 writes mismatch 0 and returns. */
+int pd_assign(const pd_grid* grid, int N, int d, const double* theta,
+              int32_t* labels_out, double* gap_out, const int32_t* ref_labels,
+              int64_t* mismatch_out, void* stream);
+
+/* Grain moments for the initialisations of Sec. 5.5.2: counts_out[i] =
+ * |G_i| and mom_out[i][k] = sum_{x in G_i} psi_{alpha_k}(x) for the
+ * Legendre multi-indices of degree <= dm (1..4).  Accumulated exactly in
+ * 64-bit fixed point (resolution 2^-36 per term), so the result is
+ * independent of thread order.  mom_out: device double[N][K_dm];
+ * counts_out: device int64[N].  Labels must be in range. */
+int pd_moments(const pd_grid* grid, const int32_t* labels, int N, int dm,
+               double* mom_out, int64_t* counts_out, void* stream);
+
+/* Synchronous: returns PD_ELABEL if any label is outside 0..N-1, else PD_OK. */
+int pd_check_labels(const pd_grid* grid, const int32_t* labels, int N,
+                    void* stream);
+
+/* Host helper (Sec. 2.3): parameters of an (anisotropic) power diagram,
+ * cost |x - y_i|^2_{A_i} - w_i, as Legendre coefficients of degree d.
+ * y: host double[N][dim]; w: host double[N]; A: host double[N][dim][dim]
+ * symmetric, or NULL for a power diagram (A_i = Id; the quadratic term,
+ * common to all grains, is then dropped, so d = 1 suffices).
+ * theta_out: host double[N][K_d], higher-degree terms zero. */
+int pd_theta_from_apd(int dim, int d, int N, const double* y, const double* w,
+                      const double* A, double* theta_out);
+
+/* Synchronous: the moment heuristic of Sec. 5.5.2 (eqs. centroid-guess to
+ * w-guess) as Legendre coefficients of degree d: centroids y', central
+ * second moments B' (normalised by |G_i|), A' = B'^-1 (identity for d = 1,
+ * for empty grains and for singular B'), w' = sqrt(det A') |G_i| / (P pi)
+ * (3-D: / (P 4pi/3)).  theta_out: device double[N][K]. */
+int pd_heuristic_init(const pd_grid* grid, const int32_t* labels, int N,
+                      int d, double* theta_out, void* stream);
+
+/* ---- the ascent scheme (Sec. 5.2) --------------------------------------- */
+#define PD_INIT_GIVEN 0     /* start from theta_io as passed               */
+#define PD_INIT_ZERO 1      /* theta = 0, the fully ambiguous state         */
+#define PD_INIT_HEURISTIC 2 /* the moment heuristic (pd_heuristic_init)     */
+
+#define PD_METHOD_LBFGS 0     /* L-BFGS, strong-Wolfe line search           */
+#define PD_METHOD_NEWTON_CG 1 /* truncated Newton with pd_hvp products      */
+
+typedef struct pd_fit_opts {
+  int d;              /* degree                                            */
+  double eps;         /* regularisation                                    */
+  int init;           /* PD_INIT_*                                         */
+  int method;         /* PD_METHOD_*                                       */
+  int max_iter;       /* iteration budget of the first phase               */
+  int lbfgs_m;        /* L-BFGS memory (10)                                */
+  int max_cg;         /* Newton-CG inner iterations (50)                   */
+  int prec;           /* precision of the first phase (PD_FP64 ...)        */
+  int refine_iter;    /* FP64 iterations after the first phase (0: none)   */
+  double gtol;        /* stop a phase when ||grad Phi||_2 <= gtol          */
+  double target_phi;  /* stop when Phi >= target_phi (-inf: never)         */
+  double switch_rtol; /* leave the first phase when the relative Phi gain
+                         of an iteration is below this (0: never)          */
+} pd_fit_opts;
+
+typedef struct pd_fit_report {
+  double phi;         /* final Phi (evaluated in FP64)                     */
+  double gnorm;       /* final ||grad Phi||_2 over the free blocks         */
+  double err;         /* final Err^G (Sec. 4)                              */
+  int iters;          /* iterations of both phases                         */
+  int iters_phase1;   /* iterations of the first phase                     */
+  int64_t evals;      /* objective+gradient evaluations                    */
+  int64_t hvps;       /* Hessian-vector products                           */
+  int status;         /* 0 budget, 1 gtol, 2 line search stalled, 3 target */
+  double seconds;     /* wall time of the call                             */
+} pd_fit_report;
+
+/* Synchronous: maximise Phi over theta with the gauge theta_{N-1} = 0
+ * (Remark 4.3) by the selected method; an optional FP64 refinement phase
+ * follows a reduced-precision phase.  theta_io: device double[N][K] (read
+ * when init == PD_INIT_GIVEN; always written, gauge-fixed).  report: host.
+ * Labels are checked (PD_ELABEL).  Returns PD_OK, or an error code (the
+ * report then holds the state reached). */
+int pd_fit(const pd_grid* grid, const int32_t* labels, int N,
+           const pd_fit_opts* opts, double* theta_io, pd_fit_report* report,
+           void* stream);
+
+/* ---- tracing of the library's own kernels ------------------------------ */
+/* pd_prof_enable(1) clears the record and starts timing every kernel this
+ * library launches, with a pair of CUDA events recorded on the launching
+ * stream around the launch; pd_prof_enable(0) stops recording (the record
+ * is kept).  pd_prof_read synchronises the recorded events and fills, for
+ * up to cap distinct kernels, their names (static strings), launch counts
+ * and total device milliseconds (host arrays); it returns the number of
+ * distinct kernels recorded, or a negative code.  Timing adds two event
+ * records per launch and is meant for profiling runs, not production. */
+int pd_prof_enable(int on);
+int pd_prof_read(int cap, const char** names, int64_t* launches, double* total_ms);
+
+/* Release cached library state on the current device (memory pool
+ * reservations are trimmed).  Safe to call at any time when no call of
+ * this library is in flight. */
+void pd_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_H_ */

@@ -1,0 +1,442 @@
+// pd_fit.cu -- the ascent scheme (Sec. 5.2): maximise Phi over the
+// gauge-fixed parameters (theta_{N-1} = 0, Remark 4.3) by L-BFGS with a
+// strong-Wolfe line search, or by truncated Newton with Hessian-vector
+// products (eq. hess).  The host runs the optimiser in double; every
+// objective/gradient or Hessian-vector evaluation is one device evaluation
+// of this library.
+//
+// Constants (the paper fixes none of them): L-BFGS memory m (10); strong
+// Wolfe c1 = 1e-4, c2 = 0.9, at most 25 evaluations per line search;
+// bracketing doubles the step; zooming uses a cubic interpolant kept at
+// least 10% of the bracket away from its ends, else bisection; the first
+// iteration tries the step 1/||g||_2, later ones the unit step; the initial
+// inverse Hessian is gamma I with gamma = s.y / y.y of the newest pair; a
+// pair is stored only if s.y > 1e-300; a non-descent direction restarts the
+// memory.  Newton-CG: conjugate gradients on (-H) s = grad Phi to relative
+// residual min(0.5, sqrt(||g||)), at most max_cg steps, stopping at
+// non-positive curvature (steepest ascent when that happens at once).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "pd.h"
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+using Vec = std::vector<double>;
+
+double dot(const Vec& a, const Vec& b) {
+  double s = 0.0;
+  for (size_t q = 0; q < a.size(); ++q) s += a[q] * b[q];
+  return s;
+}
+
+class Problem {
+ public:
+  Problem(const pd_grid* grid, const Geom& g, const int32_t* labels, int N, int d, double eps,
+          cudaStream_t st)
+      : grid_(grid), g_(g), labels_(labels), N_(N), d_(d), K_(basis_K(grid->dim, d)), eps_(eps), st_(st),
+        sc_(st) {
+    d_theta_ = sc_.get<double>((size_t)N * K_);
+    d_grad_ = sc_.get<double>((size_t)N * K_);
+    d_v_ = sc_.get<double>((size_t)N * K_);
+    d_obj_ = sc_.get<double>(1);
+    d_mis_ = sc_.get<int64_t>(1);
+    d_lab_ = sc_.get<int32_t>((size_t)(g.P > 0 ? g.P : 1));
+    h_theta_.assign((size_t)N * K_, 0.0);
+    h_grad_.assign((size_t)N * K_, 0.0);
+  }
+  bool ok() const { return sc_.ok(); }
+  int n_free() const { return (N_ - 1) * K_; }
+  int K() const { return K_; }
+  int64_t evals = 0, hvps = 0;
+
+  // f = -Phi, gf = -grad Phi on the free blocks
+  int eval(const Vec& x, int prec, double* f, Vec* gf) {
+    int rc = upload(x, d_theta_);
+    if (rc) return rc;
+    EvalCall c{g_, grid_->dim, d_, N_, prec, eps_, labels_, d_theta_, nullptr, d_obj_, gf ? d_grad_ : nullptr,
+               nullptr};
+    rc = (prec == PD_BF16 || prec == PD_BF16X3) ? eval_tc(c, st_) : eval_simt(c, st_);
+    if (rc) return rc;
+    double phi = 0.0;
+    if (cudaMemcpyAsync(&phi, d_obj_, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess) return PD_ECUDA;
+    if (gf && cudaMemcpyAsync(h_grad_.data(), d_grad_, sizeof(double) * h_grad_.size(), cudaMemcpyDeviceToHost,
+                              st_) != cudaSuccess)
+      return PD_ECUDA;
+    if (cudaStreamSynchronize(st_) != cudaSuccess) return PD_ECUDA;
+    ++evals;
+    *f = -phi;
+    if (gf) {
+      gf->resize(n_free());
+      for (int q = 0; q < n_free(); ++q) (*gf)[q] = -h_grad_[q];
+    }
+    return PD_OK;
+  }
+
+  // out = (Hessian of -Phi) v on the free blocks
+  int hvp(const Vec& x, const Vec& v, int prec, Vec* out) {
+    int rc = upload(x, d_theta_);
+    if (rc) return rc;
+    rc = upload(v, d_v_);
+    if (rc) return rc;
+    EvalCall c{g_, grid_->dim, d_, N_, prec == PD_FP64 ? PD_FP64 : PD_FP32, eps_, labels_, d_theta_, d_v_,
+               nullptr, nullptr, d_grad_};
+    rc = eval_simt(c, st_);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(h_grad_.data(), d_grad_, sizeof(double) * h_grad_.size(), cudaMemcpyDeviceToHost, st_) !=
+        cudaSuccess)
+      return PD_ECUDA;
+    if (cudaStreamSynchronize(st_) != cudaSuccess) return PD_ECUDA;
+    ++hvps;
+    out->resize(n_free());
+    for (int q = 0; q < n_free(); ++q) (*out)[q] = -h_grad_[q];
+    return PD_OK;
+  }
+
+  int mismatch(const Vec& x, int64_t* miss) {
+    int rc = upload(x, d_theta_);
+    if (rc) return rc;
+    rc = assign_simt(g_, grid_->dim, d_, N_, d_theta_, d_lab_, nullptr, labels_, d_mis_, st_);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(miss, d_mis_, sizeof(int64_t), cudaMemcpyDeviceToHost, st_) != cudaSuccess) return PD_ECUDA;
+    return cudaStreamSynchronize(st_) == cudaSuccess ? PD_OK : PD_ECUDA;
+  }
+
+  int write_theta(const Vec& x, double* dst) {
+    int rc = upload(x, d_theta_);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(dst, d_theta_, sizeof(double) * h_theta_.size(), cudaMemcpyDeviceToDevice, st_) !=
+        cudaSuccess)
+      return PD_ECUDA;
+    return cudaStreamSynchronize(st_) == cudaSuccess ? PD_OK : PD_ECUDA;
+  }
+
+ private:
+  // free blocks x -> full [N][K] with the last block zero
+  int upload(const Vec& x, double* dst) {
+    for (int q = 0; q < n_free(); ++q) h_theta_[q] = x[q];
+    for (int k = 0; k < K_; ++k) h_theta_[(size_t)(N_ - 1) * K_ + k] = 0.0;
+    if (cudaMemcpyAsync(dst, h_theta_.data(), sizeof(double) * h_theta_.size(), cudaMemcpyHostToDevice, st_) !=
+        cudaSuccess)
+      return PD_ECUDA;
+    // the host staging buffer is reused by the next upload
+    return cudaStreamSynchronize(st_) == cudaSuccess ? PD_OK : PD_ECUDA;
+  }
+
+  const pd_grid* grid_;
+  Geom g_;
+  const int32_t* labels_;
+  int N_, d_, K_;
+  double eps_;
+  cudaStream_t st_;
+  Scratch sc_;
+  double *d_theta_, *d_grad_, *d_v_, *d_obj_;
+  int64_t* d_mis_;
+  int32_t* d_lab_;
+  Vec h_theta_, h_grad_;
+};
+
+// Safeguarded cubic step between (a, fa, ga) and (b, fb, gb).
+double cubic_step(double a, double fa, double ga, double b, double fb, double gb) {
+  const double lo = fmin(a, b), hi = fmax(a, b);
+  const double t1 = ga + gb - 3.0 * (fa - fb) / (a - b);
+  const double rad = t1 * t1 - ga * gb;
+  if (rad >= 0.0) {
+    double t2 = sqrt(rad);
+    if (b < a) t2 = -t2;
+    const double z = b - (b - a) * ((gb + t2 - t1) / (gb - ga + 2.0 * t2));
+    if (isfinite(z) && z >= lo && z <= hi) return z;
+  }
+  return 0.5 * (a + b);
+}
+
+struct Point {
+  Vec x, g;
+  double f;
+};
+
+// Strong-Wolfe search along dir from cur; returns the step (0 on failure,
+// with *out = cur re-evaluated).
+int wolfe(Problem& pb, int prec, const Point& cur, const Vec& dir, double a0, Point* out, double* step) {
+  const double c1 = 1e-4, c2 = 0.9;
+  const int budget = 25;
+  const int n = (int)cur.x.size();
+  const double d0 = dot(cur.g, dir);
+  int used = 0;
+  auto try_at = [&](double a, Point* p) {
+    p->x.resize(n);
+    for (int q = 0; q < n; ++q) p->x[q] = cur.x[q] + a * dir[q];
+    ++used;
+    return pb.eval(p->x, prec, &p->f, &p->g);
+  };
+  double ap = 0.0, fp = cur.f, dp = d0;
+  double a = a0;
+  double lo = 0, flo = 0, glo = 0, hi = 0, fhi = 0, ghi = 0;
+  bool have_bracket = false;
+  Point p;
+  while (used < budget) {
+    int rc = try_at(a, &p);
+    if (rc) return rc;
+    const double da = dot(p.g, dir);
+    if (!isfinite(p.f) || p.f > cur.f + c1 * a * d0 || (used > 1 && p.f >= fp)) {
+      lo = ap; flo = fp; glo = dp;
+      hi = a; fhi = p.f; ghi = da;
+      have_bracket = true;
+      break;
+    }
+    if (fabs(da) <= -c2 * d0) {
+      *out = p;
+      *step = a;
+      return PD_OK;
+    }
+    if (da >= 0.0) {
+      lo = a; flo = p.f; glo = da;
+      hi = ap; fhi = fp; ghi = dp;
+      have_bracket = true;
+      break;
+    }
+    ap = a; fp = p.f; dp = da;
+    a *= 2.0;
+  }
+  if (have_bracket) {
+    const double xnorm = sqrt(dot(cur.x, cur.x)), dnorm = sqrt(dot(dir, dir));
+    while (used < budget) {
+      const double w = fabs(hi - lo);
+      double t = isfinite(fhi) ? cubic_step(lo, flo, glo, hi, fhi, ghi) : 0.5 * (lo + hi);
+      if (t < fmin(lo, hi) + 0.1 * w || t > fmax(lo, hi) - 0.1 * w) t = 0.5 * (lo + hi);
+      int rc = try_at(t, &p);
+      if (rc) return rc;
+      const double dt = dot(p.g, dir);
+      if (!isfinite(p.f) || p.f > cur.f + c1 * t * d0 || p.f >= flo) {
+        hi = t; fhi = p.f; ghi = dt;
+      } else {
+        if (fabs(dt) <= -c2 * d0) {
+          *out = p;
+          *step = t;
+          return PD_OK;
+        }
+        if (dt * (hi - lo) >= 0.0) { hi = lo; fhi = flo; ghi = glo; }
+        lo = t; flo = p.f; glo = dt;
+      }
+      if (fabs(hi - lo) * dnorm < 1e-16 * (1.0 + xnorm)) break;
+    }
+    if (lo > 0.0) {
+      int rc = try_at(lo, &p);
+      if (rc) return rc;
+      *out = p;
+      *step = lo;
+      return PD_OK;
+    }
+  }
+  // failure: stay at the current point (re-evaluated, as a search would)
+  Point back;
+  back.x = cur.x;
+  int rc = pb.eval(back.x, prec, &back.f, &back.g);
+  if (rc) return rc;
+  *out = back;
+  *step = 0.0;
+  return PD_OK;
+}
+
+struct PhaseResult {
+  int iters = 0;
+  int status = 0;  // 0 budget, 1 gtol, 2 stalled, 3 target, 4 switch
+};
+
+int lbfgs_phase(Problem& pb, int prec, Point& cur, int max_iter, int m, double gtol, double target_phi,
+                double switch_rtol, bool first_scaled, PhaseResult* res) {
+  const int n = (int)cur.x.size();
+  std::vector<Vec> S, Y;
+  std::vector<double> rho;
+  Vec dir(n), alpha(m);
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    const double gn = sqrt(dot(cur.g, cur.g));
+    if (gn <= gtol) { res->status = 1; break; }
+    if (-cur.f >= target_phi) { res->status = 3; break; }
+    for (int q = 0; q < n; ++q) dir[q] = -cur.g[q];
+    const int h = (int)S.size();  // newest pair last
+    for (int j = h - 1; j >= 0; --j) {
+      alpha[j] = rho[j] * dot(S[j], dir);
+      for (int q = 0; q < n; ++q) dir[q] -= alpha[j] * Y[j][q];
+    }
+    if (h > 0) {
+      const double gamma = dot(S[h - 1], Y[h - 1]) / dot(Y[h - 1], Y[h - 1]);
+      for (int q = 0; q < n; ++q) dir[q] *= gamma;
+    }
+    for (int j = 0; j < h; ++j) {
+      const double beta = rho[j] * dot(Y[j], dir);
+      for (int q = 0; q < n; ++q) dir[q] += (alpha[j] - beta) * S[j][q];
+    }
+    if (dot(dir, cur.g) >= 0.0) {
+      S.clear(); Y.clear(); rho.clear();
+      for (int q = 0; q < n; ++q) dir[q] = -cur.g[q];
+    }
+    const double a0 = (it == 0 && first_scaled) ? 1.0 / gn : 1.0;
+    Point nxt;
+    double step = 0.0;
+    int rc = wolfe(pb, prec, cur, dir, a0, &nxt, &step);
+    if (rc) return rc;
+    if (step == 0.0) { res->status = 2; break; }
+    Vec s(n), y(n);
+    for (int q = 0; q < n; ++q) { s[q] = nxt.x[q] - cur.x[q]; y[q] = nxt.g[q] - cur.g[q]; }
+    const double sy = dot(s, y);
+    if (sy > 1e-300) {
+      if ((int)S.size() == m) { S.erase(S.begin()); Y.erase(Y.begin()); rho.erase(rho.begin()); }
+      S.push_back(std::move(s)); Y.push_back(std::move(y)); rho.push_back(1.0 / sy);
+    }
+    const double gain = cur.f - nxt.f;
+    cur = std::move(nxt);
+    if (switch_rtol > 0.0 && gain <= switch_rtol * fabs(cur.f)) { ++it; res->status = 4; break; }
+  }
+  res->iters = it;
+  return PD_OK;
+}
+
+int newton_phase(Problem& pb, int prec, Point& cur, int max_iter, int max_cg, double gtol, double target_phi,
+                 PhaseResult* res) {
+  const int n = (int)cur.x.size();
+  Vec s(n), r(n), p(n), hp;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    const double gn = sqrt(dot(cur.g, cur.g));
+    if (gn <= gtol) { res->status = 1; break; }
+    if (-cur.f >= target_phi) { res->status = 3; break; }
+    const double tol = (gn < 0.25 ? sqrt(gn) : 0.5) * gn;
+    for (int q = 0; q < n; ++q) { s[q] = 0.0; r[q] = -cur.g[q]; p[q] = r[q]; }
+    double rr = dot(r, r);
+    for (int j = 0; j < max_cg; ++j) {
+      int rc = pb.hvp(cur.x, p, prec, &hp);
+      if (rc) return rc;
+      const double curv = dot(p, hp);
+      if (curv <= 0.0) {
+        if (j == 0)
+          for (int q = 0; q < n; ++q) s[q] = -cur.g[q];
+        break;
+      }
+      const double a = rr / curv;
+      for (int q = 0; q < n; ++q) { s[q] += a * p[q]; r[q] -= a * hp[q]; }
+      const double rr2 = dot(r, r);
+      if (sqrt(rr2) <= tol) break;
+      const double b = rr2 / rr;
+      for (int q = 0; q < n; ++q) p[q] = r[q] + b * p[q];
+      rr = rr2;
+    }
+    if (dot(s, cur.g) >= 0.0)
+      for (int q = 0; q < n; ++q) s[q] = -cur.g[q];
+    Point nxt;
+    double step = 0.0;
+    int rc = wolfe(pb, prec, cur, s, 1.0, &nxt, &step);
+    if (rc) return rc;
+    if (step == 0.0) { res->status = 2; break; }
+    cur = std::move(nxt);
+  }
+  res->iters = it;
+  return PD_OK;
+}
+
+}  // namespace
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const pd_fit_opts* opts, double* theta_io,
+                      pd_fit_report* report, void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  Geom g;
+  int rc = validate_grid(grid, &g);
+  if (rc) return rc;
+  if (!opts || !labels || !theta_io || !report || N < 2 || g.P < 1) return PD_EINVAL;
+  if (!(opts->eps > 0.0) || !isfinite(opts->eps) || opts->d < 1 || opts->max_iter < 0 || opts->refine_iter < 0)
+    return PD_EINVAL;
+  if (opts->prec < PD_FP64 || opts->prec > PD_BF16X3) return PD_EINVAL;
+  if (opts->method != PD_METHOD_LBFGS && opts->method != PD_METHOD_NEWTON_CG) return PD_EINVAL;
+  if (opts->method == PD_METHOD_LBFGS && opts->lbfgs_m < 1) return PD_EINVAL;
+  if (pd_K(grid->dim, opts->d) < 0) return PD_EINVAL;
+  if ((grid->dim == 2 && opts->d > PD_MAX_DEGREE_2D) || (grid->dim == 3 && opts->d > PD_MAX_DEGREE_3D))
+    return PD_ENOTSUP;
+  memset(report, 0, sizeof(*report));
+  cudaStream_t st = (cudaStream_t)stream;
+  device_sm_count();
+  rc = pd_check_labels(grid, labels, N, stream);
+  if (rc) return rc;
+
+  Problem pb(grid, g, labels, N, opts->d, opts->eps, st);
+  if (!pb.ok()) return PD_ENOMEM;
+  const int K = pb.K();
+  const int n = pb.n_free();
+
+  // initial parameters, gauge-fixed by subtracting the last block
+  std::vector<double> th((size_t)N * K, 0.0);
+  if (opts->init == PD_INIT_HEURISTIC) {
+    rc = pd_heuristic_init(grid, labels, N, opts->d, theta_io, stream);
+    if (rc) return rc;
+  } else if (opts->init != PD_INIT_GIVEN && opts->init != PD_INIT_ZERO) {
+    return PD_EINVAL;
+  }
+  if (opts->init != PD_INIT_ZERO) {
+    if (cudaMemcpyAsync(th.data(), theta_io, sizeof(double) * th.size(), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return PD_ECUDA;
+  }
+  Point cur;
+  cur.x.resize(n);
+  for (int i = 0; i < N - 1; ++i)
+    for (int k = 0; k < K; ++k) cur.x[(size_t)i * K + k] = th[(size_t)i * K + k] - th[(size_t)(N - 1) * K + k];
+  for (double v : cur.x)
+    if (!isfinite(v)) return PD_ENAN;
+
+  const double target = isnan(opts->target_phi) ? -INFINITY : opts->target_phi;
+  int prec = opts->prec;
+  rc = pb.eval(cur.x, prec, &cur.f, &cur.g);
+  if (rc) return rc;
+  PhaseResult r1, r2;
+  if (opts->method == PD_METHOD_LBFGS)
+    rc = lbfgs_phase(pb, prec, cur, opts->max_iter, opts->lbfgs_m, opts->gtol, target, opts->switch_rtol, true, &r1);
+  else
+    rc = newton_phase(pb, prec, cur, opts->max_iter, opts->max_cg, opts->gtol, target, &r1);
+  if (rc) return rc;
+  int status = r1.status;
+  if (opts->refine_iter > 0 && status != 3) {
+    if (prec != PD_FP64) {
+      prec = PD_FP64;
+      rc = pb.eval(cur.x, prec, &cur.f, &cur.g);
+      if (rc) return rc;
+    }
+    if (opts->method == PD_METHOD_LBFGS)
+      rc = lbfgs_phase(pb, prec, cur, opts->refine_iter, opts->lbfgs_m, opts->gtol, target, 0.0, false, &r2);
+    else
+      rc = newton_phase(pb, prec, cur, opts->refine_iter, opts->max_cg, opts->gtol, target, &r2);
+    if (rc) return rc;
+    status = r2.status;
+  }
+  // final report in double precision
+  double f_final = cur.f;
+  std::vector<double> gfin = cur.g;
+  if (prec != PD_FP64) {
+    rc = pb.eval(cur.x, PD_FP64, &f_final, &gfin);
+    if (rc) return rc;
+  }
+  int64_t miss = 0;
+  rc = pb.mismatch(cur.x, &miss);
+  if (rc) return rc;
+  rc = pb.write_theta(cur.x, theta_io);
+  if (rc) return rc;
+  report->phi = -f_final;
+  report->gnorm = sqrt(dot(gfin, gfin));
+  report->err = (double)miss / (double)g.P;
+  report->iters = r1.iters + r2.iters;
+  report->iters_phase1 = r1.iters;
+  report->evals = pb.evals;
+  report->hvps = pb.hvps;
+  report->status = status == 4 ? 0 : status;
+  report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return isfinite(report->phi) ? PD_OK : PD_ENAN;
+}

@@ -1,0 +1,489 @@
+// pd_simt_kernels.cuh -- CUDA-core (FFMA / DFMA) kernels of libpd:
+//   objective + gradient (eqs. Phi, grad), Hessian-vector products
+//   (eq. hess), arg-min assignment (eq. Li_def), features, grain moments.
+//
+// Evaluation structure (two passes over the pixels, nothing of size P x N is
+// ever stored):
+//   pass 1, one thread per pixel: features eta(x) in registers, logits of
+//           every grain against parameter tiles staged in shared memory,
+//           online log-sum-exp; writes log S(x) (4 or 8 bytes per pixel)
+//           and a per-block partial of sum_x log p_{G(x)}(x).
+//   pass 2, one thread per grain: pixel tiles (features, log S, label)
+//           staged in shared memory, the thread recomputes its logit, forms
+//           p_i(x) and accumulates (delta_{iG(x)} - p_i(x)) eta(x); per-tile
+//           sums are carried in double per pixel chunk.
+//   reduce: fixed-order double sum over chunks (bitwise reproducible).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "pd_common.cuh"
+#include "pd_internal.h"
+
+namespace pd {
+// Everything here has internal linkage: each translation unit that includes
+// this header gets its own copies of the kernels it instantiates.
+namespace {
+
+constexpr int kLseThreads = 256;
+constexpr int kGradThreads = 128;  // grains per block in pass 2
+constexpr int kPixTile = 128;      // pixels per shared-memory tile in pass 2
+constexpr int kChunk = 8;          // grains per online-LSE rescale
+
+template <int K, typename T>
+__device__ __forceinline__ T dot_k(const T* __restrict__ a, const T* __restrict__ b) {
+  T acc = a[0] * b[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) acc = fma(a[k], b[k], acc);
+  return acc;
+}
+
+static __device__ __forceinline__ double block_sum_fixed(double v, double* sbuf) {
+  // fixed-order block reduction: warp tree, then warp sums in order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sbuf[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sbuf[w];
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// theta -> scaled working copy thS[i][k] = theta[i][k] * scale, padded rows.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_scale_theta(const double* __restrict__ theta, int N, int K, int KP,
+                              double scale, T* __restrict__ out) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)N * KP) return;
+  int i = (int)(q / KP), k = (int)(q % KP);
+  out[q] = k < K ? (T)(theta[(int64_t)i * K + k] * scale) : (T)0;
+}
+
+template <typename T>
+__global__ void k_copy_pad(const double* __restrict__ v, int N, int K, int KP, T* __restrict__ out) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)N * KP) return;
+  int i = (int)(q / KP), k = (int)(q % KP);
+  out[q] = k < K ? (T)v[(int64_t)i * K + k] : (T)0;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: per-pixel log-sum-exp (and, for HVP, ubar(x) = sum_k p_k u_k).
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int D, int PPT, bool HVP>
+__global__ void __launch_bounds__(kLseThreads)
+k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__ thS,
+        const T* __restrict__ vS, T* __restrict__ lse_out, T* __restrict__ ubar_out,
+        double* __restrict__ obj_part) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<T>(K);
+  constexpr int GT = HVP ? 64 : 128;  // grains per shared tile
+  __shared__ __align__(16) T sth[GT * KP];
+  __shared__ __align__(16) T sv[HVP ? GT * KP : 1];
+  __shared__ double sred[kLseThreads / 32];
+
+  const int64_t base = (int64_t)blockIdx.x * (kLseThreads * PPT);
+  T eta[PPT][K];
+  T m[PPT], s[PPT], t[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int64_t j = base + q * kLseThreads + threadIdx.x;
+    T x[DIM];
+    if (j < g.P) {
+      pixel_coords<DIM>(g, j, x);
+    } else {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) x[a] = (T)0;
+    }
+    legendre_features<DIM, D>(x, eta[q]);
+    m[q] = -INFINITY;
+    s[q] = (T)0;
+    t[q] = (T)0;
+  }
+
+  for (int g0 = 0; g0 < N; g0 += GT) {
+    const int gn = min(GT, N - g0);
+    __syncthreads();
+    {
+      // rows g0..g0+gn-1 are contiguous: gn*KP elements, 16-byte vectors
+      constexpr int VE = 16 / sizeof(T);
+      const int nv = gn * KP / VE;
+      const uint4* src = reinterpret_cast<const uint4*>(thS + (int64_t)g0 * KP);
+      uint4* dst = reinterpret_cast<uint4*>(sth);
+      for (int e = threadIdx.x; e < nv; e += kLseThreads) dst[e] = src[e];
+      if (HVP) {
+        const uint4* srcv = reinterpret_cast<const uint4*>(vS + (int64_t)g0 * KP);
+        uint4* dstv = reinterpret_cast<uint4*>(sv);
+        for (int e = threadIdx.x; e < nv; e += kLseThreads) dstv[e] = srcv[e];
+      }
+    }
+    __syncthreads();
+    int i = 0;
+    for (; i + kChunk <= gn; i += kChunk) {
+      T l[PPT][kChunk];
+      T u[PPT][HVP ? kChunk : 1];
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          l[q][c] = dot_k<K>(sth + (i + c) * KP, eta[q]);
+          if (HVP) u[q][c] = dot_k<K>(sv + (i + c) * KP, eta[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        T cm = l[q][0];
+#pragma unroll
+        for (int c = 1; c < kChunk; ++c) cm = fmax(cm, l[q][c]);
+        const T mn = fmax(m[q], cm);
+        const T r = Arith<T>::ex(m[q] - mn);
+        T add = (T)0, addu = (T)0;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+          const T e = Arith<T>::ex(l[q][c] - mn);
+          add += e;
+          if (HVP) addu = fma(e, u[q][c], addu);
+        }
+        s[q] = fma(s[q], r, add);
+        if (HVP) t[q] = fma(t[q], r, addu);
+        m[q] = mn;
+      }
+    }
+    for (; i < gn; ++i) {
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const T l = dot_k<K>(sth + i * KP, eta[q]);
+        const T mn = fmax(m[q], l);
+        const T r = Arith<T>::ex(m[q] - mn);
+        const T e = Arith<T>::ex(l - mn);
+        s[q] = fma(s[q], r, e);
+        if (HVP) {
+          const T u = dot_k<K>(sv + i * KP, eta[q]);
+          t[q] = fma(t[q], r, e * u);
+        }
+        m[q] = mn;
+      }
+    }
+  }
+
+  double racc = 0.0;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int64_t j = base + q * kLseThreads + threadIdx.x;
+    if (j >= g.P) continue;
+    const T lse = m[q] + Arith<T>::lg(s[q]);
+    if (lse_out) lse_out[j] = lse;
+    if (HVP) ubar_out[j] = t[q] / s[q];
+    if (!HVP && obj_part) {
+      const int G = labels[j];
+      if ((unsigned)G < (unsigned)N) {
+        const T lG = dot_k<K>(thS + (int64_t)G * KP, eta[q]);
+        racc += (double)(lG - lse) * Arith<T>::to_nat;
+      } else {
+        racc = NAN;  // a label outside 0..N-1 poisons the objective
+      }
+    }
+  }
+  if (!HVP && obj_part) {
+    const double bs = block_sum_fixed(racc, sred);
+    if (threadIdx.x == 0) obj_part[blockIdx.x] = bs;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: one thread per grain over pixel tiles.
+//   GRAD: c = delta_{iG(x)} - p_i(x)
+//   HVP : c = p_i(x) (u_i(x) - ubar(x))
+// accumulates c * eta(x) per chunk of pixels into part[chunk][i][k].
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int D, bool HVP>
+__global__ void __launch_bounds__(kGradThreads)
+k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__ thS,
+        const T* __restrict__ vS, const T* __restrict__ lse, const T* __restrict__ ubar,
+        int64_t ppc, double* __restrict__ part) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<T>(K);
+  __shared__ __align__(16) T seta[kPixTile * KP];
+  __shared__ T slse[kPixTile];
+  __shared__ T subar[HVP ? kPixTile : 1];
+  __shared__ int slab[kPixTile];
+
+  const int i = blockIdx.y * kGradThreads + threadIdx.x;
+  const bool vi = i < N;
+  T th[K], vv[HVP ? K : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    th[k] = vi ? thS[(int64_t)i * KP + k] : (T)0;
+    if (HVP) vv[k] = vi ? vS[(int64_t)i * KP + k] : (T)0;
+  }
+  double acc64[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc64[k] = 0.0;
+
+  const int64_t p0 = (int64_t)blockIdx.x * ppc;
+  const int64_t p1 = min(p0 + ppc, g.P);
+  for (int64_t t0 = p0; t0 < p1; t0 += kPixTile) {
+    const int tn = (int)min((int64_t)kPixTile, p1 - t0);
+    __syncthreads();
+    if (threadIdx.x < tn) {
+      const int64_t j = t0 + threadIdx.x;
+      T x[DIM], e[K];
+      pixel_coords<DIM>(g, j, x);
+      legendre_features<DIM, D>(x, e);
+#pragma unroll
+      for (int k = 0; k < K; ++k) seta[threadIdx.x * KP + k] = e[k];
+      slse[threadIdx.x] = lse[j];
+      if (HVP) subar[threadIdx.x] = ubar[j];
+      else slab[threadIdx.x] = labels[j];
+    }
+    __syncthreads();
+    T acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = (T)0;
+    for (int q = 0; q < tn; ++q) {
+      const T* e = seta + q * KP;
+      const T l = dot_k<K>(th, e);
+      const T p = Arith<T>::ex(l - slse[q]);
+      T c;
+      if (HVP) {
+        const T u = dot_k<K>(vv, e);
+        c = p * (u - subar[q]);
+      } else {
+        c = (slab[q] == i ? (T)1 : (T)0) - p;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fma(c, e[k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc64[k] += (double)acc[k];
+  }
+  if (vi) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[((int64_t)blockIdx.x * N + i) * K + k] = acc64[k];
+  }
+}
+
+// Fixed-order sum over chunks: out[q] = scale * sum_c part[c][q].
+static __global__ void k_reduce_parts(const double* __restrict__ part, int nchunks, int64_t NK,
+                               double scale, double* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= NK) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * NK + q];
+  out[q] = s * scale;
+}
+
+// Fixed-order sum of the per-block objective partials: *out = scale * sum.
+static __global__ void k_reduce_obj(const double* __restrict__ part, int n, double scale,
+                             double* __restrict__ out) {
+  __shared__ double sred[32];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
+  const double bs = block_sum_fixed(s, sred);
+  if (threadIdx.x == 0) *out = bs * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Arg-min assignment in double, smallest index on ties (eq. Li_def).
+// ---------------------------------------------------------------------------
+constexpr int kAssignThreads = 256;
+constexpr int kAssignGT = 128;
+
+template <int DIM, int D>
+__global__ void __launch_bounds__(kAssignThreads)
+k_assign(Geom g, int N, const double* __restrict__ theta, int32_t* __restrict__ out,
+         double* __restrict__ gap, const int32_t* __restrict__ ref,
+         unsigned long long* __restrict__ mismatch) {
+  constexpr int K = basis_K(DIM, D);
+  __shared__ double sth[kAssignGT * K];
+  __shared__ int swarp[kAssignThreads / 32];
+  const int64_t j = (int64_t)blockIdx.x * kAssignThreads + threadIdx.x;
+  double x[DIM], eta[K];
+  if (j < g.P) {
+    pixel_coords<DIM>(g, j, x);
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = 0.0;
+  }
+  legendre_features<DIM, D>(x, eta);
+  double best = INFINITY, second = INFINITY;
+  int bi = 0;
+  for (int g0 = 0; g0 < N; g0 += kAssignGT) {
+    const int gn = min(kAssignGT, N - g0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < gn * K; e += kAssignThreads) sth[e] = theta[(int64_t)g0 * K + e];
+    __syncthreads();
+    for (int i = 0; i < gn; ++i) {
+      const double h = dot_k<K>(sth + i * K, eta);
+      if (h < best) {
+        second = best;
+        best = h;
+        bi = g0 + i;
+      } else if (h < second) {
+        second = h;
+      }
+    }
+  }
+  int miss = 0;
+  if (j < g.P) {
+    out[j] = bi;
+    if (gap) gap[j] = second - best;
+    if (ref) miss = (ref[j] != bi);
+  }
+  if (mismatch) {
+    const int wsum = __popc(__ballot_sync(0xffffffffu, miss));
+    if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < kAssignThreads / 32; ++w) tot += swarp[w];
+      if (tot) atomicAdd(mismatch, (unsigned long long)tot);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Features (testing aid): eta_out[j][k].
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int D>
+__global__ void k_features(Geom g, T* __restrict__ out) {
+  constexpr int K = basis_K(DIM, D);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= g.P) return;
+  T x[DIM], eta[K];
+  pixel_coords<DIM>(g, j, x);
+  legendre_features<DIM, D>(x, eta);
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[j * K + k] = eta[k];
+}
+
+// ---------------------------------------------------------------------------
+// Grain moments in 64-bit fixed point (exact, order independent).
+// ---------------------------------------------------------------------------
+template <int DIM, int DM>
+__global__ void k_moments(Geom g, const int32_t* __restrict__ labels, int N, double fx_scale,
+                          unsigned long long* __restrict__ mom, unsigned long long* __restrict__ cnt) {
+  constexpr int K = basis_K(DIM, DM);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = j < g.P;
+  int G = valid ? labels[j] : -1;
+  if (G < 0 || G >= N) G = -1;
+  double x[DIM], eta[K];
+  if (valid) {
+    pixel_coords<DIM>(g, j, x);
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = 0.0;
+  }
+  legendre_features<DIM, DM>(x, eta);
+  long long fx[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) fx[k] = (G >= 0) ? __double2ll_rn(eta[k] * fx_scale) : 0ll;
+  // warp aggregation when the whole warp shares one label (common: grains
+  // are spatially coherent); integer sums keep the result order independent
+  const int G0 = __shfl_sync(0xffffffffu, G, 0);
+  const bool uniform = __all_sync(0xffffffffu, G == G0) && G0 >= 0;
+  if (uniform) {
+    unsigned long long c = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      long long v = fx[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&mom[(int64_t)G0 * K + k], (unsigned long long)v);
+    }
+    c = 32;
+    if ((threadIdx.x & 31) == 0) atomicAdd(&cnt[G0], c);
+  } else if (G >= 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) atomicAdd(&mom[(int64_t)G * K + k], (unsigned long long)fx[k]);
+    atomicAdd(&cnt[G], 1ull);
+  }
+}
+
+static __global__ void k_moments_final(const unsigned long long* __restrict__ mom, int64_t n, double inv_scale,
+                                double* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = (double)(long long)mom[q] * inv_scale;
+}
+
+static __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_t P, int N, int* __restrict__ bad) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool b = j < P && (labels[j] < 0 || labels[j] >= N);
+  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+// ===========================================================================
+// Launch of one objective/gradient or HVP evaluation for a fixed
+// (precision, dimension, degree).
+// ===========================================================================
+inline int chunks_for(int64_t P, int grain_tiles, int sms) {
+  int64_t tiles = (P + kPixTile - 1) / kPixTile;
+  int64_t want = (int64_t)sms * 8 / grain_tiles;
+  if (want < 1) want = 1;
+  if (want > tiles) want = tiles;
+  return (int)want;
+}
+
+template <typename T, int DIM, int D>
+int eval_simt_dd(const EvalCall& c, cudaStream_t st) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<T>(K);
+  const int N = c.N;
+  const int64_t P = c.g.P;
+  const bool hvp = c.v != nullptr;
+  const bool want_grad = c.grad != nullptr;
+  const int sms = device_sm_count();
+
+  constexpr int ppt = 2;
+  const int blocks1 = (int)((P + kLseThreads * ppt - 1) / (kLseThreads * ppt));
+  const int gtiles = (N + kGradThreads - 1) / kGradThreads;
+  const int nch = chunks_for(P, gtiles, sms);
+  const int64_t tiles = (P + kPixTile - 1) / kPixTile;
+  const int64_t ppc = ((tiles + nch - 1) / nch) * kPixTile;
+  const int nch_eff = (int)((P + ppc - 1) / ppc);
+
+  Scratch sc(st);
+  T* thS = sc.get<T>((size_t)N * KP);
+  T* vS = hvp ? sc.get<T>((size_t)N * KP) : nullptr;
+  T* lse = (want_grad || hvp) ? sc.get<T>((size_t)P) : nullptr;
+  T* ubar = hvp ? sc.get<T>((size_t)P) : nullptr;
+  double* objp = (!hvp && c.obj) ? sc.get<double>((size_t)blocks1) : nullptr;
+  double* part = (want_grad || hvp) ? sc.get<double>((size_t)nch_eff * N * K) : nullptr;
+  if (!sc.ok()) return PD_ENOMEM;
+
+  const double tscale = Arith<T>::theta_scale(c.eps);
+  const int64_t nth = (int64_t)N * KP;
+  PD_TIMED(st, "scale_theta", k_scale_theta<T><<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(c.theta, N, K, KP, tscale, thS));
+  if (hvp) {
+    PD_TIMED(st, "scale_theta", k_copy_pad<T><<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(c.v, N, K, KP, vS));
+    PD_TIMED(st, "simt_hvp_pass1", k_pass1<T, DIM, D, ppt, true><<<blocks1, kLseThreads, 0, st>>>(c.g, c.labels, N, thS, vS, lse, ubar, nullptr));
+    dim3 grid2(nch_eff, gtiles);
+    PD_TIMED(st, "simt_hvp_pass2", k_pass2<T, DIM, D, true><<<grid2, kGradThreads, 0, st>>>(c.g, c.labels, N, thS, vS, lse, ubar, ppc, part));
+  } else {
+    PD_TIMED(st, "simt_lse_pass1", k_pass1<T, DIM, D, ppt, false><<<blocks1, kLseThreads, 0, st>>>(c.g, c.labels, N, thS, nullptr, lse, nullptr, objp));
+    if (want_grad) {
+      dim3 grid2(nch_eff, gtiles);
+      PD_TIMED(st, "simt_grad_pass2", k_pass2<T, DIM, D, false><<<grid2, kGradThreads, 0, st>>>(c.g, c.labels, N, thS, nullptr, lse, nullptr, ppc, part));
+    }
+  }
+  if (c.obj && !hvp) PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, blocks1, 1.0 / (double)P, c.obj));
+  if (want_grad || hvp) {
+    const int64_t NK = (int64_t)N * K;
+    const double scale = hvp ? -1.0 / (c.eps * c.eps * (double)P) : -1.0 / (c.eps * (double)P);
+    PD_TIMED(st, "reduce_parts", k_reduce_parts<<<(unsigned)((NK + 255) / 256), 256, 0, st>>>(part, nch_eff, NK, scale, hvp ? c.hv : c.grad));
+  }
+  if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+  return PD_OK;
+}
+
+}  // namespace
+}  // namespace pd

@@ -1,0 +1,114 @@
+// pd_simt_misc.cu -- launchers of the assignment, feature, moment and label
+// kernels, and the precision/dimension dispatch of the CUDA-core evaluation.
+#include "pd_simt_kernels.cuh"
+
+namespace pd {
+
+int eval_simt_f32_2d(const EvalCall& c, cudaStream_t st);
+int eval_simt_f64_2d(const EvalCall& c, cudaStream_t st);
+int eval_simt_f32_3d(const EvalCall& c, cudaStream_t st);
+int eval_simt_f64_3d(const EvalCall& c, cudaStream_t st);
+
+int eval_simt(const EvalCall& c, cudaStream_t st) {
+  if (c.dim == 2) {
+    if (c.prec == PD_FP64) return eval_simt_f64_2d(c, st);
+    if (c.prec == PD_FP32) return eval_simt_f32_2d(c, st);
+  } else if (c.dim == 3) {
+    if (c.prec == PD_FP64) return eval_simt_f64_3d(c, st);
+    if (c.prec == PD_FP32) return eval_simt_f32_3d(c, st);
+  }
+  return PD_ENOTSUP;
+}
+
+template <class F>
+static bool dispatch_dim_deg(int dim, int d, F&& f) {
+  using std::integral_constant;
+  if (dim == 2) {
+    switch (d) {
+      case 1: f(integral_constant<int, 2>{}, integral_constant<int, 1>{}); return true;
+      case 2: f(integral_constant<int, 2>{}, integral_constant<int, 2>{}); return true;
+      case 3: f(integral_constant<int, 2>{}, integral_constant<int, 3>{}); return true;
+      case 4: f(integral_constant<int, 2>{}, integral_constant<int, 4>{}); return true;
+      case 5: f(integral_constant<int, 2>{}, integral_constant<int, 5>{}); return true;
+      case 6: f(integral_constant<int, 2>{}, integral_constant<int, 6>{}); return true;
+      case 7: f(integral_constant<int, 2>{}, integral_constant<int, 7>{}); return true;
+      default: return false;
+    }
+  } else if (dim == 3) {
+    switch (d) {
+      case 1: f(integral_constant<int, 3>{}, integral_constant<int, 1>{}); return true;
+      case 2: f(integral_constant<int, 3>{}, integral_constant<int, 2>{}); return true;
+      case 3: f(integral_constant<int, 3>{}, integral_constant<int, 3>{}); return true;
+      case 4: f(integral_constant<int, 3>{}, integral_constant<int, 4>{}); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
+int assign_simt(const Geom& g, int dim, int d, int N, const double* theta, int32_t* out, double* gap,
+                const int32_t* ref, int64_t* mismatch, cudaStream_t st) {
+  if (mismatch && cudaMemsetAsync(mismatch, 0, sizeof(int64_t), st) != cudaSuccess) return PD_ECUDA;
+  if (g.P == 0) return PD_OK;
+  const unsigned blocks = (unsigned)((g.P + kAssignThreads - 1) / kAssignThreads);
+  bool ok = dispatch_dim_deg(dim, d, [&](auto dimc, auto degc) {
+    constexpr int DIM = decltype(dimc)::value;
+    constexpr int D = decltype(degc)::value;
+    PD_TIMED(st, "assign", k_assign<DIM, D><<<blocks, kAssignThreads, 0, st>>>(g, N, theta, out, gap, ref, reinterpret_cast<unsigned long long*>(ref ? mismatch : nullptr)));
+  });
+  if (!ok) return PD_ENOTSUP;
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+int features_simt(const Geom& g, int dim, int d, int prec, void* out, cudaStream_t st) {
+  if (g.P == 0) return PD_OK;
+  const unsigned blocks = (unsigned)((g.P + 255) / 256);
+  bool ok = dispatch_dim_deg(dim, d, [&](auto dimc, auto degc) {
+    constexpr int DIM = decltype(dimc)::value;
+    constexpr int D = decltype(degc)::value;
+    if (prec == PD_FP64) k_features<double, DIM, D><<<blocks, 256, 0, st>>>(g, (double*)out);
+    else k_features<float, DIM, D><<<blocks, 256, 0, st>>>(g, (float*)out);
+  });
+  if (!ok) return PD_ENOTSUP;
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+int moments_simt(const Geom& g, int dim, int dm, const int32_t* labels, int N, double* mom_out,
+                 int64_t* counts_out, cudaStream_t st) {
+  const int K = basis_K(dim, dm);
+  Scratch sc(st);
+  unsigned long long* mom = sc.get<unsigned long long>((size_t)N * K);
+  if (!sc.ok()) return PD_ENOMEM;
+  if (cudaMemsetAsync(mom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+  if (cudaMemsetAsync(counts_out, 0, sizeof(int64_t) * N, st) != cudaSuccess) return PD_ECUDA;
+  // |psi| <= 1, so a grain sum is bounded by P: pick the largest power-of-two
+  // scale that keeps P * scale below 2^62.
+  int bits = 0;
+  while (bits < 62 && ((int64_t)1 << bits) <= g.P) ++bits;
+  const int shift = 62 - bits;
+  const double scale = ldexp(1.0, shift);
+  if (g.P > 0) {
+    const unsigned blocks = (unsigned)((g.P + 255) / 256);
+    bool ok = true;
+    auto launch = [&](auto dimc, auto dmc) {
+      constexpr int DIM = decltype(dimc)::value;
+      constexpr int DM = decltype(dmc)::value;
+      PD_TIMED(st, "moments", k_moments<DIM, DM><<<blocks, 256, 0, st>>>(g, labels, N, scale, mom, reinterpret_cast<unsigned long long*>(counts_out)));
+    };
+    if (dm < 1 || dm > 4) return PD_ENOTSUP;
+    ok = dispatch_dim_deg(dim, dm, launch);
+    if (!ok) return PD_ENOTSUP;
+  }
+  const int64_t n = (int64_t)N * K;
+  k_moments_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, n, ldexp(1.0, -shift), mom_out);
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+int check_labels_simt(const int32_t* labels, int64_t P, int N, int* bad_dev, cudaStream_t st) {
+  if (cudaMemsetAsync(bad_dev, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
+  if (P == 0) return PD_OK;
+  k_check_labels<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(labels, P, N, bad_dev);
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+}  // namespace pd

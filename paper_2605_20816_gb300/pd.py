@@ -1,0 +1,267 @@
+"""Thin Python binding of libpd (ctypes).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch tensors become device pointers, the current torch
+CUDA stream becomes the stream argument, and a negative status code becomes
+a ``PdError``.  All arithmetic happens inside libpd's CUDA kernels; there is
+no CPU fallback.  If libpd.so is missing it is built from csrc/ with nvcc,
+and any failure to build or load raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+PD_OK, PD_EINVAL, PD_ELABEL, PD_ENAN, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+PD_FP64, PD_FP32, PD_BF16, PD_BF16X3 = 0, 1, 2, 3
+PD_INIT_GIVEN, PD_INIT_ZERO, PD_INIT_HEURISTIC = 0, 1, 2
+PD_METHOD_LBFGS, PD_METHOD_NEWTON_CG = 0, 1
+PREC = {"fp64": PD_FP64, "fp32": PD_FP32, "bf16": PD_BF16, "bf16x3": PD_BF16X3}
+
+
+class PdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+
+
+class pd_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int64 * 3), ("coords", C.c_void_p), ("P", C.c_int64)]
+
+
+class pd_eval_opts(C.Structure):
+    _fields_ = [("d", C.c_int), ("eps", C.c_double), ("prec", C.c_int)]
+
+
+class pd_fit_opts(C.Structure):
+    _fields_ = [("d", C.c_int), ("eps", C.c_double), ("init", C.c_int), ("method", C.c_int),
+                ("max_iter", C.c_int), ("lbfgs_m", C.c_int), ("max_cg", C.c_int), ("prec", C.c_int),
+                ("refine_iter", C.c_int), ("gtol", C.c_double), ("target_phi", C.c_double),
+                ("switch_rtol", C.c_double)]
+
+
+class pd_fit_report(C.Structure):
+    _fields_ = [("phi", C.c_double), ("gnorm", C.c_double), ("err", C.c_double), ("iters", C.c_int),
+                ("iters_phase1", C.c_int), ("evals", C.c_int64), ("hvps", C.c_int64), ("status", C.c_int),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the in-tree libpd.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp, i64, dbl, ip = C.c_void_p, C.c_int64, C.c_double, C.c_int
+            gp = C.POINTER(pd_grid)
+            L.pd_K.argtypes = [ip, ip]
+            L.pd_alpha.argtypes = [ip, ip, C.POINTER(C.c_int)]
+            L.pd_strerror.argtypes = [ip]
+            L.pd_strerror.restype = C.c_char_p
+            L.pd_features.argtypes = [gp, ip, ip, vp, vp]
+            L.pd_objective_grad.argtypes = [gp, vp, ip, vp, C.POINTER(pd_eval_opts), vp, vp, vp]
+            L.pd_hvp.argtypes = [gp, vp, ip, vp, vp, C.POINTER(pd_eval_opts), vp, vp]
+            L.pd_assign.argtypes = [gp, ip, ip, vp, vp, vp, vp, vp, vp]
+            L.pd_moments.argtypes = [gp, vp, ip, ip, vp, vp, vp]
+            L.pd_check_labels.argtypes = [gp, vp, ip, vp]
+            L.pd_theta_from_apd.argtypes = [ip, ip, ip, vp, vp, vp, vp]
+            L.pd_heuristic_init.argtypes = [gp, vp, ip, ip, vp, vp]
+            L.pd_fit.argtypes = [gp, vp, ip, C.POINTER(pd_fit_opts), vp, C.POINTER(pd_fit_report), vp]
+            L.pd_prof_enable.argtypes = [ip]
+            L.pd_prof_read.argtypes = [ip, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+            L.pd_release.argtypes = []
+            L.pd_release.restype = None
+            _lib = L
+    return _lib
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().pd_strerror(code).decode()
+    except Exception:
+        return "status %d" % code
+
+
+def _check(rc: int, where: str):
+    if rc != PD_OK:
+        raise PdError(rc, where)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Pixel set: structured grid ``shape`` = (n1, n2[, n3]) (axis 1
+    fastest), or an explicit point list ``coords`` (CUDA float64 [P, dim])."""
+
+    def __init__(self, shape=None, coords: torch.Tensor | None = None):
+        if coords is not None:
+            self.coords = coords.contiguous().to(torch.float64)
+            self.dim = int(self.coords.shape[1])
+            self.P = int(self.coords.shape[0])
+            n = [0, 0, 0]
+            ptr = self.coords.data_ptr()
+        else:
+            self.coords = None
+            self.shape = tuple(int(s) for s in shape)
+            self.dim = len(self.shape)
+            self.P = int(math.prod(self.shape))
+            n = list(self.shape) + [1] * (3 - self.dim)
+            ptr = None
+        self.c = pd_grid(self.dim, (C.c_int64 * 3)(*n), ptr, self.P)
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+def pd_K(dim: int, d: int) -> int:
+    return lib().pd_K(dim, d)
+
+
+def pd_alpha(dim: int, d: int):
+    K = pd_K(dim, d)
+    buf = (C.c_int * (K * dim))()
+    rc = lib().pd_alpha(dim, d, buf)
+    if rc < 0:
+        raise PdError(rc, "pd_alpha")
+    return [tuple(buf[k * dim:(k + 1) * dim]) for k in range(K)]
+
+
+def pd_features(grid: Grid, d: int, prec: int = PD_FP64) -> torch.Tensor:
+    K = pd_K(grid.dim, d)
+    out = torch.empty((grid.P, K), dtype=torch.float64 if prec == PD_FP64 else torch.float32, device="cuda")
+    _check(lib().pd_features(grid.ref, d, prec, _ptr(out), _stream()), "pd_features")
+    return out
+
+
+def pd_objective_grad(grid: Grid, labels: torch.Tensor, N: int, theta: torch.Tensor, d: int, eps: float,
+                      prec: int = PD_FP64, want_grad: bool = True, obj_out=None, grad_out=None):
+    """Returns (Phi as a 0-d CUDA float64 tensor, grad [N, K] or None)."""
+    opts = pd_eval_opts(d, float(eps), int(prec))
+    obj = obj_out if obj_out is not None else torch.empty((), dtype=torch.float64, device="cuda")
+    grad = None
+    if want_grad:
+        grad = grad_out if grad_out is not None else torch.empty_like(theta, dtype=torch.float64)
+    _check(lib().pd_objective_grad(grid.ref, _ptr(labels), N, _ptr(theta), C.byref(opts), _ptr(obj),
+                                   _ptr(grad), _stream()), "pd_objective_grad")
+    return obj, grad
+
+
+def pd_hvp(grid: Grid, labels, N: int, theta: torch.Tensor, v: torch.Tensor, d: int, eps: float,
+           prec: int = PD_FP64, out=None):
+    opts = pd_eval_opts(d, float(eps), int(prec))
+    hv = out if out is not None else torch.empty_like(theta, dtype=torch.float64)
+    _check(lib().pd_hvp(grid.ref, _ptr(labels), N, _ptr(theta), _ptr(v), C.byref(opts), _ptr(hv), _stream()),
+           "pd_hvp")
+    return hv
+
+
+def pd_assign(grid: Grid, N: int, d: int, theta: torch.Tensor, want_gap: bool = False,
+              ref_labels: torch.Tensor | None = None):
+    """Returns (labels int32 [P], gap float64 [P] or None, mismatch int64 0-d or None)."""
+    lab = torch.empty(grid.P, dtype=torch.int32, device="cuda")
+    gap = torch.empty(grid.P, dtype=torch.float64, device="cuda") if want_gap else None
+    mis = torch.empty((), dtype=torch.int64, device="cuda") if ref_labels is not None else None
+    _check(lib().pd_assign(grid.ref, N, d, _ptr(theta), _ptr(lab), _ptr(gap), _ptr(ref_labels), _ptr(mis),
+                           _stream()), "pd_assign")
+    return lab, gap, mis
+
+
+def pd_moments(grid: Grid, labels: torch.Tensor, N: int, dm: int):
+    K = pd_K(grid.dim, dm)
+    mom = torch.empty((N, K), dtype=torch.float64, device="cuda")
+    cnt = torch.empty(N, dtype=torch.int64, device="cuda")
+    _check(lib().pd_moments(grid.ref, _ptr(labels), N, dm, _ptr(mom), _ptr(cnt), _stream()), "pd_moments")
+    return mom, cnt
+
+
+def pd_check_labels(grid: Grid, labels: torch.Tensor, N: int) -> int:
+    """Returns the status code (PD_OK or PD_ELABEL); raises on other errors."""
+    rc = lib().pd_check_labels(grid.ref, _ptr(labels), N, _stream())
+    if rc not in (PD_OK, PD_ELABEL):
+        raise PdError(rc, "pd_check_labels")
+    return rc
+
+
+def pd_theta_from_apd(dim: int, d: int, y, w, A=None):
+    """Host conversion; y [N, dim], w [N], A [N, dim, dim] or None (numpy
+    or CPU tensors).  Returns a CPU float64 tensor [N, K]."""
+    y = torch.as_tensor(y, dtype=torch.float64).contiguous()
+    w = torch.as_tensor(w, dtype=torch.float64).contiguous()
+    Ah = None if A is None else torch.as_tensor(A, dtype=torch.float64).contiguous()
+    N = int(w.numel())
+    out = torch.empty((N, pd_K(dim, d)), dtype=torch.float64)
+    rc = lib().pd_theta_from_apd(dim, d, N, C.c_void_p(y.data_ptr()), C.c_void_p(w.data_ptr()),
+                                 None if Ah is None else C.c_void_p(Ah.data_ptr()), C.c_void_p(out.data_ptr()))
+    _check(rc, "pd_theta_from_apd")
+    return out
+
+
+def pd_heuristic_init(grid: Grid, labels: torch.Tensor, N: int, d: int) -> torch.Tensor:
+    out = torch.empty((N, pd_K(grid.dim, d)), dtype=torch.float64, device="cuda")
+    _check(lib().pd_heuristic_init(grid.ref, _ptr(labels), N, d, _ptr(out), _stream()), "pd_heuristic_init")
+    return out
+
+
+def pd_fit(grid: Grid, labels: torch.Tensor, N: int, d: int, eps: float, theta: torch.Tensor | None = None,
+           init: int = PD_INIT_ZERO, method: int = PD_METHOD_LBFGS, max_iter: int = 1000, lbfgs_m: int = 10,
+           max_cg: int = 50, prec: int = PD_FP64, refine_iter: int = 0, gtol: float = 0.0,
+           target_phi: float = -math.inf, switch_rtol: float = 0.0):
+    """Returns (theta [N, K] CUDA float64, report dict)."""
+    K = pd_K(grid.dim, d)
+    th = torch.zeros((N, K), dtype=torch.float64, device="cuda") if theta is None else theta.clone().contiguous()
+    opts = pd_fit_opts(d, float(eps), init, method, max_iter, lbfgs_m, max_cg, prec, refine_iter, gtol,
+                       target_phi, switch_rtol)
+    rep = pd_fit_report()
+    _check(lib().pd_fit(grid.ref, _ptr(labels), N, C.byref(opts), _ptr(th), C.byref(rep), _stream()), "pd_fit")
+    return th, rep.as_dict()
+
+
+def pd_prof_enable(on: bool):
+    _check(lib().pd_prof_enable(1 if on else 0), "pd_prof_enable")
+
+
+def pd_prof_read():
+    """{kernel name: (launches, total device ms)} of the traced launches."""
+    cap = 64
+    names = (C.c_char_p * cap)()
+    cnt = (C.c_int64 * cap)()
+    ms = (C.c_double * cap)()
+    n = lib().pd_prof_read(cap, names, cnt, ms)
+    if n < 0:
+        raise PdError(n, "pd_prof_read")
+    return {names[q].decode(): (int(cnt[q]), float(ms[q])) for q in range(min(n, cap))}
+
+
+def pd_release():
+    lib().pd_release()
