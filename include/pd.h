@@ -138,7 +138,8 @@ int pd_hvp(const pd_grid* grid, const int32_t* labels, int N,
  * ref_labels (device int32[P] or NULL) with mismatch_out (device int64
  * scalar): the number of pixels with labels_out != ref_labels, i.e.
  * Err^G * P (Sec. 4); mismatch_out is overwritten, not accumulated.
- * P == 0 writes mismatch 0 and returns. */
+ * P == 0 writes 0 to mismatch_out (if given; ref_labels may then be NULL)
+ * and returns. */
 int pd_assign(const pd_grid* grid, int N, int d, const double* theta,
               int32_t* labels_out, double* gap_out, const int32_t* ref_labels,
               int64_t* mismatch_out, void* stream);

@@ -242,7 +242,7 @@ int pd_assign(const pd_grid* grid, int N, int d, const double* theta, int32_t* l
   if (N < 1 || d < 1) return PD_EINVAL;
   if (!degree_ok(grid->dim, d)) return PD_ENOTSUP;
   if (g.P > 0 && (!theta || !labels_out)) return PD_EINVAL;
-  if ((ref_labels == nullptr) != (mismatch_out == nullptr)) return PD_EINVAL;
+  if (g.P > 0 && (ref_labels == nullptr) != (mismatch_out == nullptr)) return PD_EINVAL;
   device_sm_count();
   return assign_simt(g, grid->dim, d, N, theta, labels_out, gap_out, ref_labels, mismatch_out,
                      (cudaStream_t)stream);

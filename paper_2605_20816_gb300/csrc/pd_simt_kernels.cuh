@@ -202,7 +202,11 @@ k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
 // Pass 2: one thread per grain over pixel tiles.
 //   GRAD: c = delta_{iG(x)} - p_i(x)
 //   HVP : c = p_i(x) (u_i(x) - ubar(x))
-// accumulates c * eta(x) per chunk of pixels into part[chunk][i][k].
+// accumulates c * eta(x) per chunk of pixels into part[chunk][i][k].  Two
+// pixels per step give two independent dependency chains.  When c is zero
+// for every grain of a warp at both pixels (p underflows to zero and no
+// label matches, the common case for small eps) the accumulation is skipped:
+// adding c * eta with c = 0 changes nothing, so results are identical.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int D, bool HVP>
 __global__ void __launch_bounds__(kGradThreads)
@@ -215,6 +219,7 @@ k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
   __shared__ T slse[kPixTile];
   __shared__ T subar[HVP ? kPixTile : 1];
   __shared__ int slab[kPixTile];
+  __shared__ double sacc[K * kGradThreads];  // per-thread double accumulators
 
   const int i = blockIdx.y * kGradThreads + threadIdx.x;
   const bool vi = i < N;
@@ -223,10 +228,8 @@ k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
   for (int k = 0; k < K; ++k) {
     th[k] = vi ? thS[(int64_t)i * KP + k] : (T)0;
     if (HVP) vv[k] = vi ? vS[(int64_t)i * KP + k] : (T)0;
+    sacc[k * kGradThreads + threadIdx.x] = 0.0;
   }
-  double acc64[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc64[k] = 0.0;
 
   const int64_t p0 = (int64_t)blockIdx.x * ppc;
   const int64_t p1 = min(p0 + ppc, g.P);
@@ -248,37 +251,66 @@ k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
     T acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = (T)0;
-    for (int q = 0; q < tn; ++q) {
-      const T* e = seta + q * KP;
-      const T l = dot_k<K>(th, e);
+    auto coef = [&](int q, T l) -> T {
       const T p = Arith<T>::ex(l - slse[q]);
       T c;
       if (HVP) {
-        const T u = dot_k<K>(vv, e);
+        const T u = dot_k<K>(vv, seta + q * KP);
         c = p * (u - subar[q]);
       } else {
         c = (slab[q] == i ? (T)1 : (T)0) - p;
       }
+      return vi ? c : (T)0;
+    };
+    int q = 0;
+    for (; q + 2 <= tn; q += 2) {
+      const T* e0 = seta + q * KP;
+      const T* e1 = e0 + KP;
+      const T l0 = dot_k<K>(th, e0);
+      const T l1 = dot_k<K>(th, e1);
+      const T c0 = coef(q, l0);
+      const T c1 = coef(q + 1, l1);
+      if (__any_sync(0xffffffffu, c0 != (T)0 || c1 != (T)0)) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] = fma(c, e[k], acc[k]);
+        for (int k = 0; k < K; ++k) acc[k] = fma(c1, e1[k], fma(c0, e0[k], acc[k]));
+      }
+    }
+    if (q < tn) {
+      const T* e0 = seta + q * KP;
+      const T c0 = coef(q, dot_k<K>(th, e0));
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fma(c0, e0[k], acc[k]);
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc64[k] += (double)acc[k];
+    for (int k = 0; k < K; ++k) sacc[k * kGradThreads + threadIdx.x] += (double)acc[k];
   }
   if (vi) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) part[((int64_t)blockIdx.x * N + i) * K + k] = acc64[k];
+    for (int k = 0; k < K; ++k)
+      part[((int64_t)blockIdx.x * N + i) * K + k] = sacc[k * kGradThreads + threadIdx.x];
   }
 }
 
-// Fixed-order sum over chunks: out[q] = scale * sum_c part[c][q].
-static __global__ void k_reduce_parts(const double* __restrict__ part, int nchunks, int64_t NK,
-                               double scale, double* __restrict__ out) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= NK) return;
+// Fixed-order sum over chunks: out[q] = scale * sum_c part[c][q].  A block
+// covers 32 consecutive q (coalesced) with 8 chunk phases; phase y sums the
+// chunks c = y (mod 8) in ascending order, then the 8 phase sums are added
+// in phase order: the same order every run.
+constexpr int kRedPhases = 8;
+static __global__ void __launch_bounds__(32 * kRedPhases)
+k_reduce_parts(const double* __restrict__ part, int nchunks, int64_t NK, double scale, double* __restrict__ out) {
+  __shared__ double ssum[kRedPhases][32];
+  const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * NK + q];
-  out[q] = s * scale;
+  if (q < NK)
+    for (int c = threadIdx.y; c < nchunks; c += kRedPhases) s += part[(int64_t)c * NK + q];
+  ssum[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && q < NK) {
+    double t = 0.0;
+#pragma unroll
+    for (int y = 0; y < kRedPhases; ++y) t += ssum[y][threadIdx.x];
+    out[q] = t * scale;
+  }
 }
 
 // Fixed-order sum of the per-block objective partials: *out = scale * sum.
@@ -427,7 +459,7 @@ static __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_
 // ===========================================================================
 inline int chunks_for(int64_t P, int grain_tiles, int sms) {
   int64_t tiles = (P + kPixTile - 1) / kPixTile;
-  int64_t want = (int64_t)sms * 8 / grain_tiles;
+  int64_t want = ((int64_t)sms * 6 + grain_tiles - 1) / grain_tiles;
   if (want < 1) want = 1;
   if (want > tiles) want = tiles;
   return (int)want;
@@ -479,7 +511,7 @@ int eval_simt_dd(const EvalCall& c, cudaStream_t st) {
   if (want_grad || hvp) {
     const int64_t NK = (int64_t)N * K;
     const double scale = hvp ? -1.0 / (c.eps * c.eps * (double)P) : -1.0 / (c.eps * (double)P);
-    PD_TIMED(st, "reduce_parts", k_reduce_parts<<<(unsigned)((NK + 255) / 256), 256, 0, st>>>(part, nch_eff, NK, scale, hvp ? c.hv : c.grad));
+    PD_TIMED(st, "reduce_parts", k_reduce_parts<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(part, nch_eff, NK, scale, hvp ? c.hv : c.grad));
   }
   if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
   return PD_OK;

@@ -45,14 +45,20 @@ def apd_params(seed: int, N: int, dim: int = 2, lam=(0.5, 2.0), w_max: float = 0
     return y, w, A
 
 
-def poly_params(seed: int, N: int, dim: int, K: int):
-    """Sites uniform in [-1,1]^dim and a standard-normal [N, K] coefficient
-    array.  A degree-d polynomial diagram is built by each side from these:
-    the coefficients of total degree <= 1 come from the sites (a power
-    diagram with zero weights) and the rest are the normal draws."""
+def poly_params(seed: int, N: int, dim: int, K: int, sigma: float | None = None):
+    """Sites uniform in [-1,1]^dim and an [N, K] array of normal draws
+    N(0, sigma^2), sigma = 1/(2N) by default.  A degree-d polynomial diagram
+    is built by each side from these: the coefficients of total degree <= 1
+    come from the sites (a power diagram with zero weights) and the rest are
+    the normal draws.  The spread 1/(2N) keeps the perturbation comparable to
+    the power-diagram cost differences inside a cell (about 4/N), so nearly
+    all N grains stay non-empty (485 of 500 at N = 500) while about 18% of
+    the pixels change label relative to the Voronoi diagram of the sites;
+    with unit spread only about 85 of 500 grains would be non-empty."""
     g = rng(seed)
     y = g.uniform(-1.0, 1.0, size=(N, dim))
-    z = g.standard_normal((N, K))
+    s = 1.0 / (2.0 * N) if sigma is None else float(sigma)
+    z = s * g.standard_normal((N, K))
     return y, z
 
 
