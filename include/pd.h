@@ -232,6 +232,12 @@ int pd_fit(const pd_grid* grid, const int32_t* labels, int N,
 int pd_prof_enable(int on);
 int pd_prof_read(int cap, const char** names, int64_t* launches, double* total_ms);
 
+/* Synchronous throughput microbenchmark of one execution unit on the
+ * current device, for roofline denominators: kind 0 = FP32 FMA, 1 = MUFU
+ * ex2 (approximate base-2 exponential), 2 = FP64 FMA.  Writes operations
+ * per second (one FMA or one ex2 = one operation) to *ops_per_s (host). */
+int pd_microbench(int kind, double* ops_per_s, void* stream);
+
 /* Release cached library state on the current device (memory pool
  * reservations are trimmed).  Safe to call at any time when no call of
  * this library is in flight. */

@@ -83,6 +83,7 @@ def lib():
             L.pd_fit.argtypes = [gp, vp, ip, C.POINTER(pd_fit_opts), vp, C.POINTER(pd_fit_report), vp]
             L.pd_prof_enable.argtypes = [ip]
             L.pd_prof_read.argtypes = [ip, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+            L.pd_microbench.argtypes = [ip, C.POINTER(C.c_double), vp]
             L.pd_release.argtypes = []
             L.pd_release.restype = None
             _lib = L
@@ -261,6 +262,13 @@ def pd_prof_read():
     if n < 0:
         raise PdError(n, "pd_prof_read")
     return {names[q].decode(): (int(cnt[q]), float(ms[q])) for q in range(min(n, cap))}
+
+
+def pd_microbench(kind: int) -> float:
+    """Operations per second of one unit: 0 FP32 FMA, 1 MUFU ex2, 2 FP64 FMA."""
+    v = C.c_double()
+    _check(lib().pd_microbench(kind, C.byref(v), _stream()), "pd_microbench")
+    return v.value
 
 
 def pd_release():
