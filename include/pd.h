@@ -58,6 +58,8 @@ extern "C" {
 #define PD_ECUDA (-5)    /* a CUDA runtime call or kernel launch failed      */
 #define PD_ETIMEOUT (-6) /* a bounded device wait gave up                    */
 #define PD_ENOTSUP (-7)  /* valid but unsupported combination (e.g. degree)  */
+#define PD_ESCRATCH (-8) /* needs more scratch than the fixed array of
+                            pd_objective_grad_noalloc holds               */
 
 /* ---- precisions of an evaluation --------------------------------------- */
 #define PD_FP64 0  /* all arithmetic in double                              */
@@ -237,6 +239,38 @@ int pd_prof_read(int cap, const char** names, int64_t* launches, double* total_m
  * ex2 (approximate base-2 exponential), 2 = FP64 FMA.  Writes operations
  * per second (one FMA or one ex2 = one operation) to *ops_per_s (host). */
 int pd_microbench(int kind, double* ops_per_s, void* stream);
+
+/* ---- evaluation without any device allocation -------------------------- */
+/* pd_objective_grad allocates its scratch (the scaled parameters, log S per
+ * pixel, per-block and per-chunk partial sums) from the device's
+ * stream-ordered memory pool.  Some callers cannot let a library allocate:
+ * a host whose device memory is entirely reserved up front by another
+ * framework's allocator, a latency-bound loop that must not grow or touch
+ * a memory pool after start-up, or an embedding that forbids cudaMalloc /
+ * cudaMallocAsync outside its own initialisation.  This entry point gives
+ * them the same evaluation with all scratch taken from one fixed array of
+ * PD_NOALLOC_SCRATCH_BYTES compiled into the library (held on every device
+ * that loads the library until the process exits); it calls no cudaMalloc,
+ * cudaFree or any allocating routine.  The paper has no counterpart: this
+ * is a deployment variant of the objective/gradient call above.
+ *
+ * Arguments, results and precisions are those of pd_objective_grad, limited
+ * to 2-D pixel sets (PD_ENOTSUP otherwise) and PD_FP64 / PD_FP32.  A problem
+ * whose scratch (about P * 4 bytes in FP32, P * 8 in FP64, plus at least one
+ * N*K*8-byte gradient partial) does not fit returns PD_ESCRATCH before
+ * anything is enqueued.  Results equal pd_objective_grad's up to the order
+ * of the fixed cross-chunk sum (fewer chunks when scratch is tight).
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (on different streams, or from several host threads)
+ * race on it and must be serialised by the caller. */
+#define PD_NOALLOC_SCRATCH_BYTES (32u << 20)
+int pd_objective_grad_noalloc(const pd_grid* grid, const int32_t* labels,
+                              int N, const double* theta,
+                              const pd_eval_opts* opts, double* obj_out,
+                              double* grad_out, void* stream);
 
 /* Release cached library state on the current device (memory pool
  * reservations are trimmed).  Safe to call at any time when no call of

@@ -183,6 +183,7 @@ const char* pd_strerror(int code) {
     case PD_ECUDA: return "CUDA runtime error";
     case PD_ETIMEOUT: return "bounded device wait timed out";
     case PD_ENOTSUP: return "unsupported combination";
+    case PD_ESCRATCH: return "problem exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

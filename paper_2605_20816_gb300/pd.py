@@ -19,6 +19,8 @@ import torch
 from . import build as _build
 
 PD_OK, PD_EINVAL, PD_ELABEL, PD_ENAN, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+PD_ESCRATCH = -8
+PD_NOALLOC_SCRATCH_BYTES = 32 << 20
 PD_FP64, PD_FP32, PD_BF16, PD_BF16X3 = 0, 1, 2, 3
 PD_INIT_GIVEN, PD_INIT_ZERO, PD_INIT_HEURISTIC = 0, 1, 2
 PD_METHOD_LBFGS, PD_METHOD_NEWTON_CG = 0, 1
@@ -83,6 +85,7 @@ def lib():
             L.pd_fit.argtypes = [gp, vp, ip, C.POINTER(pd_fit_opts), vp, C.POINTER(pd_fit_report), vp]
             L.pd_prof_enable.argtypes = [ip]
             L.pd_prof_read.argtypes = [ip, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+            L.pd_objective_grad_noalloc.argtypes = [gp, vp, ip, vp, C.POINTER(pd_eval_opts), vp, vp, vp]
             L.pd_microbench.argtypes = [ip, C.POINTER(C.c_double), vp]
             L.pd_release.argtypes = []
             L.pd_release.restype = None
@@ -175,6 +178,19 @@ def pd_objective_grad(grid: Grid, labels: torch.Tensor, N: int, theta: torch.Ten
         grad = grad_out if grad_out is not None else torch.empty_like(theta, dtype=torch.float64)
     _check(lib().pd_objective_grad(grid.ref, _ptr(labels), N, _ptr(theta), C.byref(opts), _ptr(obj),
                                    _ptr(grad), _stream()), "pd_objective_grad")
+    return obj, grad
+
+
+def pd_objective_grad_noalloc(grid: Grid, labels: torch.Tensor, N: int, theta: torch.Tensor, d: int,
+                              eps: float, prec: int = PD_FP32, obj_out=None, grad_out=None):
+    """pd_objective_grad with all scratch in the library's fixed device
+    array, for callers that cannot allocate device memory; the caller passes
+    the output buffers (allocated here only when omitted)."""
+    opts = pd_eval_opts(d, float(eps), int(prec))
+    obj = obj_out if obj_out is not None else torch.empty((), dtype=torch.float64, device="cuda")
+    grad = grad_out if grad_out is not None else torch.empty_like(theta, dtype=torch.float64)
+    _check(lib().pd_objective_grad_noalloc(grid.ref, _ptr(labels), N, _ptr(theta), C.byref(opts), _ptr(obj),
+                                           _ptr(grad), _stream()), "pd_objective_grad_noalloc")
     return obj, grad
 
 
