@@ -259,7 +259,7 @@ int lbfgs_phase(Problem& pb, int prec, Point& cur, int max_iter, int m, double g
   for (; it < max_iter; ++it) {
     const double gn = sqrt(dot(cur.g, cur.g));
     if (gn <= gtol) { res->status = 1; break; }
-    if (-cur.f >= target_phi) { res->status = 3; break; }
+    if (isfinite(target_phi) && -cur.f >= target_phi) { res->status = 3; break; }
     for (int q = 0; q < n; ++q) dir[q] = -cur.g[q];
     const int h = (int)S.size();  // newest pair last
     for (int j = h - 1; j >= 0; --j) {
@@ -307,7 +307,7 @@ int newton_phase(Problem& pb, int prec, Point& cur, int max_iter, int max_cg, do
   for (; it < max_iter; ++it) {
     const double gn = sqrt(dot(cur.g, cur.g));
     if (gn <= gtol) { res->status = 1; break; }
-    if (-cur.f >= target_phi) { res->status = 3; break; }
+    if (isfinite(target_phi) && -cur.f >= target_phi) { res->status = 3; break; }
     const double tol = (gn < 0.25 ? sqrt(gn) : 0.5) * gn;
     for (int q = 0; q < n; ++q) { s[q] = 0.0; r[q] = -cur.g[q]; p[q] = r[q]; }
     double rr = dot(r, r);

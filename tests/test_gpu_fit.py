@@ -1,0 +1,118 @@
+"""The ascent scheme on the GPU (pd_fit) against the oracle's (Sec. 5.2).
+
+Both implement the same L-BFGS (memory 10, strong-Wolfe line search with
+c1 = 1e-4, c2 = 0.9, first trial step 1/||g||, then 1) from the same
+description, so their iterates agree while the line searches take the same
+decisions; over long separable runs rounding differences may change a
+decision, so there the test compares what is unique: the recovered diagram
+(Err = 0) and the certificate Phi > -log 2 / |Omega| of Cor. 4.10.  On
+non-separable data the maximiser is unique (Prop. 4.11) and every method
+and precision schedule must reach its objective to 1e-8 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_20816_gb300 import pd, synth
+from helpers import power_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def config1():
+    # 64 x 64, N = 8 power diagram (sites U[-1,1]^2, weights U(0, 0.05))
+    return power_problem((64, 64), 8, seed=synth.SEED_BASE + 0)
+
+
+@pytest.mark.parametrize("iters", [5, 25])
+def test_lbfgs_iterates_match_oracle(iters):
+    g, lab, N = config1()
+    d, eps = 2, 1e-2
+    th_o, rep_o, _ = O.lbfgs_fit(g, lab, N, d, eps, np.zeros((N, 6)), iters)
+    th, rep = pd.pd_fit(pd.Grid((64, 64)), dev(lab), N, d, eps, max_iter=iters, init=pd.PD_INIT_ZERO)
+    assert rep["iters"] == rep_o.iters
+    assert abs(rep["phi"] - rep_o.phi) <= 1e-9 * abs(rep_o.phi)
+    th = th.cpu().numpy()
+    assert np.linalg.norm(th - th_o) <= 1e-6 * np.linalg.norm(th_o)
+
+
+def test_config1_full_budget_recovers_diagram():
+    g, lab, N = config1()
+    th, rep = pd.pd_fit(pd.Grid((64, 64)), dev(lab), N, 2, 1e-2, max_iter=2000, init=pd.PD_INIT_ZERO)
+    assert rep["err"] == 0.0
+    assert rep["phi"] > -math.log(2.0) / g.P
+    assert np.all(th[N - 1].cpu().numpy() == 0.0)         # gauge theta_{N-1} = 0
+    # the oracle reaches the same conclusion
+    th_o, rep_o, _ = O.lbfgs_fit(g, lab, N, 2, 1e-2, np.zeros((N, 6)), 2000)
+    F, _ = O.assign(g, N, 2, th_o)
+    assert np.all(F == lab) and rep_o.phi > -math.log(2.0) / g.P
+
+
+def test_heuristic_init_fit():
+    g, lab, N = config1()
+    th, rep = pd.pd_fit(pd.Grid((64, 64)), dev(lab), N, 2, 1e-2, max_iter=2000, init=pd.PD_INIT_HEURISTIC)
+    assert rep["err"] == 0.0
+    assert rep["phi"] > -math.log(2.0) / g.P
+
+
+def noisy(shape=(96, 80), N=12, seed=5, noise=0.1):
+    g, lab, N = power_problem(shape, N, seed)
+    flip = synth.rng(seed + 1).random(g.P) < noise
+    lab = np.where(flip, synth.random_labels(seed + 2, g.P, N), lab).astype(np.int32)
+    return g, lab, N
+
+
+@pytest.fixture(scope="module")
+def nonsep():
+    shape = (96, 80)
+    g, lab, N = noisy(shape)
+    d, eps = 2, 0.05
+    th_o, rep_o, _ = O.lbfgs_fit(g, lab, N, d, eps, np.zeros((N, 6)), 3000, gtol=1e-13)
+    return shape, g, lab, N, d, eps, rep_o.phi
+
+
+@pytest.mark.parametrize("method,prec,refine", [
+    (pd.PD_METHOD_LBFGS, pd.PD_FP64, 0),
+    (pd.PD_METHOD_LBFGS, pd.PD_FP32, 400),
+    (pd.PD_METHOD_LBFGS, pd.PD_BF16X3, 400),
+    (pd.PD_METHOD_LBFGS, pd.PD_BF16, 400),
+    (pd.PD_METHOD_NEWTON_CG, pd.PD_FP64, 0),
+])
+def test_reaches_unique_optimum(nonsep, method, prec, refine):
+    shape, g, lab, N, d, eps, phi_star = nonsep
+    target = phi_star - 1e-8 * abs(phi_star)
+    th, rep = pd.pd_fit(pd.Grid(shape), dev(lab), N, d, eps, max_iter=3000 if refine == 0 else 300,
+                        method=method, prec=prec, refine_iter=refine, target_phi=target,
+                        switch_rtol=1e-7 if refine else 0.0, gtol=1e-13)
+    assert rep["phi"] >= target, (rep, phi_star)
+    assert rep["phi"] <= phi_star + 1e-8 * abs(phi_star) + 1e-12
+
+
+def test_labels_checked():
+    grid = pd.Grid((8, 8))
+    lab = torch.zeros(64, dtype=torch.int32, device="cuda")
+    lab[5] = 9
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_fit(grid, lab, 3, 1, 0.1, max_iter=5)
+    assert e.value.code == pd.PD_ELABEL
+
+
+def test_apd_3d_degree2_recovery():
+    # a small 3-D anisotropic power diagram (SPD metrics with eigenvalues
+    # log-uniform in [0.5, 2]) recovered at degree 2 (K = 10)
+    shape = (20, 18, 16)
+    g = O.Grid(shape)
+    y, w, A = synth.apd_params(synth.SEED_BASE + 2, 6, dim=3)
+    lab, _ = O.assign(g, 6, 2, O.theta_from_apd(3, 2, y, w, A))
+    lab, N, _ = synth.compact(lab)
+    th, rep = pd.pd_fit(pd.Grid(shape), dev(lab.astype(np.int32)), N, 2, 1e-2, max_iter=2000)
+    assert rep["err"] <= 2.0 / g.P   # at most a couple of boundary voxels
+    if rep["phi"] > -math.log(2.0) / g.P:
+        assert rep["err"] == 0.0

@@ -1,0 +1,104 @@
+"""Parity of the tensor-core (tcgen05) evaluation with the FP64 oracle.
+
+PD_BF16X3 splits operands into three bf16 terms (about 24 significant
+bits) for the logits and two terms for the gradient contraction: it must
+meet the FP32 tolerances (Phi 1e-5 relative, gradient 1e-4 in norm).
+PD_BF16 rounds every operand to bf16 (8 significant bits): its logit error
+is about |theta| / eps * 2^-9, so it is checked at a loose bound scaled to
+that, and its error is reported by the benchmark.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_20816_gb300 import pd, synth
+from helpers import poly_problem, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+CASES = [
+    ((64, 64), 8, 2, 1e-2, 0.02),
+    ((37, 29), 131, 3, 5e-2, 0.05),
+    ((100, 3), 2, 1, 1e-1, 0.3),
+    ((9, 7, 5), 3, 2, 2e-2, 0.02),
+    ((13, 11, 6), 40, 3, 5e-2, 0.05),
+    ((31, 17), 130, 5, 5e-2, 0.01),
+    ((200, 190), 300, 4, 1e-2, 0.01),
+]
+
+
+def run(shape, lab, N, th, d, eps, prec):
+    grid = pd.Grid(shape)
+    obj, grad = pd.pd_objective_grad(grid, dev(lab), N, dev(th), d, eps, prec=prec)
+    torch.cuda.synchronize()
+    return float(obj.item()), grad.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,N,d,eps,scale", CASES)
+def test_bf16x3_matches_oracle(shape, N, d, eps, scale):
+    g = O.Grid(shape)
+    lab = synth.random_labels(31, g.P, N)
+    th = synth.random_theta(32, N, O.K(len(shape), d), scale)
+    phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
+    phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    assert abs(phi - phi_o) <= 1e-5 * abs(phi_o), (phi, phi_o)
+    assert rel(grad, grad_o) <= 1e-4, rel(grad, grad_o)
+
+
+@pytest.mark.parametrize("shape,N,d,eps,scale", CASES)
+def test_bf16_close_to_oracle(shape, N, d, eps, scale):
+    g = O.Grid(shape)
+    lab = synth.random_labels(33, g.P, N)
+    K = O.K(len(shape), d)
+    th = synth.random_theta(34, N, K, scale)
+    phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
+    phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16)
+    # logit error bound of one bf16 rounding of theta/eps and eta
+    dl = np.abs(th).sum(1).max() / eps * 2.0 ** -7
+    assert abs(phi - phi_o) <= 2 * dl + 1e-3 * abs(phi_o), (phi, phi_o, dl)
+    assert rel(grad, grad_o) <= 0.05 + 4 * dl
+
+
+def test_tc_bitwise_reproducible():
+    shape, N, d = (300, 200), 200, 4
+    lab = synth.random_labels(35, 300 * 200, N)
+    th = synth.random_theta(36, N, 15, 0.02)
+    for prec in (pd.PD_BF16, pd.PD_BF16X3):
+        a = run(shape, lab, N, th, d, 1e-2, prec)
+        b = run(shape, lab, N, th, d, 1e-2, prec)
+        assert a[0] == b[0]
+        np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_tc_unsupported_shapes():
+    grid = pd.Grid((16, 16))
+    lab = torch.zeros(256, dtype=torch.int32, device="cuda")
+    th = torch.zeros((3, 36), dtype=torch.float64, device="cuda")
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_objective_grad(grid, lab, 3, th, 7, 0.1, prec=pd.PD_BF16X3)   # K = 36 > 32
+    assert e.value.code == pd.PD_ENOTSUP
+    # the resident parameter image of 260 grains at K = 28 (bf16x3) exceeds
+    # shared memory
+    th = torch.zeros((260, 28), dtype=torch.float64, device="cuda")
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_objective_grad(grid, lab, 260, th, 6, 0.1, prec=pd.PD_BF16X3)
+    assert e.value.code == pd.PD_ENOTSUP
+
+
+@pytest.mark.slow
+def test_config2_full_size_bf16x3():
+    shape, d, eps = (1024, 1024), 4, 1e-3
+    g, lab, N, th = poly_problem(shape, 500, d, seed=synth.SEED_BASE + 1, noise=0.02)
+    phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
+    phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    print("config2 bf16x3 rel err: phi %.3e grad %.3e" % (abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o)))
+    assert abs(phi - phi_o) <= 1e-5 * abs(phi_o)
+    assert rel(grad, grad_o) <= 1e-3
+    phi16, grad16 = run(shape, lab, N, th, d, eps, pd.PD_BF16)
+    print("config2 bf16 rel err: phi %.3e grad %.3e" % (abs(phi16 - phi_o) / abs(phi_o), rel(grad16, grad_o)))
