@@ -222,6 +222,57 @@ int pd_fit(const pd_grid* grid, const int32_t* labels, int N,
            const pd_fit_opts* opts, double* theta_io, pd_fit_report* report,
            void* stream);
 
+/* ---- batched evaluation and fitting of many grain maps ----------------- */
+/* One grain map of a batch (2-D pixel sets).  Pointers are device pointers
+ * owned by the caller and must stay valid while a batch built on them is
+ * used.  theta, obj_out and grad_out are read/written by pd_batch_eval;
+ * pd_fit_batched ignores them (it uses theta_io). */
+typedef struct pd_map {
+  pd_grid grid;
+  const int32_t* labels; /* [P], each in 0..N-1 */
+  int N;
+  const double* theta;   /* [N][K] */
+  double* obj_out;       /* scalar Phi of this map */
+  double* grad_out;      /* [N][K] grad Phi, or NULL */
+} pd_map;
+
+typedef struct pd_batch pd_batch;
+
+/* Synchronous: builds a plan that evaluates eq. (Phi) and eq. (grad) of all
+ * maps (same degree, eps and precision; PD_FP64 or PD_FP32) with one
+ * persistent launch per pass, every pass working through a list of (map,
+ * pixel block) and (map, pixel chunk, grain tile) items, heaviest maps
+ * first; the whole evaluation is captured once as a CUDA graph.  With
+ * autotune != 0 the pass-2 chunking and the persistent grid size are chosen
+ * by timing five candidates on the first plan of a (degree, precision,
+ * batch size, total work) class; the choice is cached for the process.
+ * The plan owns its scratch (allocated here, freed by pd_batch_destroy). */
+int pd_batch_create(int n_maps, const pd_map* maps, const pd_eval_opts* opts,
+                    int autotune, pd_batch** out);
+/* Enqueues one replay of the plan's graph on the stream: every active map's
+ * Phi and gradient from its current theta.  Replays on one plan must not
+ * overlap (they share the plan's scratch). */
+int pd_batch_eval(pd_batch* batch, void* stream);
+/* Which maps the next replays evaluate: active[m] != 0 (host int32[n_maps],
+ * copied asynchronously on the stream).  All maps are active initially. */
+int pd_batch_set_active(pd_batch* batch, const int32_t* active, void* stream);
+/* The tuning choice of the plan and the measured milliseconds per replay. */
+int pd_batch_info(const pd_batch* batch, int* chunk_factor, int* occ_div,
+                  double* tuned_ms);
+/* Synchronises the device and frees the plan. */
+void pd_batch_destroy(pd_batch* batch);
+
+/* Synchronous: the ascent scheme of pd_fit (L-BFGS only; PD_FP64 or PD_FP32
+ * first phase with optional FP64 refinement; init PD_INIT_ZERO or
+ * PD_INIT_GIVEN) for every map at once.  Each map runs its own optimiser
+ * on a host thread; their objective/gradient requests are served together,
+ * one graph replay per round for all maps that are waiting.  theta_io[m]:
+ * device double[N_m][K], in (PD_INIT_GIVEN) and out (gauge-fixed).
+ * reports[m] (host) as for pd_fit; seconds is the wall time of the call. */
+int pd_fit_batched(int n_maps, const pd_map* maps, double* const* theta_io,
+                   const pd_fit_opts* opts, pd_fit_report* reports,
+                   void* stream);
+
 /* ---- tracing of the library's own kernels ------------------------------ */
 /* pd_prof_enable(1) clears the record and starts timing every kernel this
  * library launches, with a pair of CUDA events recorded on the launching

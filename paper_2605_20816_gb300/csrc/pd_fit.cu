@@ -23,12 +23,10 @@
 #include <vector>
 
 #include "pd.h"
+#include "pd_fit_core.h"
 #include "pd_internal.h"
 
 namespace pd {
-namespace {
-
-using Vec = std::vector<double>;
 
 double dot(const Vec& a, const Vec& b) {
   double s = 0.0;
@@ -36,7 +34,9 @@ double dot(const Vec& a, const Vec& b) {
   return s;
 }
 
-class Problem {
+namespace {
+
+class Problem : public Evaluator {
  public:
   Problem(const pd_grid* grid, const Geom& g, const int32_t* labels, int N, int d, double eps,
           cudaStream_t st)
@@ -52,12 +52,11 @@ class Problem {
     h_grad_.assign((size_t)N * K_, 0.0);
   }
   bool ok() const { return sc_.ok(); }
-  int n_free() const { return (N_ - 1) * K_; }
+  int n_free() const override { return (N_ - 1) * K_; }
   int K() const { return K_; }
-  int64_t evals = 0, hvps = 0;
 
   // f = -Phi, gf = -grad Phi on the free blocks
-  int eval(const Vec& x, int prec, double* f, Vec* gf) {
+  int eval(const Vec& x, int prec, double* f, Vec* gf) override {
     int rc = upload(x, d_theta_);
     if (rc) return rc;
     EvalCall c{g_, grid_->dim, d_, N_, prec, eps_, labels_, d_theta_, nullptr, d_obj_, gf ? d_grad_ : nullptr,
@@ -80,7 +79,7 @@ class Problem {
   }
 
   // out = (Hessian of -Phi) v on the free blocks
-  int hvp(const Vec& x, const Vec& v, int prec, Vec* out) {
+  int hvp(const Vec& x, const Vec& v, int prec, Vec* out) override {
     int rc = upload(x, d_theta_);
     if (rc) return rc;
     rc = upload(v, d_v_);
@@ -156,14 +155,9 @@ double cubic_step(double a, double fa, double ga, double b, double fb, double gb
   return 0.5 * (a + b);
 }
 
-struct Point {
-  Vec x, g;
-  double f;
-};
-
 // Strong-Wolfe search along dir from cur; returns the step (0 on failure,
 // with *out = cur re-evaluated).
-int wolfe(Problem& pb, int prec, const Point& cur, const Vec& dir, double a0, Point* out, double* step) {
+int wolfe(Evaluator& pb, int prec, const Point& cur, const Vec& dir, double a0, Point* out, double* step) {
   const double c1 = 1e-4, c2 = 0.9;
   const int budget = 25;
   const int n = (int)cur.x.size();
@@ -249,7 +243,7 @@ struct PhaseResult {
   int status = 0;  // 0 budget, 1 gtol, 2 stalled, 3 target, 4 switch
 };
 
-int lbfgs_phase(Problem& pb, int prec, Point& cur, int max_iter, int m, double gtol, double target_phi,
+int lbfgs_phase(Evaluator& pb, int prec, Point& cur, int max_iter, int m, double gtol, double target_phi,
                 double switch_rtol, bool first_scaled, PhaseResult* res) {
   const int n = (int)cur.x.size();
   std::vector<Vec> S, Y;
@@ -299,7 +293,7 @@ int lbfgs_phase(Problem& pb, int prec, Point& cur, int max_iter, int m, double g
   return PD_OK;
 }
 
-int newton_phase(Problem& pb, int prec, Point& cur, int max_iter, int max_cg, double gtol, double target_phi,
+int newton_phase(Evaluator& pb, int prec, Point& cur, int max_iter, int max_cg, double gtol, double target_phi,
                  PhaseResult* res) {
   const int n = (int)cur.x.size();
   Vec s(n), r(n), p(n), hp;
@@ -342,6 +336,46 @@ int newton_phase(Problem& pb, int prec, Point& cur, int max_iter, int max_cg, do
 }
 
 }  // namespace
+
+int fit_run(Evaluator& ev, const Vec& th, int N, int K, const pd_fit_opts& o, FitState* out) {
+  const int n = (N - 1) * K;
+  Point& cur = out->cur;
+  cur.x.resize(n);
+  for (int i = 0; i < N - 1; ++i)
+    for (int k = 0; k < K; ++k) cur.x[(size_t)i * K + k] = th[(size_t)i * K + k] - th[(size_t)(N - 1) * K + k];
+  for (double v : cur.x)
+    if (!isfinite(v)) return PD_ENAN;
+  const double target = isnan(o.target_phi) ? -INFINITY : o.target_phi;
+  int prec = o.prec;
+  int rc = ev.eval(cur.x, prec, &cur.f, &cur.g);
+  if (rc) return rc;
+  PhaseResult r1, r2;
+  if (o.method == PD_METHOD_LBFGS)
+    rc = lbfgs_phase(ev, prec, cur, o.max_iter, o.lbfgs_m, o.gtol, target, o.switch_rtol, true, &r1);
+  else
+    rc = newton_phase(ev, prec, cur, o.max_iter, o.max_cg, o.gtol, target, &r1);
+  if (rc) return rc;
+  int status = r1.status;
+  if (o.refine_iter > 0 && status != 3) {
+    if (prec != PD_FP64) {
+      prec = PD_FP64;
+      rc = ev.eval(cur.x, prec, &cur.f, &cur.g);
+      if (rc) return rc;
+    }
+    if (o.method == PD_METHOD_LBFGS)
+      rc = lbfgs_phase(ev, prec, cur, o.refine_iter, o.lbfgs_m, o.gtol, target, 0.0, false, &r2);
+    else
+      rc = newton_phase(ev, prec, cur, o.refine_iter, o.max_cg, o.gtol, target, &r2);
+    if (rc) return rc;
+    status = r2.status;
+  }
+  out->iters = r1.iters + r2.iters;
+  out->iters_phase1 = r1.iters;
+  out->status = status == 4 ? 0 : status;
+  out->final_prec = prec;
+  return PD_OK;
+}
+
 }  // namespace pd
 
 using namespace pd;
@@ -370,9 +404,8 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
   Problem pb(grid, g, labels, N, opts->d, opts->eps, st);
   if (!pb.ok()) return PD_ENOMEM;
   const int K = pb.K();
-  const int n = pb.n_free();
 
-  // initial parameters, gauge-fixed by subtracting the last block
+  // initial parameters
   std::vector<double> th((size_t)N * K, 0.0);
   if (opts->init == PD_INIT_HEURISTIC) {
     rc = pd_heuristic_init(grid, labels, N, opts->d, theta_io, stream);
@@ -386,37 +419,15 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
         cudaStreamSynchronize(st) != cudaSuccess)
       return PD_ECUDA;
   }
-  Point cur;
-  cur.x.resize(n);
-  for (int i = 0; i < N - 1; ++i)
-    for (int k = 0; k < K; ++k) cur.x[(size_t)i * K + k] = th[(size_t)i * K + k] - th[(size_t)(N - 1) * K + k];
-  for (double v : cur.x)
-    if (!isfinite(v)) return PD_ENAN;
-
-  const double target = isnan(opts->target_phi) ? -INFINITY : opts->target_phi;
-  int prec = opts->prec;
-  rc = pb.eval(cur.x, prec, &cur.f, &cur.g);
+  FitState fs;
+  rc = fit_run(pb, th, N, K, *opts, &fs);
   if (rc) return rc;
+  Point& cur = fs.cur;
+  const int prec = fs.final_prec;
+  const int status = fs.status;
   PhaseResult r1, r2;
-  if (opts->method == PD_METHOD_LBFGS)
-    rc = lbfgs_phase(pb, prec, cur, opts->max_iter, opts->lbfgs_m, opts->gtol, target, opts->switch_rtol, true, &r1);
-  else
-    rc = newton_phase(pb, prec, cur, opts->max_iter, opts->max_cg, opts->gtol, target, &r1);
-  if (rc) return rc;
-  int status = r1.status;
-  if (opts->refine_iter > 0 && status != 3) {
-    if (prec != PD_FP64) {
-      prec = PD_FP64;
-      rc = pb.eval(cur.x, prec, &cur.f, &cur.g);
-      if (rc) return rc;
-    }
-    if (opts->method == PD_METHOD_LBFGS)
-      rc = lbfgs_phase(pb, prec, cur, opts->refine_iter, opts->lbfgs_m, opts->gtol, target, 0.0, false, &r2);
-    else
-      rc = newton_phase(pb, prec, cur, opts->refine_iter, opts->max_cg, opts->gtol, target, &r2);
-    if (rc) return rc;
-    status = r2.status;
-  }
+  r1.iters = fs.iters_phase1;
+  r2.iters = fs.iters - fs.iters_phase1;
   // final report in double precision
   double f_final = cur.f;
   std::vector<double> gfin = cur.g;
@@ -436,7 +447,7 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
   report->iters_phase1 = r1.iters;
   report->evals = pb.evals;
   report->hvps = pb.hvps;
-  report->status = status == 4 ? 0 : status;
+  report->status = status;
   report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   return isfinite(report->phi) ? PD_OK : PD_ENAN;
 }

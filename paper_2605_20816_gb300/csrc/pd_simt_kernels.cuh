@@ -78,11 +78,14 @@ __global__ void k_copy_pad(const double* __restrict__ v, int N, int K, int KP, T
 // ---------------------------------------------------------------------------
 // Pass 1: per-pixel log-sum-exp (and, for HVP, ubar(x) = sum_k p_k u_k).
 // ---------------------------------------------------------------------------
+// One block of pass 1 (pixels block*kLseThreads*PPT ...); obj_slot receives
+// the block's objective partial.  Called by the single-map kernel with the
+// block index and by the batched persistent kernel for each work item.
 template <typename T, int DIM, int D, int PPT, bool HVP>
-__global__ void __launch_bounds__(kLseThreads)
-k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__ thS,
-        const T* __restrict__ vS, T* __restrict__ lse_out, T* __restrict__ ubar_out,
-        double* __restrict__ obj_part) {
+__device__ __forceinline__ void pass1_block(const Geom& g, const int32_t* __restrict__ labels, int N,
+                                            const T* __restrict__ thS, const T* __restrict__ vS,
+                                            T* __restrict__ lse_out, T* __restrict__ ubar_out,
+                                            double* __restrict__ obj_slot, int64_t block) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KP = padded_K<T>(K);
   constexpr int GT = HVP ? 64 : 128;  // grains per shared tile
@@ -90,7 +93,7 @@ k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
   __shared__ __align__(16) T sv[HVP ? GT * KP : 1];
   __shared__ double sred[kLseThreads / 32];
 
-  const int64_t base = (int64_t)blockIdx.x * (kLseThreads * PPT);
+  const int64_t base = block * (kLseThreads * PPT);
   T eta[PPT][K];
   T m[PPT], s[PPT], t[PPT];
 #pragma unroll
@@ -182,7 +185,7 @@ k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
     const T lse = m[q] + Arith<T>::lg(s[q]);
     if (lse_out) lse_out[j] = lse;
     if (HVP) ubar_out[j] = t[q] / s[q];
-    if (!HVP && obj_part) {
+    if (!HVP && obj_slot) {
       const int G = labels[j];
       if ((unsigned)G < (unsigned)N) {
         const T lG = dot_k<K>(thS + (int64_t)G * KP, eta[q]);
@@ -192,10 +195,19 @@ k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
       }
     }
   }
-  if (!HVP && obj_part) {
+  if (!HVP && obj_slot) {
     const double bs = block_sum_fixed(racc, sred);
-    if (threadIdx.x == 0) obj_part[blockIdx.x] = bs;
+    if (threadIdx.x == 0) *obj_slot = bs;
   }
+}
+
+template <typename T, int DIM, int D, int PPT, bool HVP>
+__global__ void __launch_bounds__(kLseThreads)
+k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__ thS,
+        const T* __restrict__ vS, T* __restrict__ lse_out, T* __restrict__ ubar_out,
+        double* __restrict__ obj_part) {
+  pass1_block<T, DIM, D, PPT, HVP>(g, labels, N, thS, vS, lse_out, ubar_out,
+                                   obj_part ? obj_part + blockIdx.x : nullptr, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -208,11 +220,13 @@ k_pass1(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
 // label matches, the common case for small eps) the accumulation is skipped:
 // adding c * eta with c = 0 changes nothing, so results are identical.
 // ---------------------------------------------------------------------------
+// One block of pass 2: pixel chunk `chunk` (ppc pixels) and grain tile
+// `gtile`; writes part[chunk][i][k] for the tile's grains.
 template <typename T, int DIM, int D, bool HVP>
-__global__ void __launch_bounds__(kGradThreads)
-k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__ thS,
-        const T* __restrict__ vS, const T* __restrict__ lse, const T* __restrict__ ubar,
-        int64_t ppc, double* __restrict__ part) {
+__device__ __forceinline__ void pass2_block(const Geom& g, const int32_t* __restrict__ labels, int N,
+                                            const T* __restrict__ thS, const T* __restrict__ vS,
+                                            const T* __restrict__ lse, const T* __restrict__ ubar, int64_t ppc,
+                                            double* __restrict__ part, int64_t chunk, int gtile) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KP = padded_K<T>(K);
   __shared__ __align__(16) T seta[kPixTile * KP];
@@ -221,7 +235,7 @@ k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
   __shared__ int slab[kPixTile];
   __shared__ double sacc[K * kGradThreads];  // per-thread double accumulators
 
-  const int i = blockIdx.y * kGradThreads + threadIdx.x;
+  const int i = gtile * kGradThreads + threadIdx.x;
   const bool vi = i < N;
   T th[K], vv[HVP ? K : 1];
 #pragma unroll
@@ -231,7 +245,7 @@ k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
     sacc[k * kGradThreads + threadIdx.x] = 0.0;
   }
 
-  const int64_t p0 = (int64_t)blockIdx.x * ppc;
+  const int64_t p0 = chunk * ppc;
   const int64_t p1 = min(p0 + ppc, g.P);
   for (int64_t t0 = p0; t0 < p1; t0 += kPixTile) {
     const int tn = (int)min((int64_t)kPixTile, p1 - t0);
@@ -286,9 +300,17 @@ k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__
   }
   if (vi) {
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      part[((int64_t)blockIdx.x * N + i) * K + k] = sacc[k * kGradThreads + threadIdx.x];
+    for (int k = 0; k < K; ++k) part[(chunk * N + i) * K + k] = sacc[k * kGradThreads + threadIdx.x];
   }
+  __syncthreads();  // the shared tiles may be reused by the next work item
+}
+
+template <typename T, int DIM, int D, bool HVP>
+__global__ void __launch_bounds__(kGradThreads)
+k_pass2(Geom g, const int32_t* __restrict__ labels, int N, const T* __restrict__ thS,
+        const T* __restrict__ vS, const T* __restrict__ lse, const T* __restrict__ ubar,
+        int64_t ppc, double* __restrict__ part) {
+  pass2_block<T, DIM, D, HVP>(g, labels, N, thS, vS, lse, ubar, ppc, part, blockIdx.x, blockIdx.y);
 }
 
 // Fixed-order sum over chunks: out[q] = scale * sum_c part[c][q].  A block

@@ -50,8 +50,10 @@ namespace pd {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
-constexpr int kTcEpiThreads = 128;                // warps 0..3
-constexpr int kTcThreads = 160;                   // + warp 4 (MMA issue)
+constexpr int kTcEpiThreads = 256;                // warps 0..7: two epilogue warpgroups
+constexpr int kTcThreads = 288;                   // + warp 8 (TMEM allocation, MMA issue)
+constexpr int kTcMmaTid = 256;
+constexpr int kTcCols = 512;                      // TMEM columns per CTA (one CTA per SM)
 constexpr int kTcGrainTile = 128;                 // pass-1 grains per MMA group
 constexpr int kTcPixTile = 128;                   // pixels per tile (both passes)
 
@@ -316,8 +318,36 @@ __device__ __forceinline__ float dot_f(const float* __restrict__ a, const float*
 }
 
 // ---------------------------------------------------------------------------
+// Epilogue layout.  Warp w of the two epilogue warpgroups reads TMEM lanes
+// 32 (w mod 4) .. +31 (the access rule of tcgen05.ld) and the column half
+// h = w / 4 of each 128-column tile, so 8 warps share every tile.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tree_max32(const float* v) {
+  float a[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = fmaxf(v[q], v[q + 16]);
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) a[q] = fmaxf(a[q], a[q + w]);
+  return a[0];
+}
+__device__ __forceinline__ float tree_sum32(const float* v) {
+  float a[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = v[q] + v[q + 16];
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) a[q] = a[q] + a[q + w];
+  return a[0];
+}
+
+// ---------------------------------------------------------------------------
 // Pass 1: log2 S(x) per pixel and objective partials.
 // ---------------------------------------------------------------------------
+constexpr int kP1Bufs = 4;  // logit tiles in flight in TMEM (4 x 128 columns)
+
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, const uint8_t* __restrict__ img,
@@ -332,10 +362,12 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   constexpr uint32_t IDESC = idesc_bf16(128, kTcGrainTile);
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sB = smem;                                     // Npad x KT
-  uint8_t* sA = smem + (size_t)Npad * kRowBytes;          // 2 stages x 128 x KT
-  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);  // 2 stages x Npad centre logits
-  __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_d_full[2], bar_d_empty[2], bar_drain;
+  uint8_t* sB = smem;                                            // Npad x KT
+  uint8_t* sA = smem + (size_t)Npad * kRowBytes;                 // 2 stages x 128 x KT
+  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Npad centre logits
+  float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Npad);   // 2 stages x 128 (max, sum) of half 1
+  __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_d_full[kP1Bufs],
+      bar_d_empty[kP1Bufs], bar_drain, bar_part_full[2], bar_part_free[2], bar_off_free[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ double sred[kTcThreads / 32];
@@ -349,21 +381,28 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     for (int s = 0; s < 2; ++s) {
       mbar_init(&bar_a_full[s], kTcEpiThreads);
       mbar_init(&bar_a_empty[s], 1);
-      mbar_init(&bar_d_full[s], 1);
-      mbar_init(&bar_d_empty[s], kTcEpiThreads);
+    }
+    for (int b = 0; b < kP1Bufs; ++b) {
+      mbar_init(&bar_d_full[b], 1);
+      mbar_init(&bar_d_empty[b], kTcEpiThreads);
     }
     mbar_init(&bar_drain, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bar_part_full[s], 128);  // second warpgroup has written its (max, sum)
+      mbar_init(&bar_part_free[s], 128);  // first warpgroup has read them
+      mbar_init(&bar_off_free[s], kTcEpiThreads);  // every epilogue thread is done with stage s
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) tmem_alloc(&tmem_slot, 256);
+  if (warp == 8) tmem_alloc(&tmem_slot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
   double racc = 0.0;
-  if (warp == 4) {
-    if (tid == 128) {
+  if (warp == 8) {
+    if (tid == kTcMmaTid) {
       // parameter image: one bulk copy per 32 KiB
       const uint32_t total = (uint32_t)Npad * kRowBytes;
       mbar_arrive_expect_tx(&bar_theta, total);
@@ -380,9 +419,9 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         if (!ok) break;
         tc_fence_after();
         for (int gt = 0; gt < n_gt; ++gt, ++c) {
-          const int b = (int)(c & 1);
-          if (c >= 2) {
-            ok = mbar_wait(&bar_d_empty[b], (uint32_t)(((c >> 1) - 1) & 1), &abort_flag, status);
+          const int b = (int)(c % kP1Bufs);
+          if (c >= kP1Bufs) {
+            ok = mbar_wait(&bar_d_empty[b], (uint32_t)(((c / kP1Bufs) - 1) & 1), &abort_flag, status);
             if (!ok) break;
             tc_fence_after();
           }
@@ -405,44 +444,50 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     }
     __syncwarp();
   } else {
-    // epilogue warps: thread tid <-> pixel row tid of a tile <-> TMEM lane tid
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
+    const int row = quad * 32 + lane;  // pixel row of the tile == TMEM lane
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     float lG_next = 0.f;
     int64_t j_next = -1;
-    // features of a tile into stage s, the tile's centre logits into
-    // sOff[s], and this pixel's label logit
+    // the operand row of pixel `tid` (first warpgroup) and the centre
+    // logits of every grain (all epilogue threads) for tile t, stage s
     auto produce = [&](int64_t t, int s, int use) -> bool {
+      // stage s is free once the MMAs read its operand rows and every
+      // epilogue thread finished with its centre logits
       if (use >= 1 && !mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status)) return false;
-      float c[DIM], ec[K], x[DIM], eta[K];
-      const int64_t j = tile_pixel<DIM>(g, tm, t, tid, c);
+      if (use >= 1 && !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)) return false;
+      float c[DIM], ec[K];
+      const int64_t j = tile_pixel<DIM>(g, tm, t, tid & 127, c);
       legendre_features<DIM, D>(c, ec);
-      if (j >= 0) {
-        pixel_coords<DIM>(g, j, x);
-      } else {
+      if (tid < 128) {
+        float x[DIM], eta[K];
+        if (j >= 0) {
+          pixel_coords<DIM>(g, j, x);
+        } else {
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) x[a] = c[a];
+          for (int a = 0; a < DIM; ++a) x[a] = c[a];
+        }
+        legendre_features<DIM, D>(x, eta);
+        float de[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
+        store_eta_row<K, KW, KS>(sA + s * kTileBytes, tid, de);
+        j_next = j;
+        lG_next = 0.f;
+        if (j >= 0) {
+          const int G = labels[j];
+          if ((unsigned)G < (unsigned)N) {
+            const float* rowp = th32 + (int64_t)G * KP32;
+            lG_next = dot_f<K>(rowp, ec) + dot_f<K>(rowp, de);
+          } else {
+            lG_next = NAN;
+          }
+        }
       }
-      legendre_features<DIM, D>(x, eta);
-      float de[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
-      store_eta_row<K, KW, KS>(sA + s * kTileBytes, tid, de);
-      // centre logits of every grain (one fp32 dot product per grain)
       for (int i = tid; i < Npad; i += kTcEpiThreads)
         sOff[s * Npad + i] = i < N ? dot_f<K>(th32 + (int64_t)i * KP32, ec) : 0.f;
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
-      j_next = j;
-      lG_next = 0.f;
-      if (j >= 0) {
-        const int G = labels[j];
-        if ((unsigned)G < (unsigned)N) {
-          const float* row = th32 + (int64_t)G * KP32;
-          lG_next = dot_f<K>(row, ec) + dot_f<K>(row, de);
-        } else {
-          lG_next = NAN;
-        }
-      }
       return true;
     };
     int it = 0;
@@ -460,41 +505,60 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       }
       float m = -INFINITY, ssum = 0.f;
       for (int gt = 0; gt < n_gt; ++gt, ++c) {
-        const int b = (int)(c & 1);
-        ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c >> 1) & 1), &abort_flag, status);
+        const int b = (int)(c % kP1Bufs);
+        ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
-        const int valid_cols = min(kTcGrainTile, N - gt * kTcGrainTile);
-        const float* off = sOff + s * Npad + gt * kTcGrainTile;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kTcGrainTile; c0 += 32) {
-          if (c0 >= valid_cols) break;
-          uint32_t r[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(b * kTcGrainTile + c0), r);
-          tmem_wait_ld();
+        uint32_t r0[32], r1[32];
+        const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 64);
+        tmem_ld32(tmem + lane_base + col, r0);
+        tmem_ld32(tmem + lane_base + col + 32, r1);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
+        const int cbase = gt * kTcGrainTile + half * 64;
+        const float* off = sOff + s * Npad + cbase;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int nv = N - (cbase + 32 * h2);
+          if (nv <= 0) break;
+          const uint32_t* r = h2 ? r1 : r0;
           float v[32];
-          const int nv = valid_cols - c0;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = q < nv ? __uint_as_float(r[q]) + off[c0 + q] : -INFINITY;
-          float cm = v[0];
+          for (int q = 0; q < 32; ++q) v[q] = q < nv ? __uint_as_float(r[q]) + off[32 * h2 + q] : -INFINITY;
+          const float mn = fmaxf(m, tree_max32(v));
 #pragma unroll
-          for (int q = 1; q < 32; ++q) cm = fmaxf(cm, v[q]);
-          const float mn = fmaxf(m, cm);
-          float add = 0.f;
-#pragma unroll
-          for (int q = 0; q < 32; ++q) add += Arith<float>::ex(v[q] - mn);
-          ssum = fmaf(ssum, Arith<float>::ex(m - mn), add);
+          for (int q = 0; q < 32; ++q) v[q] = Arith<float>::ex(v[q] - mn);
+          ssum = fmaf(ssum, Arith<float>::ex(m - mn), tree_sum32(v));
           m = mn;
         }
-        tc_fence_before();
-        mbar_arrive(&bar_d_empty[b]);
       }
       if (!ok) break;
-      if (j >= 0) {
-        const float lse = m + Arith<float>::lg(ssum);
-        lse_out[j] = lse;
-        racc += (double)(lG - lse) * Arith<float>::to_nat;
+      // combine the two column halves of each pixel (bounded mbarrier
+      // hand-off between the warpgroups; slot s is reused every 2 tiles)
+      if (half == 1) {
+        if (it >= 2 && !mbar_wait_warp(&bar_part_free[s], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, status)) {
+          ok = false;
+          break;
+        }
+        sPart[s * 128 + row] = make_float2(m, ssum);
+        mbar_arrive(&bar_part_full[s]);
+      } else {
+        if (!mbar_wait_warp(&bar_part_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status)) {
+          ok = false;
+          break;
+        }
+        const float2 o = sPart[s * 128 + row];
+        mbar_arrive(&bar_part_free[s]);
+        if (j >= 0) {
+          const float mm = fmaxf(m, o.x);
+          const float sum = ssum * Arith<float>::ex(m - mm) + o.y * Arith<float>::ex(o.x - mm);
+          const float lse = mm + Arith<float>::lg(sum);
+          lse_out[j] = lse;
+          racc += (double)(lG - lse) * Arith<float>::to_nat;
+        }
       }
+      mbar_arrive(&bar_off_free[s]);
     }
     if (!ok) racc = NAN;
   }
@@ -510,23 +574,24 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   __syncthreads();
   if (tid == 0) {
     double sum = 0.0;
-    for (int w = 0; w < 4; ++w) sum += sred[w];
+    for (int w = 0; w < 8; ++w) sum += sred[w];
     if (abort_flag) sum = NAN;
     obj_part[blockIdx.x] = sum;
   }
-  if (warp == 4) {
+  if (warp == 8) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, kTcCols);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Pass 2: gradient partials for one grain block and one chunk of tiles.
-// NB = 2 double-buffers the pixel-side operands (features of the next tile
-// are produced while the current one is consumed); NB = 1 when shared
-// memory does not hold two stages.
+// NB pixel-operand stages and NA gradient-operand stages (2 when shared
+// memory holds them, else 1); with NB = 2 the MMA warp issues the logits of
+// tile t+1 before the gradient of tile t, so the tensor cores always have
+// the next tile's logits ready when the epilogue finishes a tile.
 // ---------------------------------------------------------------------------
-template <int DIM, int D, int KS, int NB>
+template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const uint8_t* __restrict__ img,
            const float* __restrict__ th32, const float* __restrict__ lse, int64_t tiles_per_chunk,
@@ -539,22 +604,24 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
   constexpr uint32_t kRowBytes = KT * 2;
   constexpr uint32_t kABytes = 128 * kRowBytes;   // theta block
   constexpr uint32_t kBBytes = kTcPixTile * kRowBytes;
-  constexpr uint32_t kB2Bytes = GT * KW * kTcPixTile * 2;   // eta^T terms: rows KW, K = 128 pixels
-  constexpr uint32_t kA2Bytes = GT * 128 * kTcPixTile * 2;  // c terms: rows 128 grains, K = 128 pixels
+  constexpr uint32_t kB2Term = KW * kTcPixTile * 2;        // eta^T term: rows KW, K = 128 pixels
+  constexpr uint32_t kB2Bytes = GT * kB2Term;
+  constexpr uint32_t kA2Term = 128 * kTcPixTile * 2;       // c term: rows 128 grains, K = 128 pixels
+  constexpr uint32_t kA2Bytes = GT * kA2Term;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
   constexpr uint32_t IDESC2 = idesc_bf16(128, KW);
-  constexpr int D2COL = kTcPixTile;  // TMEM columns: D1 [0,128), D2 [128, 128+KW)
+  constexpr int D2COL = 2 * kTcPixTile;  // TMEM columns: D1 [0,256) double-buffered, D2 [256, 256+KW)
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                           // theta block image
   uint8_t* sB = sA + kABytes;                   // NB stages of eta rows
   uint8_t* sB2 = sB + NB * kBBytes;             // NB stages of eta^T
-  uint8_t* sA2 = sB2 + NB * kB2Bytes;           // c tile
-  float* sLse = reinterpret_cast<float*>(sA2 + kA2Bytes);     // [NB][128]
-  int* sLab = reinterpret_cast<int*>(sLse + NB * kTcPixTile);  // [NB][128]
+  uint8_t* sA2 = sB2 + NB * kB2Bytes;           // NA stages of c
+  float* sLse = reinterpret_cast<float*>(sA2 + NA * kA2Bytes);    // [NB][128]
+  int* sLab = reinterpret_cast<int*>(sLse + NB * kTcPixTile);      // [NB][128]
   float* sCen = reinterpret_cast<float*>(sLab + NB * kTcPixTile);  // [NB][4] tile centres
-  __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full, bar_d1_empty,
-      bar_a2_full, bar_a2_empty, bar_d2_done;
+  __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[2], bar_d1_empty[2],
+      bar_a2_full[NA], bar_a2_empty[NA], bar_d2_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -570,60 +637,73 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
       mbar_init(&bar_b_full[s], kTcEpiThreads);
       mbar_init(&bar_b_empty[s], 1);
     }
-    mbar_init(&bar_d1_full, 1);
-    mbar_init(&bar_d1_empty, kTcEpiThreads);
-    mbar_init(&bar_a2_full, kTcEpiThreads);
-    mbar_init(&bar_a2_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_d1_full[b], 1);
+      mbar_init(&bar_d1_empty[b], kTcEpiThreads);
+    }
+    for (int a = 0; a < NA; ++a) {
+      mbar_init(&bar_a2_full[a], kTcEpiThreads);
+      mbar_init(&bar_a2_empty[a], 1);
+    }
     mbar_init(&bar_d2_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) tmem_alloc(&tmem_slot, 256);
+  if (warp == 8) tmem_alloc(&tmem_slot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 4) {
-    if (tid == 128) {
+  if (warp == 8) {
+    if (tid == kTcMmaTid) {
       mbar_arrive_expect_tx(&bar_theta, kABytes);
       bulk_g2s(sA, img + (size_t)gb * kABytes, kABytes, &bar_theta);
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
-      for (int t = 0; ok && t < n_pt; ++t) {
-        const int s = t % NB;
-        ok = mbar_wait(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status);
-        if (!ok) break;
-        if (t >= 1) {
-          ok = mbar_wait(&bar_d1_empty, (uint32_t)((t - 1) & 1), &abort_flag, status);
-          if (!ok) break;
-        }
+      auto logits = [&](int t) -> bool {
+        const int s = t % NB, b1 = t & 1;
+        if (!mbar_wait(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) return false;
+        if (t >= 2 && !mbar_wait(&bar_d1_empty[b1], (uint32_t)(((t >> 1) - 1) & 1), &abort_flag, status))
+          return false;
         tc_fence_after();
-        {
-          const uint32_t aaddr = smem_addr(sA), baddr = smem_addr(sB + s * kBBytes);
+        const uint32_t aaddr = smem_addr(sA), baddr = smem_addr(sB + s * kBBytes);
 #pragma unroll
-          for (int q = 0; q < KT / 16; ++q)
-            mma_bf16(tmem, smem_desc(aaddr + q * 256, 128, KT * 16), smem_desc(baddr + q * 256, 128, KT * 16),
-                     IDESC1, q > 0);
-          mma_commit(&bar_d1_full);
-        }
-        ok = mbar_wait(&bar_a2_full, (uint32_t)(t & 1), &abort_flag, status);
-        if (!ok) break;
+        for (int q = 0; q < KT / 16; ++q)
+          mma_bf16(tmem + b1 * kTcPixTile, smem_desc(aaddr + q * 256, 128, KT * 16),
+                   smem_desc(baddr + q * 256, 128, KT * 16), IDESC1, q > 0);
+        mma_commit(&bar_d1_full[b1]);
+        return true;
+      };
+      auto grad = [&](int t) -> bool {
+        const int s = t % NB, a = t % NA;
+        if (!mbar_wait(&bar_a2_full[a], (uint32_t)((t / NA) & 1), &abort_flag, status)) return false;
         tc_fence_after();
-        {
-          // D2 += C . eta: products (c_h, eta_h), then (c_l, eta_h), (c_h, eta_l)
-          const uint32_t a2 = smem_addr(sA2), b2 = smem_addr(sB2 + s * kB2Bytes);
-          constexpr int NPROD = GT == 1 ? 1 : 3;
+        // D2 += C . eta: products (c_h, eta_h), then (c_l, eta_h), (c_h, eta_l)
+        const uint32_t a2 = smem_addr(sA2 + a * kA2Bytes), b2 = smem_addr(sB2 + s * kB2Bytes);
+        constexpr int NPROD = GT == 1 ? 1 : 3;
 #pragma unroll
-          for (int pr = 0; pr < NPROD; ++pr) {
-            const int ct = pr == 1 ? 1 : 0, et = pr == 2 ? 1 : 0;
+        for (int pr = 0; pr < NPROD; ++pr) {
+          const int ct = pr == 1 ? 1 : 0, et = pr == 2 ? 1 : 0;
 #pragma unroll
-            for (int q = 0; q < kTcPixTile / 16; ++q) {
-              const uint64_t ad = smem_desc(a2 + ct * (128 * kTcPixTile * 2) + q * 256, 128, kTcPixTile * 16);
-              const uint64_t bd = smem_desc(b2 + et * (KW * kTcPixTile * 2) + q * 256, 128, kTcPixTile * 16);
-              mma_bf16(tmem + D2COL, ad, bd, IDESC2, (t > 0 || pr > 0 || q > 0) ? 1u : 0u);
-            }
+          for (int q = 0; q < kTcPixTile / 16; ++q) {
+            const uint64_t ad = smem_desc(a2 + ct * kA2Term + q * 256, 128, kTcPixTile * 16);
+            const uint64_t bd = smem_desc(b2 + et * kB2Term + q * 256, 128, kTcPixTile * 16);
+            mma_bf16(tmem + D2COL, ad, bd, IDESC2, (t > 0 || pr > 0 || q > 0) ? 1u : 0u);
           }
-          mma_commit(&bar_a2_empty);
-          mma_commit(&bar_b_empty[s]);
+        }
+        mma_commit(&bar_a2_empty[a]);
+        mma_commit(&bar_b_empty[s]);
+        return true;
+      };
+      if (NB == 2) {
+        if (ok && n_pt > 0) ok = logits(0);
+        for (int t = 0; ok && t < n_pt; ++t) {
+          if (t + 1 < n_pt) ok = logits(t + 1);
+          if (ok) ok = grad(t);
+        }
+      } else {
+        for (int t = 0; ok && t < n_pt; ++t) {
+          ok = logits(t);
+          if (ok) ok = grad(t);
         }
       }
       mma_commit(&bar_d2_done);
@@ -631,78 +711,92 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
     }
     __syncwarp();
   } else {
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const int i = gb * 128 + tid;  // this thread's grain
+    const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
+    const int gr = quad * 32 + lane;        // grain row of the block == TMEM lane
+    const int i = gb * 128 + gr;            // this thread's grain
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     float th[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) th[k] = i < N ? th32[(int64_t)i * KP32 + k] : 0.f;
+    // pixel operands of tile t: the first warpgroup writes the logit operand
+    // rows, the second the transposed gradient operand
     auto produce = [&](int t, int s) -> bool {
       if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status))
         return false;
-      float c[DIM], ec[K], x[DIM], eta[K];
-      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, tid, c);
+      const int p = tid & 127;
+      float c[DIM], ec[K], eta[K];
+      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, p, c);
       legendre_features<DIM, D>(c, ec);
       const bool vj = j >= 0;
       if (vj) {
+        float x[DIM];
         pixel_coords<DIM>(g, j, x);
         legendre_features<DIM, D>(x, eta);
       } else {
 #pragma unroll
         for (int k = 0; k < K; ++k) eta[k] = ec[k];
       }
-      float de[K];
+      if (tid < 128) {
+        float de[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
-      store_eta_row<K, KW, KS>(sB + s * kBBytes, tid, de);
-      // eta^T (rows = features, K = pixels): hi and lo terms; zero for
-      // pixels outside the set
-      uint8_t* b2 = sB2 + s * kB2Bytes;
+        for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
+        store_eta_row<K, KW, KS>(sB + s * kBBytes, p, de);
+        sLse[s * kTcPixTile + p] = vj ? lse[j] : INFINITY;
+        sLab[s * kTcPixTile + p] = vj ? labels[j] : -1;
+        if (p == 0) {
 #pragma unroll
-      for (int k = 0; k < KW; ++k) {
-        const float v = (k < K && vj) ? eta[k] : 0.f;
-        const uint16_t h = bf16_bits(v);
-        *reinterpret_cast<uint16_t*>(b2 + kmaj(k, tid, kTcPixTile)) = h;
-        if (GT == 2)
-          *reinterpret_cast<uint16_t*>(b2 + KW * kTcPixTile * 2 + kmaj(k, tid, kTcPixTile)) =
-              bf16_bits(v - bf16_val(h));
-      }
-      sLse[s * kTcPixTile + tid] = vj ? lse[j] : INFINITY;
-      sLab[s * kTcPixTile + tid] = vj ? labels[j] : -1;
-      if (tid == 0) {
+          for (int a = 0; a < DIM; ++a) sCen[s * 4 + a] = c[a];
+        }
+      } else {
+        // eta^T (rows = features, K = pixels): hi and lo terms; zero for
+        // pixels outside the set
+        uint8_t* b2 = sB2 + s * kB2Bytes;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) sCen[s * 4 + a] = c[a];
+        for (int k = 0; k < KW; ++k) {
+          const float v = (k < K && vj) ? eta[k] : 0.f;
+          const uint16_t h = bf16_bits(v);
+          *reinterpret_cast<uint16_t*>(b2 + kmaj(k, p, kTcPixTile)) = h;
+          if (GT == 2) *reinterpret_cast<uint16_t*>(b2 + kB2Term + kmaj(k, p, kTcPixTile)) = bf16_bits(v - bf16_val(h));
+        }
       }
       fence_proxy_async();
       mbar_arrive(&bar_b_full[s]);
       return true;
     };
     auto consume = [&](int t) -> bool {
-      const int s = t % NB;
-      if (!mbar_wait_warp(&bar_d1_full, (uint32_t)(t & 1), &abort_flag, status)) return false;
-      if (t >= 1 && !mbar_wait_warp(&bar_a2_empty, (uint32_t)((t - 1) & 1), &abort_flag, status)) return false;
+      const int s = t % NB, b1 = t & 1, a = t % NA;
+      if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t >> 1) & 1), &abort_flag, status)) return false;
       tc_fence_after();
+      uint32_t r0[32], r1[32];
+      const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
+      tmem_ld32(tmem + lane_base + col, r0);
+      tmem_ld32(tmem + lane_base + col + 32, r1);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&bar_d1_empty[b1]);  // the logits are in registers: release the TMEM tile
       // this grain's centre logit for the tile
       float c[DIM], ec[K];
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) c[a] = sCen[s * 4 + a];
+      for (int q = 0; q < DIM; ++q) c[q] = sCen[s * 4 + q];
       legendre_features<DIM, D>(c, ec);
       const float off = dot_f<K>(th, ec);
-      const float* ls = sLse + s * kTcPixTile;
-      const int* lb = sLab + s * kTcPixTile;
-#pragma unroll 1
-      for (int c0 = 0; c0 < kTcPixTile; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)c0, r);
-        tmem_wait_ld();
+      if (t >= NA && !mbar_wait_warp(&bar_a2_empty[a], (uint32_t)(((t / NA) - 1) & 1), &abort_flag, status))
+        return false;
+      const float* ls = sLse + s * kTcPixTile + half * 64;
+      const int* lb = sLab + s * kTcPixTile + half * 64;
+      uint8_t* a2 = sA2 + a * kA2Bytes;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const uint32_t* r = h2 ? r1 : r0;
         uint32_t hi[16], lo[16];
 #pragma unroll
         for (int q = 0; q < 32; q += 2) {
           float cc[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const int x = c0 + q + u;
-            const float p = Arith<float>::ex((__uint_as_float(r[q + u]) + off) - ls[x]);
-            cc[u] = (lb[x] == i ? 1.f : 0.f) - p;
+            const int x = 32 * h2 + q + u;
+            const float pr = Arith<float>::ex((__uint_as_float(r[q + u]) + off) - ls[x]);
+            cc[u] = (lb[x] == i ? 1.f : 0.f) - pr;
           }
           const uint16_t h0 = bf16_bits(cc[0]), h1 = bf16_bits(cc[1]);
           hi[q >> 1] = (uint32_t)h0 | ((uint32_t)h1 << 16);
@@ -713,17 +807,15 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
         }
 #pragma unroll
         for (int q8 = 0; q8 < 32; q8 += 8) {
-          const uint32_t o = kmaj(tid, c0 + q8, kTcPixTile);
-          *reinterpret_cast<uint4*>(sA2 + o) = make_uint4(hi[q8 / 2], hi[q8 / 2 + 1], hi[q8 / 2 + 2], hi[q8 / 2 + 3]);
+          const uint32_t o = kmaj(gr, half * 64 + 32 * h2 + q8, kTcPixTile);
+          *reinterpret_cast<uint4*>(a2 + o) = make_uint4(hi[q8 / 2], hi[q8 / 2 + 1], hi[q8 / 2 + 2], hi[q8 / 2 + 3]);
           if (GT == 2)
-            *reinterpret_cast<uint4*>(sA2 + 128 * kTcPixTile * 2 + o) =
+            *reinterpret_cast<uint4*>(a2 + kA2Term + o) =
                 make_uint4(lo[q8 / 2], lo[q8 / 2 + 1], lo[q8 / 2 + 2], lo[q8 / 2 + 3]);
         }
       }
-      tc_fence_before();
-      mbar_arrive(&bar_d1_empty);
       fence_proxy_async();
-      mbar_arrive(&bar_a2_full);
+      mbar_arrive(&bar_a2_full[a]);
       return true;
     };
     bool ok = n_pt > 0 ? produce(0, 0) : true;
@@ -736,31 +828,33 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
         if (ok && t + 1 < n_pt) ok = produce(t + 1, 0);
       }
     }
-    // chunk result: D2 row of this grain
+    // chunk result: D2 row of this grain (first warpgroup)
     if (ok && n_pt > 0) ok = mbar_wait_warp(&bar_d2_done, 0, &abort_flag, status);
-    if (ok && n_pt > 0) {
-      tc_fence_after();
-      uint32_t r[32];
-      if (KW == 16) {
-        tmem_ld16(tmem + lane_base + (uint32_t)D2COL, r);
-      } else {
-        tmem_ld32(tmem + lane_base + (uint32_t)D2COL, r);
-      }
-      tmem_wait_ld();
-      if (i < N) {
+    if (half == 0) {
+      if (ok && n_pt > 0) {
+        tc_fence_after();
+        uint32_t r[32];
+        if (KW == 16) {
+          tmem_ld16(tmem + lane_base + (uint32_t)D2COL, r);
+        } else {
+          tmem_ld32(tmem + lane_base + (uint32_t)D2COL, r);
+        }
+        tmem_wait_ld();
+        if (i < N) {
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-          part[((int64_t)blockIdx.x * N + i) * K + k] = abort_flag ? NAN : (double)__uint_as_float(r[k]);
+          for (int k = 0; k < K; ++k)
+            part[((int64_t)blockIdx.x * N + i) * K + k] = abort_flag ? NAN : (double)__uint_as_float(r[k]);
+        }
+      } else if (i < N) {
+        for (int k = 0; k < K; ++k) part[((int64_t)blockIdx.x * N + i) * K + k] = n_pt > 0 ? NAN : 0.0;
       }
-    } else if (i < N) {
-      for (int k = 0; k < K; ++k) part[((int64_t)blockIdx.x * N + i) * K + k] = n_pt > 0 ? NAN : 0.0;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 4) {
+  if (warp == 8) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, kTcCols);
   }
 }
 
@@ -794,22 +888,21 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t P = c.g.P;
   const int Npad = (N + 127) / 128 * 128;
   const size_t row_bytes = (size_t)KT * 2;
-  const size_t smem1 = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4;
-  auto smem2_for = [&](int nb) {
-    return 128 * row_bytes + nb * kTcPixTile * row_bytes + (size_t)nb * GT * KW * kTcPixTile * 2 +
-           (size_t)GT * 128 * kTcPixTile * 2 + (size_t)nb * kTcPixTile * 8 + (size_t)nb * 16;
-  };
-  const size_t smem_cap = 220 * 1024;
-  constexpr int NB = (128 * KT * 2 + 2 * 128 * KT * 2 + 2 * GT * KW * 128 * 2 + GT * 128 * 128 * 2 + 2 * 128 * 8 +
-                      32) <= 220 * 1024
-                         ? 2
-                         : 1;
-  const size_t smem2 = smem2_for(NB);
-  if (smem1 > smem_cap || smem2 > smem_cap) return PD_ENOTSUP;  // too many grains for a resident image
-  // at least 100 KiB of dynamic shared memory per CTA keeps at most two CTAs
-  // on an SM, so their two 256-column TMEM allocations always fit
-  const size_t smem1_req = std::max<size_t>(smem1, 100 * 1024);
-  const size_t smem2_req = std::max<size_t>(smem2, 100 * 1024);
+  const size_t smem1 = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
+                       2 * kTcPixTile * 8;
+  constexpr size_t kCap = 220 * 1024;
+  // pass-2 stages: two of each when they fit, else one
+  constexpr size_t kS2Fixed = (size_t)128 * KT * 2;
+  constexpr size_t kS2PerB = (size_t)kTcPixTile * KT * 2 + (size_t)GT * KW * kTcPixTile * 2 + kTcPixTile * 8 + 16;
+  constexpr size_t kS2PerA = (size_t)GT * 128 * kTcPixTile * 2;
+  constexpr int NB = kS2Fixed + 2 * kS2PerB + 2 * kS2PerA <= kCap ? 2 : (kS2Fixed + 2 * kS2PerB + kS2PerA <= kCap ? 2 : 1);
+  constexpr int NA = kS2Fixed + 2 * kS2PerB + 2 * kS2PerA <= kCap ? 2 : 1;
+  const size_t smem2 = kS2Fixed + NB * kS2PerB + NA * kS2PerA;
+  if (smem1 > kCap || smem2 > kCap) return PD_ENOTSUP;  // too many grains for a resident image
+  // at least 120 KiB of dynamic shared memory per CTA keeps one CTA per SM,
+  // which owns all 512 TMEM columns
+  const size_t smem1_req = std::max<size_t>(smem1, 120 * 1024);
+  const size_t smem2_req = std::max<size_t>(smem2, 120 * 1024);
 
   const TileMap tm = make_tiles<DIM>(c.g);
   const int sms = device_sm_count();
@@ -846,7 +939,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
            k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, img, th32, lse, objp, status));
   if (c.grad) {
-    auto k2 = k_tc_pass2<DIM, D, KS, NB>;
+    auto k2 = k_tc_pass2<DIM, D, KS, NB, NA>;
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
     dim3 grid2(nch_eff, gblocks);
