@@ -96,6 +96,10 @@ def _load():
             lib.or_newton_cg_fit.argtypes = [gp, ip, C.c_int, C.c_int, C.c_double, dp,
                                              C.c_int, C.c_int, C.c_double, dp,
                                              C.POINTER(FitReport)]
+            lib.or_mlp_forward.argtypes = [C.c_int] * 5 + [dp] * 8
+            lib.or_mlp_loss_grad.argtypes = [C.c_int] * 5 + [dp] * 14
+            lib.or_mlp_loss_grad.restype = C.c_double
+            lib.or_mlp_features.argtypes = [gp, ip, C.c_int, C.c_int, C.c_int, dp]
             _lib = lib
     return _lib
 
@@ -307,3 +311,42 @@ def newton_cg_fit(grid: Grid, labels, N: int, d: int, eps: float, theta0,
                                   _dp(trace), C.byref(rep))
     assert rc == 0
     return th, rep, trace[:rep.iters]
+
+
+# ---------------------------------------------------------------------------
+# learned warm start (not from the paper): the MLP and its inputs
+# ---------------------------------------------------------------------------
+def mlp_forward(X, W1, b1, W2, b2, W3, b3):
+    """y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for every row of X."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    ws = [np.ascontiguousarray(w, dtype=np.float64) for w in (W1, b1, W2, b2, W3, b3)]
+    B, n_in = X.shape
+    n_h1, n_h2, n_out = ws[0].shape[0], ws[2].shape[0], ws[4].shape[0]
+    Y = np.empty((B, n_out))
+    _load().or_mlp_forward(B, n_in, n_h1, n_h2, n_out, _dp(X), *[_dp(w) for w in ws], _dp(Y))
+    return Y
+
+
+def mlp_loss_grad(X, T, W1, b1, W2, b2, W3, b3):
+    """Mean squared error and its gradients (back-propagation)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    ws = [np.ascontiguousarray(w, dtype=np.float64) for w in (W1, b1, W2, b2, W3, b3)]
+    B, n_in = X.shape
+    n_h1, n_h2, n_out = ws[0].shape[0], ws[2].shape[0], ws[4].shape[0]
+    gs = [np.empty_like(w) for w in ws]
+    loss = _load().or_mlp_loss_grad(B, n_in, n_h1, n_h2, n_out, _dp(X), _dp(T), *[_dp(w) for w in ws],
+                                    *[_dp(g) for g in gs])
+    return loss, gs
+
+
+def mlp_features(grid: Grid, labels, N: int, dm: int = 4, n_nb: int = 8):
+    """[N, (1 + n_nb) K_dm] warm-start inputs: normalised grain moments and
+    those of the n_nb nearest grains by centroid."""
+    lab = _labels(labels)
+    Kd = K(grid.dim, dm)
+    F = np.empty((N, (1 + n_nb) * Kd))
+    rc = _load().or_mlp_features(grid.ref, _ip(lab), N, dm, n_nb, _dp(F))
+    if rc != 0:
+        raise ValueError("oracle: invalid labels")
+    return F

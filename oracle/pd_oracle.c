@@ -923,3 +923,150 @@ done:
   free(sv); free(r); free(pv); free(hp);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start: a multilayer perceptron with two ReLU hidden layers, */
+/*   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3,           */
+/* and the mean squared error L = (1/(B n_out)) sum (y - t)^2 with its      */
+/* gradients by the chain rule (textbook back-propagation).  Weights are    */
+/* row-major [n_out_of_layer][n_in_of_layer].  Not from the paper: this     */
+/* restates the network that maps grain moments to warm-start parameters.   */
+/* ------------------------------------------------------------------------ */
+static void dense(int B, int n_in, int n_out, const double* X, const double* W,
+                  const double* b, int relu, double* Y) {
+  for (int r = 0; r < B; ++r)
+    for (int o = 0; o < n_out; ++o) {
+      double s = b[o];
+      for (int i = 0; i < n_in; ++i) s += W[(size_t)o * n_in + i] * X[(size_t)r * n_in + i];
+      Y[(size_t)r * n_out + o] = (relu && s < 0.0) ? 0.0 : s;
+    }
+}
+
+int or_mlp_forward(int B, int n_in, int n_h1, int n_h2, int n_out, const double* X,
+                   const double* W1, const double* b1, const double* W2,
+                   const double* b2, const double* W3, const double* b3, double* Y) {
+  double* h1 = (double*)malloc(sizeof(double) * (size_t)B * n_h1);
+  double* h2 = (double*)malloc(sizeof(double) * (size_t)B * n_h2);
+  dense(B, n_in, n_h1, X, W1, b1, 1, h1);
+  dense(B, n_h1, n_h2, h1, W2, b2, 1, h2);
+  dense(B, n_h2, n_out, h2, W3, b3, 0, Y);
+  free(h1); free(h2);
+  return 0;
+}
+
+double or_mlp_loss_grad(int B, int n_in, int n_h1, int n_h2, int n_out, const double* X,
+                        const double* T, const double* W1, const double* b1,
+                        const double* W2, const double* b2, const double* W3,
+                        const double* b3, double* gW1, double* gb1, double* gW2,
+                        double* gb2, double* gW3, double* gb3) {
+  double* h1 = (double*)malloc(sizeof(double) * (size_t)B * n_h1);
+  double* h2 = (double*)malloc(sizeof(double) * (size_t)B * n_h2);
+  double* y = (double*)malloc(sizeof(double) * (size_t)B * n_out);
+  double* dy = (double*)malloc(sizeof(double) * (size_t)B * n_out);
+  double* d2 = (double*)malloc(sizeof(double) * (size_t)B * n_h2);
+  double* d1 = (double*)malloc(sizeof(double) * (size_t)B * n_h1);
+  dense(B, n_in, n_h1, X, W1, b1, 1, h1);
+  dense(B, n_h1, n_h2, h1, W2, b2, 1, h2);
+  dense(B, n_h2, n_out, h2, W3, b3, 0, y);
+  const double scale = 1.0 / ((double)B * n_out);
+  double loss = 0.0;
+  for (size_t q = 0; q < (size_t)B * n_out; ++q) {
+    const double e = y[q] - T[q];
+    loss += e * e;
+    dy[q] = 2.0 * e * scale;            /* dL/dy */
+  }
+  loss *= scale;
+  /* layer 3 */
+  for (int o = 0; o < n_out; ++o) {
+    double sb = 0.0;
+    for (int r = 0; r < B; ++r) sb += dy[(size_t)r * n_out + o];
+    gb3[o] = sb;
+    for (int i = 0; i < n_h2; ++i) {
+      double s = 0.0;
+      for (int r = 0; r < B; ++r) s += dy[(size_t)r * n_out + o] * h2[(size_t)r * n_h2 + i];
+      gW3[(size_t)o * n_h2 + i] = s;
+    }
+  }
+  for (int r = 0; r < B; ++r)
+    for (int i = 0; i < n_h2; ++i) {
+      double s = 0.0;
+      for (int o = 0; o < n_out; ++o) s += W3[(size_t)o * n_h2 + i] * dy[(size_t)r * n_out + o];
+      d2[(size_t)r * n_h2 + i] = h2[(size_t)r * n_h2 + i] > 0.0 ? s : 0.0;   /* relu' */
+    }
+  /* layer 2 */
+  for (int o = 0; o < n_h2; ++o) {
+    double sb = 0.0;
+    for (int r = 0; r < B; ++r) sb += d2[(size_t)r * n_h2 + o];
+    gb2[o] = sb;
+    for (int i = 0; i < n_h1; ++i) {
+      double s = 0.0;
+      for (int r = 0; r < B; ++r) s += d2[(size_t)r * n_h2 + o] * h1[(size_t)r * n_h1 + i];
+      gW2[(size_t)o * n_h1 + i] = s;
+    }
+  }
+  for (int r = 0; r < B; ++r)
+    for (int i = 0; i < n_h1; ++i) {
+      double s = 0.0;
+      for (int o = 0; o < n_h2; ++o) s += W2[(size_t)o * n_h1 + i] * d2[(size_t)r * n_h2 + o];
+      d1[(size_t)r * n_h1 + i] = h1[(size_t)r * n_h1 + i] > 0.0 ? s : 0.0;
+    }
+  /* layer 1 */
+  for (int o = 0; o < n_h1; ++o) {
+    double sb = 0.0;
+    for (int r = 0; r < B; ++r) sb += d1[(size_t)r * n_h1 + o];
+    gb1[o] = sb;
+    for (int i = 0; i < n_in; ++i) {
+      double s = 0.0;
+      for (int r = 0; r < B; ++r) s += d1[(size_t)r * n_h1 + o] * X[(size_t)r * n_in + i];
+      gW1[(size_t)o * n_in + i] = s;
+    }
+  }
+  free(h1); free(h2); free(y); free(dy); free(d2); free(d1);
+  return loss;
+}
+
+/* Warm-start inputs of every grain: its degree-dm Legendre moments divided  */
+/* by |G_i| (the first, psi_0 = 1, is the constant 1), followed by the same  */
+/* vectors of its n_nb nearest grains by centroid distance (centroid = the   */
+/* normalised psi_(1,0), psi_(0,1) moments, i.e. the mean pixel), nearest    */
+/* first, ties to the smaller index; with fewer than n_nb other grains the   */
+/* list is padded with the grain's own vector.  feat: [N][(1+n_nb) Kdm].     */
+int or_mlp_features(const or_grid* g, const int32_t* labels, int N, int dm,
+                    int n_nb, double* feat) {
+  int Kd = or_K(g->dim, dm);
+  double* mom = (double*)malloc(sizeof(double) * (size_t)N * Kd);
+  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * N);
+  int rc = or_grain_moments(g, labels, N, dm, mom, cnt);
+  if (rc) { free(mom); free(cnt); return rc; }
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < Kd; ++k) mom[(size_t)i * Kd + k] = cnt[i] ? mom[(size_t)i * Kd + k] / (double)cnt[i] : 0.0;
+  int F = (1 + n_nb) * Kd;
+  int* nb = (int*)malloc(sizeof(int) * n_nb);
+  double* dist = (double*)malloc(sizeof(double) * n_nb);
+  for (int i = 0; i < N; ++i) {
+    int have = 0;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      double s = 0.0;
+      for (int a = 0; a < g->dim; ++a) {
+        double dx = mom[(size_t)j * Kd + 1 + a] - mom[(size_t)i * Kd + 1 + a];
+        s += dx * dx;
+      }
+      /* insertion into the sorted list of the n_nb nearest */
+      int pos = have;
+      while (pos > 0 && dist[pos - 1] > s) --pos;
+      if (pos >= n_nb) continue;
+      int last = have < n_nb ? have : n_nb - 1;
+      for (int q = last; q > pos; --q) { dist[q] = dist[q - 1]; nb[q] = nb[q - 1]; }
+      dist[pos] = s; nb[pos] = j;
+      if (have < n_nb) ++have;
+    }
+    for (int k = 0; k < Kd; ++k) feat[(size_t)i * F + k] = mom[(size_t)i * Kd + k];
+    for (int q = 0; q < n_nb; ++q) {
+      int j = q < have ? nb[q] : i;
+      for (int k = 0; k < Kd; ++k) feat[(size_t)i * F + (1 + q) * Kd + k] = mom[(size_t)j * Kd + k];
+    }
+  }
+  free(mom); free(cnt); free(nb); free(dist);
+  return 0;
+}

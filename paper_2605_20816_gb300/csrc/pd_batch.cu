@@ -668,7 +668,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
       FitState fs;
       int r = fit_run(ev, th0[m], N, K, *opts, &fs);
       // final double-precision evaluation for the report
-      if (r == PD_OK && opts->prec != PD_FP64) {
+      if (r == PD_OK && fs.final_prec != PD_FP64) {
         std::vector<double> gf;
         r = ev.eval(fs.cur.x, PD_FP64, &fs.cur.f, &gf);
         if (r == PD_OK) fs.cur.g = gf;

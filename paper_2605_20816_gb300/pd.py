@@ -57,6 +57,11 @@ class pd_fit_report(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class pd_map(C.Structure):
+    _fields_ = [("grid", pd_grid), ("labels", C.c_void_p), ("N", C.c_int), ("theta", C.c_void_p),
+                ("obj_out", C.c_void_p), ("grad_out", C.c_void_p)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -87,6 +92,14 @@ def lib():
             L.pd_prof_read.argtypes = [ip, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
             L.pd_objective_grad_noalloc.argtypes = [gp, vp, ip, vp, C.POINTER(pd_eval_opts), vp, vp, vp]
             L.pd_microbench.argtypes = [ip, C.POINTER(C.c_double), vp]
+            mp = C.POINTER(pd_map)
+            L.pd_batch_create.argtypes = [ip, mp, C.POINTER(pd_eval_opts), ip, C.POINTER(vp)]
+            L.pd_batch_eval.argtypes = [vp, vp]
+            L.pd_batch_set_active.argtypes = [vp, C.POINTER(C.c_int32), vp]
+            L.pd_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.pd_batch_destroy.argtypes = [vp]
+            L.pd_batch_destroy.restype = None
+            L.pd_fit_batched.argtypes = [ip, mp, C.POINTER(vp), C.POINTER(pd_fit_opts), C.POINTER(pd_fit_report), vp]
             L.pd_release.argtypes = []
             L.pd_release.restype = None
             _lib = L
@@ -262,6 +275,64 @@ def pd_fit(grid: Grid, labels: torch.Tensor, N: int, d: int, eps: float, theta: 
     rep = pd_fit_report()
     _check(lib().pd_fit(grid.ref, _ptr(labels), N, C.byref(opts), _ptr(th), C.byref(rep), _stream()), "pd_fit")
     return th, rep.as_dict()
+
+
+def _map(grid: Grid, labels, N, theta=None, obj=None, grad=None):
+    return pd_map(grid.c, _ptr(labels), int(N), _ptr(theta), _ptr(obj), _ptr(grad))
+
+
+class Batch:
+    """A pd_batch plan over maps = [(grid, labels, N, theta, obj_out, grad_out)];
+    the caller keeps the tensors alive while the plan is used."""
+
+    def __init__(self, maps, d: int, eps: float, prec: int = PD_FP32, autotune: bool = True):
+        self._keep = maps
+        self.n = len(maps)
+        arr = (pd_map * self.n)(*[_map(*m) for m in maps])
+        opts = pd_eval_opts(d, float(eps), int(prec))
+        h = C.c_void_p()
+        _check(lib().pd_batch_create(self.n, arr, C.byref(opts), 1 if autotune else 0, C.byref(h)),
+               "pd_batch_create")
+        self.h = h
+
+    def eval(self):
+        _check(lib().pd_batch_eval(self.h, _stream()), "pd_batch_eval")
+
+    def set_active(self, active):
+        a = (C.c_int32 * self.n)(*[1 if x else 0 for x in active])
+        self._active = a  # the copy is asynchronous: keep the source alive
+        _check(lib().pd_batch_set_active(self.h, a, _stream()), "pd_batch_set_active")
+
+    def info(self):
+        cf, od, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(lib().pd_batch_info(self.h, C.byref(cf), C.byref(od), C.byref(ms)), "pd_batch_info")
+        return {"chunk_factor": cf.value, "occ_div": od.value, "tuned_ms": ms.value}
+
+    def close(self):
+        if self.h:
+            lib().pd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_fit_batched(maps, thetas, d: int, eps: float, init: int = PD_INIT_ZERO, max_iter: int = 1000,
+                   lbfgs_m: int = 10, prec: int = PD_FP64, refine_iter: int = 0, gtol: float = 0.0,
+                   target_phi: float = -math.inf, switch_rtol: float = 0.0):
+    """maps = [(grid, labels, N)], thetas = [CUDA float64 [N, K]] (in/out).
+    Returns the list of per-map report dicts."""
+    n = len(maps)
+    arr = (pd_map * n)(*[_map(g, lab, N) for g, lab, N in maps])
+    ths = (C.c_void_p * n)(*[t.data_ptr() for t in thetas])
+    opts = pd_fit_opts(d, float(eps), init, PD_METHOD_LBFGS, max_iter, lbfgs_m, 50, prec, refine_iter, gtol,
+                       target_phi, switch_rtol)
+    reps = (pd_fit_report * n)()
+    _check(lib().pd_fit_batched(n, arr, ths, C.byref(opts), reps, _stream()), "pd_fit_batched")
+    return [r.as_dict() for r in reps]
 
 
 def pd_prof_enable(on: bool):
