@@ -273,6 +273,56 @@ int pd_fit_batched(int n_maps, const pd_map* maps, double* const* theta_io,
                    const pd_fit_opts* opts, pd_fit_report* reports,
                    void* stream);
 
+/* ---- learned warm start (not from the paper) -------------------------- */
+/* A three-layer perceptron y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 that
+ * maps the features of a grain (pd_mlp_features) to its parameters, gauge-
+ * fixed to zero mean over the grains and scaled to unit root-mean-square
+ * norm over the grains.  Weights are kept in fp32 for training and used in
+ * bf16 with fp32 accumulation by the forward and backward kernels.
+ * Parameters are laid out W1 [h1][in], b1, W2 [h2][h1], b2, W3 [out][h2], b3. */
+typedef struct pd_mlp pd_mlp;
+
+/* Synchronous: allocates a network with He-uniform weights drawn from a
+ * counter-based generator keyed by seed (zero biases). */
+int pd_mlp_create(int n_in, int n_h1, int n_h2, int n_out, uint64_t seed,
+                  pd_mlp** out);
+void pd_mlp_destroy(pd_mlp* net);
+int64_t pd_mlp_num_params(const pd_mlp* net);
+/* Synchronous copies of all parameters to/from host float[num_params];
+ * rounded != 0 returns the bf16 values the kernels use. */
+int pd_mlp_get_params(const pd_mlp* net, float* host, int rounded);
+int pd_mlp_set_params(pd_mlp* net, const float* host);
+/* Y [B][out] = network(X [B][in]); device pointers. */
+int pd_mlp_forward(const pd_mlp* net, const float* X, int B, float* Y,
+                   void* stream);
+/* Mean squared error of the network on (X, T [B][out]) and its gradient
+ * with respect to every parameter (device float[num_params]). */
+int pd_mlp_loss_grad(const pd_mlp* net, const float* X, const float* T, int B,
+                     float* loss_out, float* grad_out, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on (X, T). */
+int pd_mlp_train_step(pd_mlp* net, const float* X, const float* T, int B,
+                      float lr, float* loss_out, void* stream);
+/* Per-grain inputs of the network: the grain's Legendre moments of degree
+ * <= 4 divided by |G_i| (first entry 1), then those of its 8 nearest grains
+ * by centroid (the mean pixel), nearest first, ties to the smaller index,
+ * padded with the grain's own moments.  feat_out: device float
+ * [N][9 K_4] (135 in 2-D). */
+int pd_mlp_features(const pd_grid* grid, const int32_t* labels, int N,
+                    float* feat_out, void* stream);
+/* Training targets of one map from its parameters theta (device double
+ * [N][K], K <= 64): (theta_i - mean_j theta_j) / s, s the root-mean-square
+ * norm of the centred rows; out: device float[N][K]. */
+int pd_mlp_targets(const double* theta, int N, int K, float* out, void* stream);
+/* Synchronous: starting parameters for pd_fit (init PD_INIT_GIVEN) from the
+ * network's prediction: the prediction is gauge-fixed (theta_{N-1} = 0,
+ * Remark 4.3) and scaled by the s in {2^(q/2): q = -16..40} that maximises
+ * Phi(s theta) at (d, eps, prec) -- the network predicts the shape of the
+ * diagram, not the sharpness that eps asks for (Lemma 4.1).  theta_out:
+ * device double[N][K]; scale_out (host, may be NULL) receives s. */
+int pd_warm_start(const pd_mlp* net, const pd_grid* grid,
+                  const int32_t* labels, int N, int d, double eps, int prec,
+                  double* theta_out, double* scale_out, void* stream);
+
 /* ---- tracing of the library's own kernels ------------------------------ */
 /* pd_prof_enable(1) clears the record and starts timing every kernel this
  * library launches, with a pair of CUDA events recorded on the launching

@@ -1,0 +1,535 @@
+// pd_mlp.cu -- learned warm start: per-grain moment features, a three-layer
+// perceptron (two ReLU hidden layers) with bf16 weights and fp32
+// accumulation, its forward and backward kernels, Adam training, and the
+// warm-start entry point that turns the network's prediction into starting
+// parameters for the ascent scheme.  (Not from the paper.)
+//
+// Network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with x the features
+// of one grain and y its gauge-fixed (zero mean over grains), scale-
+// normalised (unit root-mean-square norm over grains) parameter vector.
+// The forward pass reads bf16 weights (rounded from the fp32 master copy
+// after every update) and accumulates in fp32; the backward pass uses the
+// same bf16 weights; weight gradients are summed over the batch in fixed
+// order (split over the batch, then a fixed-order sum of the splits).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pd.h"
+#include "pd_internal.h"
+
+struct pd_mlp {
+  int n_in = 0, n_h1 = 0, n_h2 = 0, n_out = 0;
+  size_t n_params = 0;
+  float* w = nullptr;        // fp32 master parameters: W1 b1 W2 b2 W3 b3
+  __nv_bfloat16* wb = nullptr;  // bf16 copy used by the kernels
+  float* m = nullptr;        // Adam moments
+  float* v = nullptr;
+  int64_t step = 0;
+  size_t o_w1 = 0, o_b1 = 0, o_w2 = 0, o_b2 = 0, o_w3 = 0, o_b3 = 0;
+};
+
+namespace pd {
+namespace {
+
+constexpr int kGemmTile = 64;
+constexpr int kGemmK = 16;
+
+__device__ __forceinline__ float ld_f(const float* p) { return *p; }
+__device__ __forceinline__ float ld_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]) with A(m,k) = A[m*sam + k*sak],
+// B(k,n) = B[k*sbk + n*sbn]; EPI 0: plain, 1: ReLU, 2: multiply by
+// (mask[m*ldm + n] > 0) (ReLU derivative).  Split-K over blockIdx.z writes
+// slice z of C (C + z*M*ldc), k in [z*kchunk, (z+1)*kchunk).
+template <typename TA, typename TB, int EPI>
+__global__ void __launch_bounds__(256)
+k_gemm(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
+       int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, const __nv_bfloat16* __restrict__ bias,
+       const float* __restrict__ mask, int64_t ldm, int kchunk) {
+  __shared__ float As[kGemmK][kGemmTile + 4];
+  __shared__ float Bs[kGemmK][kGemmTile + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * kGemmTile, n0 = blockIdx.x * kGemmTile;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  float acc[4][4] = {};
+  for (int k0 = kb; k0 < ke; k0 += kGemmK) {
+    for (int e = threadIdx.x; e < kGemmTile * kGemmK; e += 256) {
+      const int r = e / kGemmK, c = e % kGemmK;
+      const int m = m0 + r, k = k0 + c;
+      As[c][r] = (m < M && k < ke) ? ld_f(A + (int64_t)m * sam + (int64_t)k * sak) : 0.f;
+      const int n = n0 + r;
+      Bs[c][r] = (n < N && k < ke) ? ld_f(B + (int64_t)k * sbk + (int64_t)n * sbn) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGemmK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[kk][ty * 4 + i];
+        b[i] = Bs[kk][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* Cz = C + (int64_t)blockIdx.z * M * ldc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (bias) v += __bfloat162float(bias[n]);
+      if (EPI == 1) v = fmaxf(v, 0.f);
+      if (EPI == 2) v = mask[(int64_t)m * ldm + n] > 0.f ? v : 0.f;
+      Cz[(int64_t)m * ldc + n] = v;
+    }
+  }
+}
+
+// out[q] = sum over s of part[s][q] (fixed order)
+__global__ void k_sum_slices(const float* __restrict__ part, int S, int64_t n, float* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float s = 0.f;
+  for (int z = 0; z < S; ++z) s += part[(int64_t)z * n + q];
+  out[q] = s;
+}
+
+// column sums of a [rows][cols] matrix (bias gradients), fixed order
+__global__ void k_colsum(const float* __restrict__ X, int rows, int cols, float* __restrict__ out) {
+  __shared__ float s[256];
+  const int c = blockIdx.x;
+  float a = 0.f;
+  for (int r = threadIdx.x; r < rows; r += 256) a += X[(int64_t)r * cols + c];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = s[0];
+}
+
+// dY = 2 (Y - T) / (B n_out); per-block loss partials (fixed order)
+__global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, int64_t n, float inv,
+                      float* __restrict__ dY, float* __restrict__ part) {
+  __shared__ float s[256];
+  float a = 0.f;
+  for (int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x; q < n; q += (int64_t)gridDim.x * 256) {
+    const float e = Y[q] - T[q];
+    a = fmaf(e, e, a);
+    dY[q] = 2.f * e * inv;
+  }
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_mse_final(const float* __restrict__ part, int n, float inv, float* __restrict__ loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float s = 0.f;
+    for (int q = 0; q < n; ++q) s += part[q];
+    *loss = s * inv;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, float* __restrict__ m,
+                       float* __restrict__ v, const float* __restrict__ g, int64_t n, float lr, float b1, float b2,
+                       float c1, float c2, float epsa) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const float gq = g[q];
+  const float mq = b1 * m[q] + (1.f - b1) * gq;
+  const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+  m[q] = mq;
+  v[q] = vq;
+  const float wq = w[q] - lr * (mq * c1) / (sqrtf(vq * c2) + epsa);
+  w[q] = wq;
+  wb[q] = __float2bfloat16_rn(wq);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) wb[q] = __float2bfloat16_rn(w[q]);
+}
+
+// Counter-based uniform draw in [-1, 1) (splitmix64 of seed and index).
+__device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.f - 1.f;
+}
+
+// He-uniform weights (limit sqrt(6 / fan_in)), zero biases.
+__global__ void k_init(float* __restrict__ w, int64_t n, int64_t o_start, int fan_in, int is_bias, uint64_t seed) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  w[q] = is_bias ? 0.f : hash_uniform(seed, (uint64_t)(o_start + q)) * sqrtf(6.f / (float)fan_in);
+}
+
+// ---------------------------------------------------------------------------
+// Features: normalised degree-4 moments of a grain and of its 8 nearest
+// grains by centroid (nearest first, ties to the smaller index; padded with
+// the grain's own vector).
+// ---------------------------------------------------------------------------
+constexpr int kNb = 8;
+
+__global__ void k_norm_moments(const double* __restrict__ mom, const int64_t* __restrict__ cnt, int N, int Kd,
+                               double* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)N * Kd) return;
+  const int i = (int)(q / Kd);
+  out[q] = cnt[i] ? mom[q] / (double)cnt[i] : 0.0;
+}
+
+__global__ void k_knn_features(const double* __restrict__ nm, int N, int Kd, int dim, float* __restrict__ feat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double dist[kNb];
+  int nb[kNb];
+  int have = 0;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    double s = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      const double dx = nm[(int64_t)j * Kd + 1 + a] - nm[(int64_t)i * Kd + 1 + a];
+      s += dx * dx;
+    }
+    int pos = have;
+    while (pos > 0 && dist[pos - 1] > s) --pos;
+    if (pos >= kNb) continue;
+    const int last = have < kNb ? have : kNb - 1;
+    for (int q = last; q > pos; --q) {
+      dist[q] = dist[q - 1];
+      nb[q] = nb[q - 1];
+    }
+    dist[pos] = s;
+    nb[pos] = j;
+    if (have < kNb) ++have;
+  }
+  const int F = (1 + kNb) * Kd;
+  for (int k = 0; k < Kd; ++k) feat[(int64_t)i * F + k] = (float)nm[(int64_t)i * Kd + k];
+  for (int q = 0; q < kNb; ++q) {
+    const int j = q < have ? nb[q] : i;
+    for (int k = 0; k < Kd; ++k) feat[(int64_t)i * F + (1 + q) * Kd + k] = (float)nm[(int64_t)j * Kd + k];
+  }
+}
+
+template <typename TA, typename TB, int EPI>
+int gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
+         int64_t sbn, float* C, int64_t ldc, const __nv_bfloat16* bias, const float* mask, int64_t ldm,
+         int splits = 1) {
+  const int kchunk = ((K + splits - 1) / splits + kGemmK - 1) / kGemmK * kGemmK;
+  const int sz = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + kGemmTile - 1) / kGemmTile, (M + kGemmTile - 1) / kGemmTile, sz);
+  PD_TIMED(st, "mlp_gemm",
+           (k_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, mask, ldm,
+                                                       kchunk)));
+  return sz;
+}
+
+struct Acts {
+  float *h1, *h2, *y;
+};
+
+int forward(const pd_mlp* net, const float* X, int B, Acts a, cudaStream_t st) {
+  const __nv_bfloat16* W1 = net->wb + net->o_w1;
+  const __nv_bfloat16* W2 = net->wb + net->o_w2;
+  const __nv_bfloat16* W3 = net->wb + net->o_w3;
+  gemm<float, __nv_bfloat16, 1>(st, B, net->n_h1, net->n_in, X, net->n_in, 1, W1, 1, net->n_in, a.h1, net->n_h1,
+                                net->wb + net->o_b1, nullptr, 0);
+  gemm<float, __nv_bfloat16, 1>(st, B, net->n_h2, net->n_h1, a.h1, net->n_h1, 1, W2, 1, net->n_h1, a.h2, net->n_h2,
+                                net->wb + net->o_b2, nullptr, 0);
+  gemm<float, __nv_bfloat16, 0>(st, B, net->n_out, net->n_h2, a.h2, net->n_h2, 1, W3, 1, net->n_h2, a.y, net->n_out,
+                                net->wb + net->o_b3, nullptr, 0);
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+// Loss and gradients (into g, laid out like the parameters).
+int loss_grad(const pd_mlp* net, const float* X, const float* T, int B, float* loss, float* g, cudaStream_t st) {
+  Scratch sc(st);
+  const int H1 = net->n_h1, H2 = net->n_h2, O = net->n_out, I = net->n_in;
+  Acts a{sc.get<float>((size_t)B * H1), sc.get<float>((size_t)B * H2), sc.get<float>((size_t)B * O)};
+  float* dy = sc.get<float>((size_t)B * O);
+  float* d2 = sc.get<float>((size_t)B * H2);
+  float* d1 = sc.get<float>((size_t)B * H1);
+  const int splits = std::max(1, std::min(64, B / 512));
+  const size_t slice = (size_t)std::max(H1 * I, std::max(H2 * H1, O * H2));
+  float* part = sc.get<float>(slice * splits);
+  const int mse_blocks = 256;
+  float* lpart = sc.get<float>(mse_blocks);
+  if (!sc.ok()) return PD_ENOMEM;
+  int rc = forward(net, X, B, a, st);
+  if (rc) return rc;
+  const int64_t nY = (int64_t)B * O;
+  k_mse<<<mse_blocks, 256, 0, st>>>(a.y, T, nY, 1.f / (float)nY, dy, lpart);
+  k_mse_final<<<1, 32, 0, st>>>(lpart, mse_blocks, 1.f / (float)nY, loss);
+  const __nv_bfloat16* W2 = net->wb + net->o_w2;
+  const __nv_bfloat16* W3 = net->wb + net->o_w3;
+  // layer 3: gW3 = dy^T h2, gb3 = colsum dy, d2 = (dy W3) * relu'(h2)
+  int s = gemm<float, float, 0>(st, O, H2, B, dy, 1, O, a.h2, H2, 1, part, H2, nullptr, nullptr, 0, splits);
+  k_sum_slices<<<(O * H2 + 255) / 256, 256, 0, st>>>(part, s, (int64_t)O * H2, g + net->o_w3);
+  k_colsum<<<O, 256, 0, st>>>(dy, B, O, g + net->o_b3);
+  gemm<float, __nv_bfloat16, 2>(st, B, H2, O, dy, O, 1, W3, H2, 1, d2, H2, nullptr, a.h2, H2);
+  // layer 2
+  s = gemm<float, float, 0>(st, H2, H1, B, d2, 1, H2, a.h1, H1, 1, part, H1, nullptr, nullptr, 0, splits);
+  k_sum_slices<<<(H2 * H1 + 255) / 256, 256, 0, st>>>(part, s, (int64_t)H2 * H1, g + net->o_w2);
+  k_colsum<<<H2, 256, 0, st>>>(d2, B, H2, g + net->o_b2);
+  gemm<float, __nv_bfloat16, 2>(st, B, H1, H2, d2, H2, 1, W2, H1, 1, d1, H1, nullptr, a.h1, H1);
+  // layer 1
+  s = gemm<float, float, 0>(st, H1, I, B, d1, 1, H1, X, I, 1, part, I, nullptr, nullptr, 0, splits);
+  k_sum_slices<<<(H1 * I + 255) / 256, 256, 0, st>>>(part, s, (int64_t)H1 * I, g + net->o_w1);
+  k_colsum<<<H1, 256, 0, st>>>(d1, B, H1, g + net->o_b1);
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+}  // namespace
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" int pd_mlp_create(int n_in, int n_h1, int n_h2, int n_out, uint64_t seed, pd_mlp** out) {
+  if (!out || n_in < 1 || n_h1 < 1 || n_h2 < 1 || n_out < 1) return PD_EINVAL;
+  pd_mlp* net = new pd_mlp();
+  net->n_in = n_in;
+  net->n_h1 = n_h1;
+  net->n_h2 = n_h2;
+  net->n_out = n_out;
+  size_t o = 0;
+  net->o_w1 = o; o += (size_t)n_h1 * n_in;
+  net->o_b1 = o; o += n_h1;
+  net->o_w2 = o; o += (size_t)n_h2 * n_h1;
+  net->o_b2 = o; o += n_h2;
+  net->o_w3 = o; o += (size_t)n_out * n_h2;
+  net->o_b3 = o; o += n_out;
+  net->n_params = o;
+  if (cudaMalloc(&net->w, sizeof(float) * o) != cudaSuccess || cudaMalloc(&net->m, sizeof(float) * o) != cudaSuccess ||
+      cudaMalloc(&net->v, sizeof(float) * o) != cudaSuccess ||
+      cudaMalloc(&net->wb, sizeof(__nv_bfloat16) * o) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(net->w);
+    cudaFree(net->m);
+    cudaFree(net->v);
+    delete net;
+    return PD_ENOMEM;
+  }
+  cudaMemset(net->m, 0, sizeof(float) * o);
+  cudaMemset(net->v, 0, sizeof(float) * o);
+  struct L {
+    size_t off, n;
+    int fan, bias;
+  } ls[] = {{net->o_w1, (size_t)n_h1 * n_in, n_in, 0}, {net->o_b1, (size_t)n_h1, n_in, 1},
+            {net->o_w2, (size_t)n_h2 * n_h1, n_h1, 0}, {net->o_b2, (size_t)n_h2, n_h1, 1},
+            {net->o_w3, (size_t)n_out * n_h2, n_h2, 0}, {net->o_b3, (size_t)n_out, n_h2, 1}};
+  for (const L& l : ls)
+    k_init<<<(unsigned)((l.n + 255) / 256), 256>>>(net->w + l.off, (int64_t)l.n, (int64_t)l.off, l.fan, l.bias, seed);
+  k_to_bf16<<<(unsigned)((o + 255) / 256), 256>>>(net->w, net->wb, (int64_t)o);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    delete net;
+    return PD_ECUDA;
+  }
+  *out = net;
+  return PD_OK;
+}
+
+extern "C" void pd_mlp_destroy(pd_mlp* net) {
+  if (!net) return;
+  cudaDeviceSynchronize();
+  cudaFree(net->w);
+  cudaFree(net->wb);
+  cudaFree(net->m);
+  cudaFree(net->v);
+  delete net;
+}
+
+extern "C" int64_t pd_mlp_num_params(const pd_mlp* net) { return net ? (int64_t)net->n_params : -1; }
+
+extern "C" int pd_mlp_get_params(const pd_mlp* net, float* host, int rounded) {
+  if (!net || !host) return PD_EINVAL;
+  if (!rounded) return cudaMemcpy(host, net->w, sizeof(float) * net->n_params, cudaMemcpyDeviceToHost) == cudaSuccess
+                           ? PD_OK
+                           : PD_ECUDA;
+  std::vector<__nv_bfloat16> b(net->n_params);
+  if (cudaMemcpy(b.data(), net->wb, sizeof(__nv_bfloat16) * net->n_params, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PD_ECUDA;
+  for (size_t q = 0; q < net->n_params; ++q) host[q] = __bfloat162float(b[q]);
+  return PD_OK;
+}
+
+extern "C" int pd_mlp_set_params(pd_mlp* net, const float* host) {
+  if (!net || !host) return PD_EINVAL;
+  if (cudaMemcpy(net->w, host, sizeof(float) * net->n_params, cudaMemcpyHostToDevice) != cudaSuccess) return PD_ECUDA;
+  k_to_bf16<<<(unsigned)((net->n_params + 255) / 256), 256>>>(net->w, net->wb, (int64_t)net->n_params);
+  return cudaDeviceSynchronize() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+extern "C" int pd_mlp_forward(const pd_mlp* net, const float* X, int B, float* Y, void* stream) {
+  if (!net || !X || !Y || B < 0) return PD_EINVAL;
+  if (B == 0) return PD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc(st);
+  Acts a{sc.get<float>((size_t)B * net->n_h1), sc.get<float>((size_t)B * net->n_h2), Y};
+  if (!sc.ok()) return PD_ENOMEM;
+  return forward(net, X, B, a, st);
+}
+
+extern "C" int pd_mlp_loss_grad(const pd_mlp* net, const float* X, const float* T, int B, float* loss_out,
+                                float* grad_out, void* stream) {
+  if (!net || !X || !T || !loss_out || !grad_out || B < 1) return PD_EINVAL;
+  return loss_grad(net, X, T, B, loss_out, grad_out, (cudaStream_t)stream);
+}
+
+extern "C" int pd_mlp_train_step(pd_mlp* net, const float* X, const float* T, int B, float lr, float* loss_out,
+                                 void* stream) {
+  if (!net || !X || !T || !loss_out || B < 1 || !(lr > 0.f)) return PD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc(st);
+  float* g = sc.get<float>(net->n_params);
+  if (!sc.ok()) return PD_ENOMEM;
+  int rc = loss_grad(net, X, T, B, loss_out, g, st);
+  if (rc) return rc;
+  net->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f / (1.f - powf(b1, (float)net->step)), c2 = 1.f / (1.f - powf(b2, (float)net->step));
+  PD_TIMED(st, "mlp_adam",
+           (k_adam<<<(unsigned)((net->n_params + 255) / 256), 256, 0, st>>>(
+               net->w, net->wb, net->m, net->v, g, (int64_t)net->n_params, lr, b1, b2, c1, c2, 1e-8f)));
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+extern "C" int pd_mlp_features(const pd_grid* grid, const int32_t* labels, int N, float* feat_out, void* stream) {
+  Geom g;
+  int rc = validate_grid(grid, &g);
+  if (rc) return rc;
+  if (!labels || !feat_out || N < 1 || g.P < 1) return PD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int Kd = basis_K(grid->dim, 4);
+  Scratch sc(st);
+  double* mom = sc.get<double>((size_t)N * Kd);
+  double* nm = sc.get<double>((size_t)N * Kd);
+  int64_t* cnt = sc.get<int64_t>(N);
+  if (!sc.ok()) return PD_ENOMEM;
+  rc = moments_simt(g, grid->dim, 4, labels, N, mom, cnt, st);
+  if (rc) return rc;
+  const int64_t n = (int64_t)N * Kd;
+  k_norm_moments<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mom, cnt, N, Kd, nm);
+  PD_TIMED(st, "mlp_features", (k_knn_features<<<(N + 127) / 128, 128, 0, st>>>(nm, N, Kd, grid->dim, feat_out)));
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+// Training targets of one map: t_i = (theta_i - mean_j theta_j) / s with
+// s^2 = mean_i |theta_i - mean_j theta_j|^2 (one block, fixed order).
+static __global__ void k_mlp_targets(const double* __restrict__ theta, int N, int K, float* __restrict__ out) {
+  __shared__ double mean[64];
+  __shared__ double red[256];
+  for (int k = 0; k < K; ++k) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a += theta[(int64_t)i * K + k];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[k] = red[0] / N;
+    __syncthreads();
+  }
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    for (int k = 0; k < K; ++k) {
+      const double c = theta[(int64_t)i * K + k] - mean[k];
+      a += c * c;
+    }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double sc = red[0] > 0.0 ? 1.0 / sqrt(red[0] / N) : 1.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    for (int k = 0; k < K; ++k) out[(int64_t)i * K + k] = (float)((theta[(int64_t)i * K + k] - mean[k]) * sc);
+}
+
+extern "C" int pd_mlp_targets(const double* theta, int N, int K, float* out, void* stream) {
+  if (!theta || !out || N < 1 || K < 1 || K > 64) return PD_EINVAL;
+  k_mlp_targets<<<1, 256, 0, (cudaStream_t)stream>>>(theta, N, K, out);
+  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+// Synchronous: predict, restore the gauge and pick the scale.
+extern "C" int pd_warm_start(const pd_mlp* net, const pd_grid* grid, const int32_t* labels, int N, int d, double eps,
+                             int prec, double* theta_out, double* scale_out, void* stream) {
+  Geom g;
+  int rc = validate_grid(grid, &g);
+  if (rc) return rc;
+  if (!net || !labels || !theta_out || N < 2 || d < 1 || !(eps > 0.0)) return PD_EINVAL;
+  const int K = basis_K(grid->dim, d);
+  const int Kd = basis_K(grid->dim, 4);
+  if (net->n_in != (1 + kNb) * Kd || net->n_out != K) return PD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc(st);
+  float* feat = sc.get<float>((size_t)N * net->n_in);
+  float* y = sc.get<float>((size_t)N * K);
+  double* th = sc.get<double>((size_t)N * K);
+  double* obj = sc.get<double>(1);
+  if (!sc.ok()) return PD_ENOMEM;
+  rc = pd_mlp_features(grid, labels, N, feat, stream);
+  if (rc) return rc;
+  rc = pd_mlp_forward(net, feat, N, y, stream);
+  if (rc) return rc;
+  std::vector<float> hy((size_t)N * K);
+  if (cudaMemcpyAsync(hy.data(), y, sizeof(float) * hy.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PD_ECUDA;
+  // gauge: theta_{N-1} = 0 (differences between grains are what the
+  // network predicts; the common shift is free, Lemma 4.2)
+  std::vector<double> base((size_t)N * K);
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < K; ++k) base[(size_t)i * K + k] = (double)hy[(size_t)i * K + k] - (double)hy[(size_t)(N - 1) * K + k];
+  // scale: maximise Phi(s * base) over s = 2^(q/2), then keep the best
+  std::vector<double> trial(base.size());
+  double best_phi = -INFINITY, best_s = 1.0;
+  pd_eval_opts o{d, eps, prec};
+  for (int q = -16; q <= 40; ++q) {
+    const double s = pow(2.0, 0.5 * q);
+    for (size_t e = 0; e < base.size(); ++e) trial[e] = s * base[e];
+    if (cudaMemcpyAsync(th, trial.data(), sizeof(double) * trial.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return PD_ECUDA;
+    rc = pd_objective_grad(grid, labels, N, th, &o, obj, nullptr, stream);
+    if (rc) return rc;
+    double phi = 0.0;
+    if (cudaMemcpyAsync(&phi, obj, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return PD_ECUDA;
+    if (isfinite(phi) && phi > best_phi) {
+      best_phi = phi;
+      best_s = s;
+    }
+  }
+  for (size_t e = 0; e < base.size(); ++e) trial[e] = best_s * base[e];
+  if (scale_out) *scale_out = best_s;
+  if (cudaMemcpyAsync(theta_out, trial.data(), sizeof(double) * trial.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PD_ECUDA;
+  return PD_OK;
+}

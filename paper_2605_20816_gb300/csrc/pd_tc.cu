@@ -366,6 +366,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   uint8_t* sA = smem + (size_t)Npad * kRowBytes;                 // 2 stages x 128 x KT
   float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Npad centre logits
   float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Npad);   // 2 stages x 128 (max, sum) of half 1
+  float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);         // 2 stages x 128 label logits
   __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_d_full[kP1Bufs],
       bar_d_empty[kP1Bufs], bar_drain, bar_part_full[2], bar_part_free[2], bar_off_free[2];
   __shared__ uint32_t tmem_slot;
@@ -474,15 +475,18 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         store_eta_row<K, KW, KS>(sA + s * kTileBytes, tid, de);
         j_next = j;
         lG_next = 0.f;
+        float start = -INFINITY;
         if (j >= 0) {
           const int G = labels[j];
           if ((unsigned)G < (unsigned)N) {
             const float* rowp = th32 + (int64_t)G * KP32;
             lG_next = dot_f<K>(rowp, ec) + dot_f<K>(rowp, de);
+            start = lG_next;
           } else {
             lG_next = NAN;
           }
         }
+        sLG[s * 128 + tid] = start;
       }
       for (int i = tid; i < Npad; i += kTcEpiThreads)
         sOff[s * Npad + i] = i < N ? dot_f<K>(th32 + (int64_t)i * KP32, ec) : 0.f;
@@ -503,7 +507,15 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         ok = produce(tn, (it + 1) & 1, (it + 1) >> 1);
         if (!ok) break;
       }
-      float m = -INFINITY, ssum = 0.f;
+      // the stage's centre and label logits were written by other epilogue
+      // threads: acquire them through the stage's full barrier
+      ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
+      if (!ok) break;
+      // the running max starts at the label logit (a lower bound of the max,
+      // usually the max itself), so most chunks of far-away grains lie more
+      // than 127 below it: their exponentials underflow to exactly zero in
+      // ex2.approx.ftz and the whole chunk is skipped
+      float m = sLG[s * 128 + row], ssum = 0.f;
       for (int gt = 0; gt < n_gt; ++gt, ++c) {
         const int b = (int)(c % kP1Bufs);
         ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
@@ -526,7 +538,9 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           float v[32];
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = q < nv ? __uint_as_float(r[q]) + off[32 * h2 + q] : -INFINITY;
-          const float mn = fmaxf(m, tree_max32(v));
+          const float cm = tree_max32(v);
+          if (__all_sync(0xffffffffu, cm < m - 127.f)) continue;
+          const float mn = fmaxf(m, cm);
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = Arith<float>::ex(v[q] - mn);
           ssum = fmaf(ssum, Arith<float>::ex(m - mn), tree_sum32(v));
@@ -742,7 +756,6 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
         for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
         store_eta_row<K, KW, KS>(sB + s * kBBytes, p, de);
         sLse[s * kTcPixTile + p] = vj ? lse[j] : INFINITY;
-        sLab[s * kTcPixTile + p] = vj ? labels[j] : -1;
         if (p == 0) {
 #pragma unroll
           for (int a = 0; a < DIM; ++a) sCen[s * 4 + a] = c[a];
@@ -765,6 +778,8 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
     };
     auto consume = [&](int t) -> bool {
       const int s = t % NB, b1 = t & 1, a = t % NA;
+      // sLse and sCen of the stage were written by other epilogue threads
+      if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) return false;
       if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t >> 1) & 1), &abort_flag, status)) return false;
       tc_fence_after();
       uint32_t r0[32], r1[32];
@@ -783,26 +798,32 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
       if (t >= NA && !mbar_wait_warp(&bar_a2_empty[a], (uint32_t)(((t / NA) - 1) & 1), &abort_flag, status))
         return false;
       const float* ls = sLse + s * kTcPixTile + half * 64;
-      const int* lb = sLab + s * kTcPixTile + half * 64;
       uint8_t* a2 = sA2 + a * kA2Bytes;
 #pragma unroll
       for (int h2 = 0; h2 < 2; ++h2) {
         const uint32_t* r = h2 ? r1 : r0;
         uint32_t hi[16], lo[16];
+        float lsv[32];
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
+          const float4 v4 = *reinterpret_cast<const float4*>(ls + 32 * h2 + q);
+          lsv[q] = v4.x - off;
+          lsv[q + 1] = v4.y - off;
+          lsv[q + 2] = v4.z - off;
+          lsv[q + 3] = v4.w - off;
+        }
 #pragma unroll
         for (int q = 0; q < 32; q += 2) {
-          float cc[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int x = 32 * h2 + q + u;
-            const float pr = Arith<float>::ex((__uint_as_float(r[q + u]) + off) - ls[x]);
-            cc[u] = (lb[x] == i ? 1.f : 0.f) - pr;
-          }
-          const uint16_t h0 = bf16_bits(cc[0]), h1 = bf16_bits(cc[1]);
-          hi[q >> 1] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+          // c = -p; the label term delta_{i G(x)} enters through the grain
+          // moments added at the final reduction
+          const float c0 = -Arith<float>::ex(__uint_as_float(r[q]) - lsv[q]);
+          const float c1 = -Arith<float>::ex(__uint_as_float(r[q + 1]) - lsv[q + 1]);
+          const __nv_bfloat162 h = __floats2bfloat162_rn(c0, c1);
+          hi[q >> 1] = *reinterpret_cast<const uint32_t*>(&h);
           if (GT == 2) {
-            const uint16_t l0 = bf16_bits(cc[0] - bf16_val(h0)), l1 = bf16_bits(cc[1] - bf16_val(h1));
-            lo[q >> 1] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(c0 - hf.x, c1 - hf.y);
+            lo[q >> 1] = *reinterpret_cast<const uint32_t*>(&l);
           }
         }
 #pragma unroll
@@ -859,6 +880,60 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
 }
 
 // ---------------------------------------------------------------------------
+// Label term of eq. (grad): sum_{x in G_i} eta(x) per grain, fp32 features
+// summed exactly in 64-bit fixed point (order independent).
+// ---------------------------------------------------------------------------
+template <int DIM, int D>
+__global__ void k_tc_label_moments(Geom g, const int32_t* __restrict__ labels, int N, double fx_scale,
+                                   unsigned long long* __restrict__ acc) {
+  constexpr int K = basis_K(DIM, D);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = j < g.P;
+  int G = valid ? labels[j] : -1;
+  if (G < 0 || G >= N) G = -1;
+  float x[DIM], eta[K];
+  if (valid) {
+    pixel_coords<DIM>(g, j, x);
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = 0.f;
+  }
+  legendre_features<DIM, D>(x, eta);
+  const int G0 = __shfl_sync(0xffffffffu, G, 0);
+  const bool uniform = __all_sync(0xffffffffu, G == G0) && G0 >= 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    long long v = G >= 0 ? __double2ll_rn((double)eta[k] * fx_scale) : 0ll;
+    if (uniform) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&acc[(int64_t)G0 * K + k], (unsigned long long)v);
+    } else if (G >= 0) {
+      atomicAdd(&acc[(int64_t)G * K + k], (unsigned long long)v);
+    }
+  }
+}
+
+// out[q] = scale * (base[q] / fx + sum_c part[c][q]), fixed order
+__global__ void __launch_bounds__(32 * kRedPhases)
+k_tc_reduce_grad(const double* __restrict__ part, int nchunks, int64_t NK, const unsigned long long* __restrict__ base,
+                 double inv_fx, double scale, double* __restrict__ out) {
+  __shared__ double ssum[kRedPhases][32];
+  const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  double s = 0.0;
+  if (q < NK)
+    for (int c = threadIdx.y; c < nchunks; c += kRedPhases) s += part[(int64_t)c * NK + q];
+  ssum[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && q < NK) {
+    double t = (double)(long long)base[q] * inv_fx;
+#pragma unroll
+    for (int y = 0; y < kRedPhases; ++y) t += ssum[y][threadIdx.x];
+    out[q] = t * scale;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 template <int DIM>
@@ -889,7 +964,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int Npad = (N + 127) / 128 * 128;
   const size_t row_bytes = (size_t)KT * 2;
   const size_t smem1 = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
-                       2 * kTcPixTile * 8;
+                       2 * kTcPixTile * 8 + 2 * kTcPixTile * 4;
   constexpr size_t kCap = 220 * 1024;
   // pass-2 stages: two of each when they fit, else one
   constexpr size_t kS2Fixed = (size_t)128 * KT * 2;
@@ -922,6 +997,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   float* lse = sc.get<float>((size_t)P);
   double* objp = sc.get<double>((size_t)grid1);
   double* part = c.grad ? sc.get<double>((size_t)nch_eff * N * K) : nullptr;
+  unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
@@ -938,7 +1014,15 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     return PD_ECUDA;
   PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
            k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, img, th32, lse, objp, status));
+  // |eta| <= 1, so a grain's label sum is bounded by P: the largest
+  // power-of-two scale that keeps P * scale below 2^62
+  int bits = 0;
+  while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
+  const double fx = ldexp(1.0, 62 - bits);
   if (c.grad) {
+    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+    PD_TIMED(st, "tc_label_moments",
+             (k_tc_label_moments<DIM, D><<<(unsigned)((P + 255) / 256), 256, 0, st>>>(c.g, c.labels, N, fx, lmom)));
     auto k2 = k_tc_pass2<DIM, D, KS, NB, NA>;
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
@@ -950,8 +1034,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   if (c.grad) {
     const int64_t NK = (int64_t)N * K;
     PD_TIMED(st, "reduce_parts",
-             k_reduce_parts<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
-                 part, nch_eff, NK, -1.0 / (c.eps * (double)P), c.grad));
+             k_tc_reduce_grad<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
+                 part, nch_eff, NK, lmom, 1.0 / fx, -1.0 / (c.eps * (double)P), c.grad));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }

@@ -100,6 +100,19 @@ def lib():
             L.pd_batch_destroy.argtypes = [vp]
             L.pd_batch_destroy.restype = None
             L.pd_fit_batched.argtypes = [ip, mp, C.POINTER(vp), C.POINTER(pd_fit_opts), C.POINTER(pd_fit_report), vp]
+            L.pd_mlp_create.argtypes = [ip, ip, ip, ip, C.c_uint64, C.POINTER(vp)]
+            L.pd_mlp_destroy.argtypes = [vp]
+            L.pd_mlp_destroy.restype = None
+            L.pd_mlp_num_params.argtypes = [vp]
+            L.pd_mlp_num_params.restype = C.c_int64
+            L.pd_mlp_get_params.argtypes = [vp, vp, ip]
+            L.pd_mlp_set_params.argtypes = [vp, vp]
+            L.pd_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+            L.pd_mlp_loss_grad.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+            L.pd_mlp_train_step.argtypes = [vp, vp, vp, ip, C.c_float, vp, vp]
+            L.pd_mlp_features.argtypes = [gp, vp, ip, vp, vp]
+            L.pd_mlp_targets.argtypes = [vp, ip, ip, vp, vp]
+            L.pd_warm_start.argtypes = [vp, gp, vp, ip, ip, C.c_double, ip, vp, C.POINTER(C.c_double), vp]
             L.pd_release.argtypes = []
             L.pd_release.restype = None
             _lib = L
@@ -333,6 +346,88 @@ def pd_fit_batched(maps, thetas, d: int, eps: float, init: int = PD_INIT_ZERO, m
     reps = (pd_fit_report * n)()
     _check(lib().pd_fit_batched(n, arr, ths, C.byref(opts), reps, _stream()), "pd_fit_batched")
     return [r.as_dict() for r in reps]
+
+
+class MLP:
+    """The warm-start network (pd_mlp_*)."""
+
+    def __init__(self, n_in=135, n_h1=256, n_h2=256, n_out=15, seed=1):
+        h = C.c_void_p()
+        _check(lib().pd_mlp_create(n_in, n_h1, n_h2, n_out, seed, C.byref(h)), "pd_mlp_create")
+        self.h = h
+        self.dims = (n_in, n_h1, n_h2, n_out)
+        self.n_params = int(lib().pd_mlp_num_params(h))
+
+    def params(self, rounded=True):
+        out = torch.empty(self.n_params, dtype=torch.float32)
+        _check(lib().pd_mlp_get_params(self.h, C.c_void_p(out.data_ptr()), 1 if rounded else 0), "pd_mlp_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = torch.as_tensor(flat, dtype=torch.float32).contiguous()
+        _check(lib().pd_mlp_set_params(self.h, C.c_void_p(flat.data_ptr())), "pd_mlp_set_params")
+
+    def unflatten(self, flat):
+        n_in, h1, h2, o = self.dims
+        sizes = [(h1, n_in), (h1,), (h2, h1), (h2,), (o, h2), (o,)]
+        out, q = [], 0
+        for sz in sizes:
+            n = int(math.prod(sz))
+            out.append(flat[q:q + n].reshape(sz))
+            q += n
+        return out
+
+    def forward(self, X):
+        Y = torch.empty((X.shape[0], self.dims[3]), dtype=torch.float32, device="cuda")
+        _check(lib().pd_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), _stream()), "pd_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T):
+        loss = torch.empty((), dtype=torch.float32, device="cuda")
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().pd_mlp_loss_grad(self.h, _ptr(X), _ptr(T), X.shape[0], _ptr(loss), _ptr(g), _stream()),
+               "pd_mlp_loss_grad")
+        return loss, g
+
+    def train_step(self, X, T, lr):
+        loss = torch.empty((), dtype=torch.float32, device="cuda")
+        _check(lib().pd_mlp_train_step(self.h, _ptr(X), _ptr(T), X.shape[0], C.c_float(lr), _ptr(loss), _stream()),
+               "pd_mlp_train_step")
+        return loss
+
+    def close(self):
+        if self.h:
+            lib().pd_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_mlp_features(grid: Grid, labels, N: int):
+    Kd = pd_K(grid.dim, 4)
+    out = torch.empty((N, 9 * Kd), dtype=torch.float32, device="cuda")
+    _check(lib().pd_mlp_features(grid.ref, _ptr(labels), N, _ptr(out), _stream()), "pd_mlp_features")
+    return out
+
+
+def pd_mlp_targets(theta: torch.Tensor):
+    N, K = theta.shape
+    out = torch.empty((N, K), dtype=torch.float32, device="cuda")
+    _check(lib().pd_mlp_targets(_ptr(theta), N, K, _ptr(out), _stream()), "pd_mlp_targets")
+    return out
+
+
+def pd_warm_start(net: MLP, grid: Grid, labels, N: int, d: int, eps: float, prec: int = PD_FP32):
+    """Returns (theta [N, K] CUDA float64, chosen scale)."""
+    th = torch.empty((N, pd_K(grid.dim, d)), dtype=torch.float64, device="cuda")
+    s = C.c_double()
+    _check(lib().pd_warm_start(net.h, grid.ref, _ptr(labels), N, d, float(eps), prec, _ptr(th), C.byref(s),
+                               _stream()), "pd_warm_start")
+    return th, s.value
 
 
 def pd_prof_enable(on: bool):
