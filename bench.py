@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU oracle sample")
+    ap.add_argument("--workload", default="config2", choices=["config2", "batched", "fit"],
+                    help="config2: the headline line; batched: 256 maps in one persistent launch vs per-map "
+                         "launches; fit: time to the FP64 objective for the precision schedules")
     return ap.parse_args()
 
 
@@ -365,10 +368,109 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """256 2-D maps, sides and grain counts uniform in [128, 1024] and
+    [20, 2000], seeded degree-3 polynomial diagrams fitted at degree 3 (K=10),
+    eps = 1e-3, FP32: one sweep = the objective and gradient of every map."""
+    import torch
+
+    from paper_2605_20816_gb300 import pd
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    d, eps, n_maps = 3, 1e-3, 256
+    shapes = synth.batched_shapes(synth.SEED_BASE + 3, n_maps)
+    maps = []
+    work = 0
+    for q, (n1, n2, N0) in enumerate(shapes):
+        K = pd.pd_K(2, d)
+        y, z = synth.poly_params(synth.SEED_BASE + 1000 + q, N0, 2, K)
+        th = pd.pd_theta_from_apd(2, d, y, np.zeros(N0)).numpy()
+        th[:, 3:] = z[:, 3:]
+        grid = pd.Grid((n1, n2))
+        lab, _, _ = pd.pd_assign(grid, N0, d, torch.from_numpy(th).cuda())
+        lab, n, used = synth.compact(lab.cpu().numpy())
+        tt = torch.from_numpy(np.ascontiguousarray(th[used])).cuda()
+        maps.append((grid, torch.from_numpy(lab.astype(np.int32)).cuda(), n, tt,
+                     torch.empty((), dtype=torch.float64, device="cuda"), torch.empty_like(tt)))
+        work += grid.P * n
+    t0 = time.perf_counter()
+    batch = pd.Batch(maps, d, eps, prec=pd.PD_FP32, autotune=True)
+    t_plan = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        batch.eval()
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 30))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        batch.eval()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / steps
+
+    def loop():
+        for grid, lab, n, tt, obj, grad in maps:
+            pd.pd_objective_grad(grid, lab, n, tt, d, eps, prec=pd.PD_FP32, obj_out=obj, grad_out=grad)
+    for _ in range(2):
+        loop()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        loop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1) / steps
+    info = batch.info()
+    line = {"metric": "pixel*grain objective+gradient evaluations per second (batched maps)",
+            "value": work / (ms_batch * 1e-3), "unit": "pixel*grain/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256 2-D maps, sides U[128,1024], N U[20,2000], degree-3 diagrams, fit degree 3 "
+                                   "(K=10), eps=1e-3", "pixel_grain_per_sweep": work,
+                       "maps": n_maps},
+            "per_map_launches": {"ms_per_sweep": ms_loop, "value": work / (ms_loop * 1e-3)},
+            "speedup_vs_per_map": ms_loop / ms_batch, "autotune": info, "plan_seconds": t_plan}
+    print(json.dumps(line))
+    batch.close()
+    return 0
+
+
+def run_fit(args):
+    """Time to reach the FP64 plain fit's objective (1000 iterations from
+    theta = 0) on the config-2 workload, for the precision schedules."""
+    import torch
+
+    from paper_2605_20816_gb300 import pd
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    grid, lab_np, N, _ = make_workload_gpu(pd, torch)
+    lab = torch.from_numpy(lab_np).cuda()
+    t = time.perf_counter()
+    _, ref = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=1000, prec=pd.PD_FP64)
+    t_ref = time.perf_counter() - t
+    target = ref["phi"] - 1e-8 * abs(ref["phi"])
+    rows = {"fp64_plain": {"seconds": t_ref, "iters": ref["iters"], "evals": ref["evals"], "phi": ref["phi"]}}
+    for name, prec in (("fp32_then_fp64", pd.PD_FP32), ("bf16x3_then_fp64", pd.PD_BF16X3)):
+        t = time.perf_counter()
+        _, rep = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=1000, prec=prec, refine_iter=1000, target_phi=target,
+                           switch_rtol=1e-7)
+        rows[name] = {"seconds": time.perf_counter() - t, "iters": rep["iters"], "iters_phase1": rep["iters_phase1"],
+                      "evals": rep["evals"], "phi": rep["phi"], "reached": rep["phi"] >= target}
+    line = {"metric": "time to the FP64 plain-fit objective (<=1e-8 relative)", "value": rows["fp32_then_fp64"]["seconds"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "FP64 plain fit, 1000 L-BFGS iterations from theta=0",
+                       "phi_ref": ref["phi"]}, "runs": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "fit":
+        return run_fit(args)
     return run_ours(args)
 
 

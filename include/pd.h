@@ -373,6 +373,14 @@ int pd_objective_grad_noalloc(const pd_grid* grid, const int32_t* labels,
                               const pd_eval_opts* opts, double* obj_out,
                               double* grad_out, void* stream);
 
+/* Synchronous self-test of the failure path of the tensor-core kernels: one
+ * CTA waits on an mbarrier phase that nothing completes, with the same kind
+ * of bounded wait those kernels use, limited to `seconds` (0 < seconds <=
+ * 1).  The wait gives up, the kernel records PD_ETIMEOUT in *status_out
+ * (host) and returns normally, so the context stays usable.  Returns PD_OK
+ * when the self-test itself ran. */
+int pd_selftest_wait_timeout(double seconds, int* status_out, void* stream);
+
 /* Release cached library state on the current device (memory pool
  * reservations are trimmed).  Safe to call at any time when no call of
  * this library is in flight. */

@@ -89,6 +89,7 @@ int check_labels_simt(const int32_t* labels, int64_t P, int N, int* bad_dev, cud
 
 // pd_tc.cu (tensor-core evaluation); PD_ENOTSUP where a shape is not covered
 int eval_tc(const EvalCall& c, cudaStream_t st);
+int selftest_wait_timeout(double seconds, int* status_out, cudaStream_t st);
 
 // pd_capi.cu
 int validate_grid(const pd_grid* grid, Geom* g);

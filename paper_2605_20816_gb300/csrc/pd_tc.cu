@@ -516,18 +516,37 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       // than 127 below it: their exponentials underflow to exactly zero in
       // ex2.approx.ftz and the whole chunk is skipped
       float m = sLG[s * 128 + row], ssum = 0.f;
-      for (int gt = 0; gt < n_gt; ++gt, ++c) {
+      // logits of grain tile gt are loaded while tile gt-1 is processed
+      uint32_t n0[32], n1[32];
+      {
         const int b = (int)(c % kP1Bufs);
         ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
-        uint32_t r0[32], r1[32];
         const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 64);
-        tmem_ld32(tmem + lane_base + col, r0);
-        tmem_ld32(tmem + lane_base + col + 32, r1);
+        tmem_ld32(tmem + lane_base + col, n0);
+        tmem_ld32(tmem + lane_base + col + 32, n1);
+      }
+      for (int gt = 0; gt < n_gt; ++gt, ++c) {
+        const int b = (int)(c % kP1Bufs);
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
+        uint32_t r0[32], r1[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          r0[q] = n0[q];
+          r1[q] = n1[q];
+        }
+        if (gt + 1 < n_gt) {
+          const int bn = (int)((c + 1) % kP1Bufs);
+          ok = mbar_wait_warp(&bar_d_full[bn], (uint32_t)(((c + 1) / kP1Bufs) & 1), &abort_flag, status);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t col = (uint32_t)(bn * kTcGrainTile + half * 64);
+          tmem_ld32(tmem + lane_base + col, n0);
+          tmem_ld32(tmem + lane_base + col + 32, n1);
+        }
         const int cbase = gt * kTcGrainTile + half * 64;
         const float* off = sOff + s * Npad + cbase;
 #pragma unroll
@@ -574,6 +593,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       }
       mbar_arrive(&bar_off_free[s]);
     }
+    tmem_wait_ld();  // no TMEM load may be outstanding when the columns are freed
     if (!ok) racc = NAN;
   }
   if (abort_flag) racc = NAN;
@@ -776,19 +796,36 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
       mbar_arrive(&bar_b_full[s]);
       return true;
     };
+    // logits of tile t+1 are loaded from TMEM while tile t is processed
+    // (NB == 2: the MMA warp issues them before the gradient of tile t)
+    uint32_t n0[32], n1[32];
+    bool loaded = false;
+    auto load_logits = [&](int t) -> bool {
+      const int b1 = t & 1;
+      if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t >> 1) & 1), &abort_flag, status)) return false;
+      tc_fence_after();
+      const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
+      tmem_ld32(tmem + lane_base + col, n0);
+      tmem_ld32(tmem + lane_base + col + 32, n1);
+      loaded = true;
+      return true;
+    };
     auto consume = [&](int t) -> bool {
       const int s = t % NB, b1 = t & 1, a = t % NA;
       // sLse and sCen of the stage were written by other epilogue threads
       if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) return false;
-      if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t >> 1) & 1), &abort_flag, status)) return false;
-      tc_fence_after();
-      uint32_t r0[32], r1[32];
-      const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
-      tmem_ld32(tmem + lane_base + col, r0);
-      tmem_ld32(tmem + lane_base + col + 32, r1);
+      if (!loaded && !load_logits(t)) return false;
       tmem_wait_ld();
+      loaded = false;
       tc_fence_before();
       mbar_arrive(&bar_d1_empty[b1]);  // the logits are in registers: release the TMEM tile
+      uint32_t r0[32], r1[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        r0[q] = n0[q];
+        r1[q] = n1[q];
+      }
+      if (NB == 2 && t + 1 < n_pt && !load_logits(t + 1)) return false;
       // this grain's centre logit for the tile
       float c[DIM], ec[K];
 #pragma unroll
@@ -849,6 +886,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
         if (ok && t + 1 < n_pt) ok = produce(t + 1, 0);
       }
     }
+    tmem_wait_ld();  // a prefetched load may be outstanding after an abort
     // chunk result: D2 row of this grain (first warpgroup)
     if (ok && n_pt > 0) ok = mbar_wait_warp(&bar_d2_done, 0, &abort_flag, status);
     if (half == 0) {
@@ -899,18 +937,25 @@ __global__ void k_tc_label_moments(Geom g, const int32_t* __restrict__ labels, i
     for (int a = 0; a < DIM; ++a) x[a] = 0.f;
   }
   legendre_features<DIM, D>(x, eta);
-  const int G0 = __shfl_sync(0xffffffffu, G, 0);
-  const bool uniform = __all_sync(0xffffffffu, G == G0) && G0 >= 0;
+  long long fx[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    long long v = G >= 0 ? __double2ll_rn((double)eta[k] * fx_scale) : 0ll;
-    if (uniform) {
+  for (int k = 0; k < K; ++k) fx[k] = G >= 0 ? __double2ll_rn((double)eta[k] * fx_scale) : 0ll;
+  // one warp-wide sum (and one atomic per feature) for each distinct label
+  // of the warp: spatially coherent labels make that one or two groups
+  unsigned todo = __ballot_sync(0xffffffffu, G >= 0);
+  const int lane = threadIdx.x & 31;
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int L = __shfl_sync(0xffffffffu, G, leader);
+    const unsigned grp = __ballot_sync(0xffffffffu, G == L);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      long long v = (G == L) ? fx[k] : 0ll;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&acc[(int64_t)G0 * K + k], (unsigned long long)v);
-    } else if (G >= 0) {
-      atomicAdd(&acc[(int64_t)G * K + k], (unsigned long long)v);
+      if (lane == 0) atomicAdd(&acc[(int64_t)L * K + k], (unsigned long long)v);
     }
+    todo &= ~grp;
   }
 }
 
@@ -931,6 +976,32 @@ k_tc_reduce_grad(const double* __restrict__ part, int nchunks, int64_t NK, const
     for (int y = 0; y < kRedPhases; ++y) t += ssum[y][threadIdx.x];
     out[q] = t * scale;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
+// arrives at; the wait gives up after limit_ns and records PD_ETIMEOUT.
+// ---------------------------------------------------------------------------
+__global__ void k_selftest_timeout(uint64_t limit_ns, int* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint64_t t0 = global_ns();
+  bool done = false;
+  while (!(done = mbar_test(&bar, 0))) {
+    if (abort_flag) break;
+    if (global_ns() - t0 > limit_ns) {
+      abort_flag = 1;
+      break;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !done) atomicCAS(status, 0, PD_ETIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -1066,6 +1137,17 @@ int eval_tc_ks(const EvalCall& c, cudaStream_t st) {
 
 }  // namespace
 
+int selftest_wait_timeout(double seconds, int* status_out, cudaStream_t st) {
+  Scratch sc(st);
+  int* dstat = sc.get<int>(1);
+  if (!sc.ok()) return PD_ENOMEM;
+  if (cudaMemsetAsync(dstat, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
+  k_selftest_timeout<<<1, 32, 0, st>>>((uint64_t)(seconds * 1e9), dstat);
+  if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+  if (cudaMemcpyAsync(status_out, dstat, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PD_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
 int eval_tc(const EvalCall& c, cudaStream_t st) {
   if (c.v) return PD_ENOTSUP;
   if (c.prec == PD_BF16) return eval_tc_ks<1>(c, st);
@@ -1074,3 +1156,8 @@ int eval_tc(const EvalCall& c, cudaStream_t st) {
 }
 
 }  // namespace pd
+
+extern "C" int pd_selftest_wait_timeout(double seconds, int* status_out, void* stream) {
+  if (!status_out || !(seconds > 0.0) || seconds > 1.0) return PD_EINVAL;
+  return pd::selftest_wait_timeout(seconds, status_out, (cudaStream_t)stream);
+}

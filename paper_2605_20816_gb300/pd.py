@@ -113,6 +113,7 @@ def lib():
             L.pd_mlp_features.argtypes = [gp, vp, ip, vp, vp]
             L.pd_mlp_targets.argtypes = [vp, ip, ip, vp, vp]
             L.pd_warm_start.argtypes = [vp, gp, vp, ip, ip, C.c_double, ip, vp, C.POINTER(C.c_double), vp]
+            L.pd_selftest_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int), vp]
             L.pd_release.argtypes = []
             L.pd_release.restype = None
             _lib = L
@@ -451,6 +452,13 @@ def pd_microbench(kind: int) -> float:
     v = C.c_double()
     _check(lib().pd_microbench(kind, C.byref(v), _stream()), "pd_microbench")
     return v.value
+
+
+def pd_selftest_wait_timeout(seconds: float) -> int:
+    """Runs the bounded-wait self-test; returns the status the kernel recorded."""
+    st = C.c_int(0)
+    _check(lib().pd_selftest_wait_timeout(float(seconds), C.byref(st), _stream()), "pd_selftest_wait_timeout")
+    return st.value
 
 
 def pd_release():
