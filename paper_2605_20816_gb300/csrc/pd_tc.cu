@@ -50,9 +50,10 @@ namespace pd {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
-constexpr int kTcEpiThreads = 256;                // warps 0..7: two epilogue warpgroups
-constexpr int kTcThreads = 288;                   // + warp 8 (TMEM allocation, MMA issue)
-constexpr int kTcMmaTid = 256;
+constexpr int kTcConsumers = 256;                 // warps 0..7: TMEM consumers
+constexpr int kTcProducers = 64;                  // warps 8..9: pixel-operand producers, 2 pixels each
+constexpr int kTcMmaWarp = 10;                    // TMEM allocation and MMA issue
+constexpr int kTcThreads = 11 * 32;               // at most 3 warps per SM sub-partition
 constexpr int kTcCols = 512;                      // TMEM columns per CTA (one CTA per SM)
 constexpr int kTcGrainTile = 128;                 // pass-1 grains per MMA group
 constexpr int kTcPixTile = 128;                   // pixels per tile (both passes)
@@ -272,8 +273,9 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
 // logits, which is unbiased.
 // ---------------------------------------------------------------------------
 struct TileMap {
-  int64_t ntx, nty, ntz;  // tiles per axis (structured grids)
+  int ntx, nty, ntz;      // tiles per axis (structured grids)
   int64_t n_tiles;
+  double inv0, inv1, inv2;  // 1 / n_a
 };
 
 template <int DIM>
@@ -283,29 +285,46 @@ struct TileShape {
   static constexpr int Z = DIM == 2 ? 1 : 4;
 };
 
-// Pixel index of row r of tile t (or -1 outside the pixel set) and the
-// coordinates of the tile centre.
+// Pixel index of row r of tile t (or -1 outside the pixel set), its
+// coordinates x and the coordinates of the tile centre c.  Only 32-bit
+// divisions by the (uniform) tile counts; pixel centres from reciprocals.
 template <int DIM>
-__device__ __forceinline__ int64_t tile_pixel(const Geom& g, const TileMap& tm, int64_t t, int r, float* c) {
+__device__ __forceinline__ int64_t tile_pixel(const Geom& g, const TileMap& tm, int64_t t, int r, float* x,
+                                              float* c) {
   if (g.coords) {
     const int64_t j0 = t * kTcPixTile;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) c[a] = (float)g.coords[j0 * DIM + a];
     const int64_t j = j0 + r;
-    return j < g.P ? j : -1;
+    if (j >= g.P) {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) x[a] = c[a];
+      return -1;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = (float)g.coords[j * DIM + a];
+    return j;
   }
   using TS = TileShape<DIM>;
-  const int64_t tx = t % tm.ntx;
-  const int64_t rest = t / tm.ntx;
-  const int64_t ty = rest % tm.nty;
-  const int64_t tz = rest / tm.nty;
-  const int64_t px = tx * TS::X + (r % TS::X);
-  const int64_t py = ty * TS::Y + ((r / TS::X) % TS::Y);
-  const int64_t pz = tz * TS::Z + (r / (TS::X * TS::Y));
-  c[0] = (float)(-1.0 + (2.0 * (double)(tx * TS::X + TS::X / 2) + 1.0) / (double)g.n0);
-  c[1] = (float)(-1.0 + (2.0 * (double)(ty * TS::Y + TS::Y / 2) + 1.0) / (double)g.n1);
-  if (DIM == 3) c[2] = (float)(-1.0 + (2.0 * (double)(tz * TS::Z + TS::Z / 2) + 1.0) / (double)g.n2);
-  if (px >= g.n0 || py >= g.n1 || (DIM == 3 && pz >= g.n2)) return -1;
+  const unsigned tt = (unsigned)t;
+  const unsigned tx = tt % (unsigned)tm.ntx;
+  const unsigned rest = tt / (unsigned)tm.ntx;
+  const unsigned ty = rest % (unsigned)tm.nty;
+  const unsigned tz = rest / (unsigned)tm.nty;
+  const int64_t px = (int64_t)tx * TS::X + (r % TS::X);
+  const int64_t py = (int64_t)ty * TS::Y + ((r / TS::X) % TS::Y);
+  const int64_t pz = (int64_t)tz * TS::Z + (r / (TS::X * TS::Y));
+  c[0] = (float)fma(2.0 * (double)(tx * TS::X + TS::X / 2) + 1.0, tm.inv0, -1.0);
+  c[1] = (float)fma(2.0 * (double)(ty * TS::Y + TS::Y / 2) + 1.0, tm.inv1, -1.0);
+  if (DIM == 3) c[2] = (float)fma(2.0 * (double)(tz * TS::Z + TS::Z / 2) + 1.0, tm.inv2, -1.0);
+  x[0] = (float)fma(2.0 * (double)px + 1.0, tm.inv0, -1.0);
+  x[1] = (float)fma(2.0 * (double)py + 1.0, tm.inv1, -1.0);
+  if (DIM == 3) x[2] = (float)fma(2.0 * (double)pz + 1.0, tm.inv2, -1.0);
+  if (px >= g.n0 || py >= g.n1 || (DIM == 3 && pz >= g.n2)) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = c[a];
+    return -1;
+  }
   return DIM == 2 ? px + g.n0 * py : px + g.n0 * (py + g.n1 * pz);
 }
 
@@ -317,11 +336,6 @@ __device__ __forceinline__ float dot_f(const float* __restrict__ a, const float*
   return acc;
 }
 
-// ---------------------------------------------------------------------------
-// Epilogue layout.  Warp w of the two epilogue warpgroups reads TMEM lanes
-// 32 (w mod 4) .. +31 (the access rule of tcgen05.ld) and the column half
-// h = w / 4 of each 128-column tile, so 8 warps share every tile.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ float tree_max32(const float* v) {
   float a[16];
 #pragma unroll
@@ -342,6 +356,19 @@ __device__ __forceinline__ float tree_sum32(const float* v) {
     for (int q = 0; q < w; ++q) a[q] = a[q] + a[q + w];
   return a[0];
 }
+
+// ---------------------------------------------------------------------------
+// Warp roles (both passes): warps 0..7 consume TMEM (warp w reads lanes
+// 32 (w mod 4) .. +31, the access rule of tcgen05.ld, and the column half
+// w / 4 of each 128-column tile); warps 8..9 produce the pixel-side
+// operands of upcoming tiles (two pixels per thread); warp 10 allocates
+// TMEM and one of its threads issues every MMA.  Eleven warps keep at most
+// three on each SM sub-partition, which leaves 168 registers per thread.  Producers run ahead of the
+// consumers by the number of operand stages, so their global loads and
+// feature arithmetic overlap the consumers' work.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_consumer(int warp) { return warp < 8; }
+__device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp < kTcMmaWarp; }
 
 // ---------------------------------------------------------------------------
 // Pass 1: log2 S(x) per pixel and objective partials.
@@ -366,9 +393,11 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   uint8_t* sA = smem + (size_t)Npad * kRowBytes;                 // 2 stages x 128 x KT
   float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Npad centre logits
   float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Npad);   // 2 stages x 128 (max, sum) of half 1
-  float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);         // 2 stages x 128 label logits
-  __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_d_full[kP1Bufs],
-      bar_d_empty[kP1Bufs], bar_drain, bar_part_full[2], bar_part_free[2], bar_off_free[2];
+  float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);        // 2 stages x 128 starting max
+  float* sLGv = sLG + 2 * 128;                                   // 2 stages x 128 label logits
+  long long* sJ = reinterpret_cast<long long*>(sLGv + 2 * 128);  // 2 stages x 128 pixel indices
+  __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_off_free[2], bar_d_full[kP1Bufs],
+      bar_d_empty[kP1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ double sred[kTcThreads / 32];
@@ -380,30 +409,28 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&bar_a_full[s], kTcEpiThreads);
+      mbar_init(&bar_a_full[s], kTcProducers);
       mbar_init(&bar_a_empty[s], 1);
+      mbar_init(&bar_off_free[s], kTcConsumers);
+      mbar_init(&bar_part_full[s], 128);
+      mbar_init(&bar_part_free[s], 128);
     }
     for (int b = 0; b < kP1Bufs; ++b) {
       mbar_init(&bar_d_full[b], 1);
-      mbar_init(&bar_d_empty[b], kTcEpiThreads);
+      mbar_init(&bar_d_empty[b], kTcConsumers);
     }
     mbar_init(&bar_drain, 1);
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&bar_part_full[s], 128);  // second warpgroup has written its (max, sum)
-      mbar_init(&bar_part_free[s], 128);  // first warpgroup has read them
-      mbar_init(&bar_off_free[s], kTcEpiThreads);  // every epilogue thread is done with stage s
-    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) tmem_alloc(&tmem_slot, kTcCols);
+  if (warp == kTcMmaWarp) tmem_alloc(&tmem_slot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
   double racc = 0.0;
-  if (warp == 8) {
-    if (tid == kTcMmaTid) {
+  if (warp == kTcMmaWarp) {
+    if (tid == kTcMmaWarp * 32) {
       // parameter image: one bulk copy per 32 KiB
       const uint32_t total = (uint32_t)Npad * kRowBytes;
       mbar_arrive_expect_tx(&bar_theta, total);
@@ -444,71 +471,54 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       mbar_wait_drain(&bar_drain, 0);
     }
     __syncwarp();
-  } else {
-    const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
-    const int row = quad * 32 + lane;  // pixel row of the tile == TMEM lane
-    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    float lG_next = 0.f;
-    int64_t j_next = -1;
-    // the operand row of pixel `tid` (first warpgroup) and the centre
-    // logits of every grain (all epilogue threads) for tile t, stage s
-    auto produce = [&](int64_t t, int s, int use) -> bool {
-      // stage s is free once the MMAs read its operand rows and every
-      // epilogue thread finished with its centre logits
-      if (use >= 1 && !mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status)) return false;
-      if (use >= 1 && !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)) return false;
+  } else if (is_producer(warp)) {
+    const int p0 = tid - kTcConsumers;  // pixel rows p0 and p0 + 64 of the tile
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+      const int s = it & 1, use = it >> 1;
+      if (use >= 1 && (!mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status) ||
+                       !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)))
+        break;
       float c[DIM], ec[K];
-      const int64_t j = tile_pixel<DIM>(g, tm, t, tid & 127, c);
-      legendre_features<DIM, D>(c, ec);
-      if (tid < 128) {
+      for (int p = p0; p < kTcPixTile; p += kTcProducers) {
         float x[DIM], eta[K];
-        if (j >= 0) {
-          pixel_coords<DIM>(g, j, x);
-        } else {
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) x[a] = c[a];
-        }
+        const int64_t j = tile_pixel<DIM>(g, tm, t, p, x, c);
+        legendre_features<DIM, D>(c, ec);
         legendre_features<DIM, D>(x, eta);
         float de[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
-        store_eta_row<K, KW, KS>(sA + s * kTileBytes, tid, de);
-        j_next = j;
-        lG_next = 0.f;
-        float start = -INFINITY;
+        store_eta_row<K, KW, KS>(sA + s * kTileBytes, p, de);
+        float start = -INFINITY, lg = 0.f;
         if (j >= 0) {
           const int G = labels[j];
           if ((unsigned)G < (unsigned)N) {
             const float* rowp = th32 + (int64_t)G * KP32;
-            lG_next = dot_f<K>(rowp, ec) + dot_f<K>(rowp, de);
-            start = lG_next;
+            lg = dot_f<K>(rowp, ec) + dot_f<K>(rowp, de);
+            start = lg;
           } else {
-            lG_next = NAN;
+            lg = NAN;
           }
         }
-        sLG[s * 128 + tid] = start;
+        sLG[s * 128 + p] = start;
+        sLGv[s * 128 + p] = lg;
+        sJ[s * 128 + p] = (long long)j;
       }
-      for (int i = tid; i < Npad; i += kTcEpiThreads)
+      for (int i = p0; i < Npad; i += kTcProducers)
         sOff[s * Npad + i] = i < N ? dot_f<K>(th32 + (int64_t)i * KP32, ec) : 0.f;
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
-      return true;
-    };
+    }
+  } else {
+    const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
+    const int row = quad * 32 + lane;  // pixel row of the tile == TMEM lane
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     int it = 0;
-    int64_t t = blockIdx.x;
-    bool ok = t < n_tiles ? produce(t, 0, 0) : true;
     int64_t c = 0;
-    for (; ok && t < n_tiles; t += gridDim.x, ++it) {
-      const int64_t j = j_next;
-      const float lG = lG_next;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
       const int s = it & 1;
-      const int64_t tn = t + gridDim.x;
-      if (tn < n_tiles) {
-        ok = produce(tn, (it + 1) & 1, (it + 1) >> 1);
-        if (!ok) break;
-      }
-      // the stage's centre and label logits were written by other epilogue
-      // threads: acquire them through the stage's full barrier
+      // the stage's operands and per-row values come from the producers
       ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
       if (!ok) break;
       // the running max starts at the label logit (a lower bound of the max,
@@ -583,12 +593,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         }
         const float2 o = sPart[s * 128 + row];
         mbar_arrive(&bar_part_free[s]);
+        const int64_t j = sJ[s * 128 + row];
         if (j >= 0) {
           const float mm = fmaxf(m, o.x);
           const float sum = ssum * Arith<float>::ex(m - mm) + o.y * Arith<float>::ex(o.x - mm);
           const float lse = mm + Arith<float>::lg(sum);
           lse_out[j] = lse;
-          racc += (double)(lG - lse) * Arith<float>::to_nat;
+          racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
         }
       }
       mbar_arrive(&bar_off_free[s]);
@@ -612,7 +623,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     if (abort_flag) sum = NAN;
     obj_part[blockIdx.x] = sum;
   }
-  if (warp == 8) {
+  if (warp == kTcMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTcCols);
   }
@@ -623,13 +634,12 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
 // NB pixel-operand stages and NA gradient-operand stages (2 when shared
 // memory holds them, else 1); with NB = 2 the MMA warp issues the logits of
 // tile t+1 before the gradient of tile t, so the tensor cores always have
-// the next tile's logits ready when the epilogue finishes a tile.
+// the next tile's logits ready when the consumers finish a tile.
 // ---------------------------------------------------------------------------
 template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const uint8_t* __restrict__ img,
-           const float* __restrict__ th32, const float* __restrict__ lse, int64_t tiles_per_chunk,
-           double* __restrict__ part, int* __restrict__ status) {
+k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const float* __restrict__ th32,
+           const float* __restrict__ lse, int64_t tiles_per_chunk, double* __restrict__ part, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * KS;                     // logits operands
@@ -651,9 +661,8 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
   uint8_t* sB = sA + kABytes;                   // NB stages of eta rows
   uint8_t* sB2 = sB + NB * kBBytes;             // NB stages of eta^T
   uint8_t* sA2 = sB2 + NB * kB2Bytes;           // NA stages of c
-  float* sLse = reinterpret_cast<float*>(sA2 + NA * kA2Bytes);    // [NB][128]
-  int* sLab = reinterpret_cast<int*>(sLse + NB * kTcPixTile);      // [NB][128]
-  float* sCen = reinterpret_cast<float*>(sLab + NB * kTcPixTile);  // [NB][4] tile centres
+  float* sLse = reinterpret_cast<float*>(sA2 + NA * kA2Bytes);     // [NB][128]
+  float* sCen = sLse + NB * kTcPixTile;                             // [NB][4] tile centres
   __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[2], bar_d1_empty[2],
       bar_a2_full[NA], bar_a2_empty[NA], bar_d2_done;
   __shared__ uint32_t tmem_slot;
@@ -668,28 +677,28 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < NB; ++s) {
-      mbar_init(&bar_b_full[s], kTcEpiThreads);
+      mbar_init(&bar_b_full[s], kTcProducers);
       mbar_init(&bar_b_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bar_d1_full[b], 1);
-      mbar_init(&bar_d1_empty[b], kTcEpiThreads);
+      mbar_init(&bar_d1_empty[b], kTcConsumers);
     }
     for (int a = 0; a < NA; ++a) {
-      mbar_init(&bar_a2_full[a], kTcEpiThreads);
+      mbar_init(&bar_a2_full[a], kTcConsumers);
       mbar_init(&bar_a2_empty[a], 1);
     }
     mbar_init(&bar_d2_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) tmem_alloc(&tmem_slot, kTcCols);
+  if (warp == kTcMmaWarp) tmem_alloc(&tmem_slot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 8) {
-    if (tid == kTcMmaTid) {
+  if (warp == kTcMmaWarp) {
+    if (tid == kTcMmaWarp * 32) {
       mbar_arrive_expect_tx(&bar_theta, kABytes);
       bulk_g2s(sA, img + (size_t)gb * kABytes, kABytes, &bar_theta);
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
@@ -744,6 +753,41 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
       mbar_wait_drain(&bar_d2_done, 0);
     }
     __syncwarp();
+  } else if (is_producer(warp)) {
+    // pixel operands of every tile: the logit operand rows, the transposed
+    // gradient operand, log2 S of the pixels and the tile centre
+    const int p0 = tid - kTcConsumers;
+    for (int t = 0; t < n_pt; ++t) {
+      const int s = t % NB;
+      if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
+      for (int p = p0; p < kTcPixTile; p += kTcProducers) {
+      float x[DIM], c[DIM], eta[K], ec[K];
+      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, p, x, c);
+      const bool vj = j >= 0;
+      const float lsev = vj ? lse[j] : INFINITY;
+      legendre_features<DIM, D>(c, ec);
+      legendre_features<DIM, D>(x, eta);
+      float de[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
+      store_eta_row<K, KW, KS>(sB + s * kBBytes, p, de);
+      uint8_t* b2 = sB2 + s * kB2Bytes;
+#pragma unroll
+      for (int k = 0; k < KW; ++k) {
+        const float v = (k < K && vj) ? eta[k] : 0.f;
+        const uint16_t h = bf16_bits(v);
+        *reinterpret_cast<uint16_t*>(b2 + kmaj(k, p, kTcPixTile)) = h;
+        if (GT == 2) *reinterpret_cast<uint16_t*>(b2 + kB2Term + kmaj(k, p, kTcPixTile)) = bf16_bits(v - bf16_val(h));
+      }
+      sLse[s * kTcPixTile + p] = lsev;
+      if (p == 0) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) sCen[s * 4 + a] = c[a];
+      }
+      }
+      fence_proxy_async();
+      mbar_arrive(&bar_b_full[s]);
+    }
   } else {
     const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
     const int gr = quad * 32 + lane;        // grain row of the block == TMEM lane
@@ -752,50 +796,6 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
     float th[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) th[k] = i < N ? th32[(int64_t)i * KP32 + k] : 0.f;
-    // pixel operands of tile t: the first warpgroup writes the logit operand
-    // rows, the second the transposed gradient operand
-    auto produce = [&](int t, int s) -> bool {
-      if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status))
-        return false;
-      const int p = tid & 127;
-      float c[DIM], ec[K], eta[K];
-      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, p, c);
-      legendre_features<DIM, D>(c, ec);
-      const bool vj = j >= 0;
-      if (vj) {
-        float x[DIM];
-        pixel_coords<DIM>(g, j, x);
-        legendre_features<DIM, D>(x, eta);
-      } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k) eta[k] = ec[k];
-      }
-      if (tid < 128) {
-        float de[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
-        store_eta_row<K, KW, KS>(sB + s * kBBytes, p, de);
-        sLse[s * kTcPixTile + p] = vj ? lse[j] : INFINITY;
-        if (p == 0) {
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) sCen[s * 4 + a] = c[a];
-        }
-      } else {
-        // eta^T (rows = features, K = pixels): hi and lo terms; zero for
-        // pixels outside the set
-        uint8_t* b2 = sB2 + s * kB2Bytes;
-#pragma unroll
-        for (int k = 0; k < KW; ++k) {
-          const float v = (k < K && vj) ? eta[k] : 0.f;
-          const uint16_t h = bf16_bits(v);
-          *reinterpret_cast<uint16_t*>(b2 + kmaj(k, p, kTcPixTile)) = h;
-          if (GT == 2) *reinterpret_cast<uint16_t*>(b2 + kB2Term + kmaj(k, p, kTcPixTile)) = bf16_bits(v - bf16_val(h));
-        }
-      }
-      fence_proxy_async();
-      mbar_arrive(&bar_b_full[s]);
-      return true;
-    };
     // logits of tile t+1 are loaded from TMEM while tile t is processed
     // (NB == 2: the MMA warp issues them before the gradient of tile t)
     uint32_t n0[32], n1[32];
@@ -810,11 +810,12 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
       loaded = true;
       return true;
     };
-    auto consume = [&](int t) -> bool {
+    bool ok = true;
+    for (int t = 0; ok && t < n_pt; ++t) {
       const int s = t % NB, b1 = t & 1, a = t % NA;
-      // sLse and sCen of the stage were written by other epilogue threads
-      if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) return false;
-      if (!loaded && !load_logits(t)) return false;
+      // sLse and sCen of the stage were written by the producers
+      if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) { ok = false; break; }
+      if (!loaded && !load_logits(t)) { ok = false; break; }
       tmem_wait_ld();
       loaded = false;
       tc_fence_before();
@@ -825,15 +826,17 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
         r0[q] = n0[q];
         r1[q] = n1[q];
       }
-      if (NB == 2 && t + 1 < n_pt && !load_logits(t + 1)) return false;
+      if (NB == 2 && t + 1 < n_pt && !load_logits(t + 1)) { ok = false; break; }
       // this grain's centre logit for the tile
       float c[DIM], ec[K];
 #pragma unroll
       for (int q = 0; q < DIM; ++q) c[q] = sCen[s * 4 + q];
       legendre_features<DIM, D>(c, ec);
       const float off = dot_f<K>(th, ec);
-      if (t >= NA && !mbar_wait_warp(&bar_a2_empty[a], (uint32_t)(((t / NA) - 1) & 1), &abort_flag, status))
-        return false;
+      if (t >= NA && !mbar_wait_warp(&bar_a2_empty[a], (uint32_t)(((t / NA) - 1) & 1), &abort_flag, status)) {
+        ok = false;
+        break;
+      }
       const float* ls = sLse + s * kTcPixTile + half * 64;
       uint8_t* a2 = sA2 + a * kA2Bytes;
 #pragma unroll
@@ -874,17 +877,6 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
       }
       fence_proxy_async();
       mbar_arrive(&bar_a2_full[a]);
-      return true;
-    };
-    bool ok = n_pt > 0 ? produce(0, 0) : true;
-    for (int t = 0; ok && t < n_pt; ++t) {
-      if (NB == 2) {
-        if (t + 1 < n_pt) ok = produce(t + 1, (t + 1) % NB);
-        if (ok) ok = consume(t);
-      } else {
-        ok = consume(t);
-        if (ok && t + 1 < n_pt) ok = produce(t + 1, 0);
-      }
     }
     tmem_wait_ld();  // a prefetched load may be outstanding after an abort
     // chunk result: D2 row of this grain (first warpgroup)
@@ -911,7 +903,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const 
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == kTcMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTcCols);
   }
@@ -1009,17 +1001,19 @@ __global__ void k_selftest_timeout(uint64_t limit_ns, int* __restrict__ status) 
 // ---------------------------------------------------------------------------
 template <int DIM>
 TileMap make_tiles(const Geom& g) {
-  TileMap tm{1, 1, 1, 0};
+  TileMap tm{1, 1, 1, 0, 1.0, 1.0, 1.0};
   if (g.coords) {
-    tm.ntx = (g.P + kTcPixTile - 1) / kTcPixTile;
-    tm.n_tiles = tm.ntx;
+    tm.n_tiles = (g.P + kTcPixTile - 1) / kTcPixTile;
     return tm;
   }
   using TS = TileShape<DIM>;
-  tm.ntx = (g.n0 + TS::X - 1) / TS::X;
-  tm.nty = (g.n1 + TS::Y - 1) / TS::Y;
-  tm.ntz = DIM == 3 ? (g.n2 + TS::Z - 1) / TS::Z : 1;
-  tm.n_tiles = tm.ntx * tm.nty * tm.ntz;
+  tm.ntx = (int)((g.n0 + TS::X - 1) / TS::X);
+  tm.nty = (int)((g.n1 + TS::Y - 1) / TS::Y);
+  tm.ntz = DIM == 3 ? (int)((g.n2 + TS::Z - 1) / TS::Z) : 1;
+  tm.n_tiles = (int64_t)tm.ntx * tm.nty * tm.ntz;
+  tm.inv0 = 1.0 / (double)g.n0;
+  tm.inv1 = 1.0 / (double)g.n1;
+  tm.inv2 = 1.0 / (double)g.n2;
   return tm;
 }
 
@@ -1034,12 +1028,14 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t P = c.g.P;
   const int Npad = (N + 127) / 128 * 128;
   const size_t row_bytes = (size_t)KT * 2;
+  // image, 2 operand stages, 2 x centre logits, 2 x (max, sum), 2 x start,
+  // 2 x label logit, 2 x pixel index
   const size_t smem1 = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
-                       2 * kTcPixTile * 8 + 2 * kTcPixTile * 4;
+                       2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 + 2 * kTcPixTile * 8;
   constexpr size_t kCap = 220 * 1024;
   // pass-2 stages: two of each when they fit, else one
   constexpr size_t kS2Fixed = (size_t)128 * KT * 2;
-  constexpr size_t kS2PerB = (size_t)kTcPixTile * KT * 2 + (size_t)GT * KW * kTcPixTile * 2 + kTcPixTile * 8 + 16;
+  constexpr size_t kS2PerB = (size_t)kTcPixTile * KT * 2 + (size_t)GT * KW * kTcPixTile * 2 + kTcPixTile * 4 + 16;
   constexpr size_t kS2PerA = (size_t)GT * 128 * kTcPixTile * 2;
   constexpr int NB = kS2Fixed + 2 * kS2PerB + 2 * kS2PerA <= kCap ? 2 : (kS2Fixed + 2 * kS2PerB + kS2PerA <= kCap ? 2 : 1);
   constexpr int NA = kS2Fixed + 2 * kS2PerB + 2 * kS2PerA <= kCap ? 2 : 1;
@@ -1099,7 +1095,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
       return PD_ECUDA;
     dim3 grid2(nch_eff, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kTcThreads, smem2_req, st>>>(c.g, tm, c.labels, N, img, th32, lse, tpc, part, status));
+             k2<<<grid2, kTcThreads, smem2_req, st>>>(c.g, tm, N, img, th32, lse, tpc, part, status));
   }
   if (c.obj) PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, grid1, 1.0 / (double)P, c.obj));
   if (c.grad) {
