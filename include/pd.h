@@ -71,6 +71,11 @@ extern "C" {
 #define PD_BF16X3 3 /* as PD_BF16 with every operand split into three bf16
                       terms (hi+mid+lo), which recovers float-level accuracy
                       on the tensor cores                                     */
+/* The tensor-core precisions serve the objective and gradient (not the HVP)
+ * for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid sides <= 2^23, and keep
+ * every grain's parameters resident in one SM's shared memory: about
+ * 104 bytes a grain (rounded up to 128 grains) at K <= 16 in PD_BF16X3,
+ * which allows N <= 1792; other combinations return PD_ENOTSUP.           */
 
 /* ---- supported sizes --------------------------------------------------- */
 #define PD_MAX_DEGREE_2D 7

@@ -19,20 +19,24 @@
 //       TMEM; the epilogue warps read their pixel row of logits and keep an
 //       online log-sum-exp; out: log2 S(x) per pixel and per-CTA objective
 //       partials.
-// pass 2  (CTA = 128 grains x a chunk of pixels)
+// pass 2  (CTA = 128 grains x a run of pixel tiles)
 //   D1 = theta_block (128 grains x K) . eta(tile)^T (128 pixels): the
 //       logits transposed, so that a thread owns one grain's row;
-//   the thread forms c = delta_{i G(x)} - ex2(l - log2 S(x)) for its grain
-//       and writes it as the A operand (grains x pixels, K-major);
+//   the thread forms c = -ex2(l - log2 S(x)) = -p_i(x) for its grain and
+//       writes it as the A operand (grains x pixels, K-major);
 //   D2 += C (128 grains x 128 pixels) . eta(tile) (128 pixels x K): the
-//       gradient contraction, accumulated in TMEM over the chunk, then
-//       written as one double partial per grain and chunk.
+//       probability part of the gradient contraction, accumulated in TMEM
+//       over a chunk of tiles, then written as one double partial per
+//       grain and chunk.  The label part sum_{x in G_i} eta(x) comes from
+//       a separate pass over the pixels (k_tc_label_moments).
 //
 // PD_BF16X3 splits every operand into three bf16 terms (hi + mid + lo,
 // about 24 significant bits) and forms the six products whose size is at
 // least 2^-16 of the leading one (hh, hm, mh, hl, mm, lh), which gives
 // float-level logits; the gradient uses two-term splits (hh, lh, hl).
-// PD_BF16 uses one term everywhere.
+// PD_BF16 uses one term everywhere.  An operand row stores each term once,
+// as KW-column slices side by side; a product is a run of MMAs whose two
+// descriptors start at the slices of its terms.
 //
 // Operands use the canonical K-major layout without swizzle: 8-row x
 // 16-byte core matrices, adjacent along K at 128 bytes (LBO) and along the
@@ -84,6 +88,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t byte
                : "r"(smem_addr(b)), "r"(bytes)
                : "memory");
   (void)state;
+}
+// Non-blocking probe of the phase (test_wait never suspends the thread).
+__device__ __forceinline__ bool mbar_peek(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
 __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   uint32_t ok;
@@ -186,58 +200,76 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 // Byte offset of element (row r, column k) of a K-major no-swizzle operand
-// whose rows are KT elements wide.
-__host__ __device__ constexpr uint32_t kmaj(int r, int k, int KT) {
-  return (uint32_t)((r >> 3) * (KT * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+// whose core matrices lie lbo bytes apart along K and sbo bytes apart along
+// the rows.
+__host__ __device__ constexpr uint32_t kmaj_s(int r, int k, uint32_t lbo, uint32_t sbo) {
+  return (uint32_t)((r >> 3) * sbo + (k >> 3) * lbo + (r & 7) * 16 + (k & 7) * 2);
 }
+// The dense case: rows KT elements wide.
+__host__ __device__ constexpr uint32_t kmaj(int r, int k, int KT) { return kmaj_s(r, k, 128u, (uint32_t)KT * 16u); }
 
-__device__ __forceinline__ uint16_t bf16_bits(float v) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-}
-__device__ __forceinline__ float bf16_val(uint16_t b) {
-  return __bfloat162float(__ushort_as_bfloat16(b));
-}
 
-// Term split of the operands.  Slice s of a BF16X3 operand holds, for the
-// parameters (theta side), term kThetaTerm[s] and, for the features, term
-// kEtaTerm[s]: products hh, hm, mh, hl, mm, lh.
+// Term split of the operands.  KS is the number of products per logit (1
+// for PD_BF16, 6 for PD_BF16X3); n_terms(KS) the bf16 terms stored per
+// value.  Product s pairs parameter term theta_term(s) with feature term
+// eta_term(s): hh, hm, mh, hl, mm, lh.
+__host__ __device__ constexpr int n_terms(int KS) { return KS == 1 ? 1 : 3; }
 __host__ __device__ constexpr int theta_term(int s) { return s == 2 || s == 4 ? 1 : (s == 5 ? 2 : 0); }
 __host__ __device__ constexpr int eta_term(int s) { return s == 1 || s == 4 ? 1 : (s == 3 ? 2 : 0); }
 
-// Writes the KS slices of a feature row (pixel r) into a K-major operand.
-template <int K, int KW, int KS>
-__device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float* eta) {
-  constexpr int KT = KW * KS;
-  uint16_t parts[3][KW];
+// The KS products of a logit chain: MMAs of K = 16 whose A and B
+// descriptors start at the term slices of the two operands (rows of KT
+// columns: slice t at column t*KW).  kind::f16, M = 128, N from idesc.
+template <int KS, int KW>
+__device__ __forceinline__ void mma_terms(uint32_t d, uint32_t aaddr, uint32_t a_sbo, bool a_theta, uint32_t baddr,
+                                          uint32_t b_sbo, uint32_t idesc) {
+#pragma unroll 1
+  for (int s = 0; s < KS; ++s) {
+    const int ta = KS == 1 ? 0 : (a_theta ? theta_term(s) : eta_term(s));
+    const int tb = KS == 1 ? 0 : (a_theta ? eta_term(s) : theta_term(s));
 #pragma unroll
-  for (int k = 0; k < KW; ++k) {
-    const float v = k < K ? eta[k] : 0.f;
-    const uint16_t h = bf16_bits(v);
-    const float r1 = v - bf16_val(h);
-    const uint16_t m = bf16_bits(r1);
-    const float r2 = r1 - bf16_val(m);
-    parts[0][k] = h;
-    parts[1][k] = m;
-    parts[2][k] = bf16_bits(r2);
+    for (int q = 0; q < KW / 16; ++q) {
+      const uint64_t ad = smem_desc(aaddr + (uint32_t)(ta * KW * 16 + q * 256), 128, a_sbo);
+      const uint64_t bd = smem_desc(baddr + (uint32_t)(tb * KW * 16 + q * 256), 128, b_sbo);
+      mma_bf16(d, ad, bd, idesc, (s > 0 || q > 0) ? 1u : 0u);
+    }
+  }
+}
+
+// Writes the terms of a feature row (pixel r) into a K-major operand.
+template <int K, int KW, int KS, uint32_t SBO = (uint32_t)KW * n_terms(KS) * 16>
+__device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float* eta) {
+  // hi, mid, lo bf16 terms (round to nearest, each of the remainder of the
+  // previous ones), two adjacent columns per 32-bit word
+  constexpr int NT = n_terms(KS);
+  uint32_t w[NT][KW / 2];
+#pragma unroll
+  for (int k = 0; k < KW; k += 2) {
+    float v0 = k < K ? eta[k] : 0.f, v1 = k + 1 < K ? eta[k + 1] : 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      w[t][k >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+      if (t + 1 < NT) {
+        const float2 f = __bfloat1622float2(h);
+        v0 -= f.x;
+        v1 -= f.y;
+      }
+    }
   }
 #pragma unroll
-  for (int s = 0; s < KS; ++s) {
-    const int t = KS == 1 ? 0 : eta_term(s);
+  for (int t = 0; t < NT; ++t) {
 #pragma unroll
     for (int k8 = 0; k8 < KW; k8 += 8) {
-      uint4 v;
-      v.x = (uint32_t)parts[t][k8 + 0] | ((uint32_t)parts[t][k8 + 1] << 16);
-      v.y = (uint32_t)parts[t][k8 + 2] | ((uint32_t)parts[t][k8 + 3] << 16);
-      v.z = (uint32_t)parts[t][k8 + 4] | ((uint32_t)parts[t][k8 + 5] << 16);
-      v.w = (uint32_t)parts[t][k8 + 6] | ((uint32_t)parts[t][k8 + 7] << 16);
-      *reinterpret_cast<uint4*>(base + kmaj(r, s * KW + k8, KT)) = v;
+      const uint4 v = make_uint4(w[t][k8 / 2], w[t][k8 / 2 + 1], w[t][k8 / 2 + 2], w[t][k8 / 2 + 3]);
+      *reinterpret_cast<uint4*>(base + kmaj_s(r, t * KW + k8, 128u, SBO)) = v;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Parameter images: rows = grains (padded to Npad with zero rows), K-major
-// no-swizzle, KS slices of KW columns; plus the float copy used for the
+// no-swizzle, one slice of KW columns per term; plus the float copy used for the
 // label logit of the objective.
 // ---------------------------------------------------------------------------
 template <int KS>
@@ -253,11 +285,8 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
   const double r2 = r1 - (double)__bfloat162float(__ushort_as_bfloat16(m));
   const uint16_t l = __bfloat16_as_ushort(__double2bfloat16(r2));
   const uint16_t parts[3] = {h, m, l};
-  const int KT = KW * KS;
-  for (int s = 0; s < KS; ++s) {
-    const int term = KS == 1 ? 0 : theta_term(s);
-    *reinterpret_cast<uint16_t*>(img + kmaj(r, s * KW + k, KT)) = parts[term];
-  }
+  const int KT = KW * n_terms(KS);
+  for (int t = 0; t < n_terms(KS); ++t) *reinterpret_cast<uint16_t*>(img + kmaj(r, t * KW + k, KT)) = parts[t];
   if (r < N && k < KP32) th32[(int64_t)r * KP32 + k] = k < K ? (float)t : 0.f;
 }
 
@@ -275,7 +304,8 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
 struct TileMap {
   int ntx, nty, ntz;      // tiles per axis (structured grids)
   int64_t n_tiles;
-  double inv0, inv1, inv2;  // 1 / n_a
+  int n0, n1, n2;         // grid sides
+  float f0, f1, f2;       // 1 / n_a rounded to float
 };
 
 template <int DIM>
@@ -287,7 +317,10 @@ struct TileShape {
 
 // Pixel index of row r of tile t (or -1 outside the pixel set), its
 // coordinates x and the coordinates of the tile centre c.  Only 32-bit
-// divisions by the (uniform) tile counts; pixel centres from reciprocals.
+// integer arithmetic and fp32: a centre -1 + (2k+1)/n is formed as the exact
+// integer 2k+1-n times the float 1/n (exact when n is a power of two, else
+// within an ulp of the rounded value); both passes use this same function,
+// so the log-sum-exp of pass 1 belongs to the very points of pass 2.
 template <int DIM>
 __device__ __forceinline__ int64_t tile_pixel(const Geom& g, const TileMap& tm, int64_t t, int r, float* x,
                                               float* c) {
@@ -309,23 +342,23 @@ __device__ __forceinline__ int64_t tile_pixel(const Geom& g, const TileMap& tm, 
   const unsigned tt = (unsigned)t;
   const unsigned tx = tt % (unsigned)tm.ntx;
   const unsigned rest = tt / (unsigned)tm.ntx;
-  const unsigned ty = rest % (unsigned)tm.nty;
-  const unsigned tz = rest / (unsigned)tm.nty;
-  const int64_t px = (int64_t)tx * TS::X + (r % TS::X);
-  const int64_t py = (int64_t)ty * TS::Y + ((r / TS::X) % TS::Y);
-  const int64_t pz = (int64_t)tz * TS::Z + (r / (TS::X * TS::Y));
-  c[0] = (float)fma(2.0 * (double)(tx * TS::X + TS::X / 2) + 1.0, tm.inv0, -1.0);
-  c[1] = (float)fma(2.0 * (double)(ty * TS::Y + TS::Y / 2) + 1.0, tm.inv1, -1.0);
-  if (DIM == 3) c[2] = (float)fma(2.0 * (double)(tz * TS::Z + TS::Z / 2) + 1.0, tm.inv2, -1.0);
-  x[0] = (float)fma(2.0 * (double)px + 1.0, tm.inv0, -1.0);
-  x[1] = (float)fma(2.0 * (double)py + 1.0, tm.inv1, -1.0);
-  if (DIM == 3) x[2] = (float)fma(2.0 * (double)pz + 1.0, tm.inv2, -1.0);
-  if (px >= g.n0 || py >= g.n1 || (DIM == 3 && pz >= g.n2)) {
+  const int ty = (int)(rest % (unsigned)tm.nty);
+  const int tz = (int)(rest / (unsigned)tm.nty);
+  const int px = (int)tx * TS::X + (r % TS::X);
+  const int py = ty * TS::Y + ((r / TS::X) % TS::Y);
+  const int pz = tz * TS::Z + (r / (TS::X * TS::Y));
+  c[0] = (float)(2 * ((int)tx * TS::X + TS::X / 2) + 1 - tm.n0) * tm.f0;
+  c[1] = (float)(2 * (ty * TS::Y + TS::Y / 2) + 1 - tm.n1) * tm.f1;
+  if (DIM == 3) c[2] = (float)(2 * (tz * TS::Z + TS::Z / 2) + 1 - tm.n2) * tm.f2;
+  x[0] = (float)(2 * px + 1 - tm.n0) * tm.f0;
+  x[1] = (float)(2 * py + 1 - tm.n1) * tm.f1;
+  if (DIM == 3) x[2] = (float)(2 * pz + 1 - tm.n2) * tm.f2;
+  if (px >= tm.n0 || py >= tm.n1 || (DIM == 3 && pz >= tm.n2)) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) x[a] = c[a];
     return -1;
   }
-  return DIM == 2 ? px + g.n0 * py : px + g.n0 * (py + g.n1 * pz);
+  return DIM == 2 ? px + (int64_t)tm.n0 * py : px + (int64_t)tm.n0 * (py + (int64_t)tm.n1 * pz);
 }
 
 template <int K>
@@ -382,7 +415,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
            int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
-  constexpr int KT = KW * KS;
+  constexpr int KT = KW * n_terms(KS);
   constexpr int KP32 = padded_K<float>(K);
   constexpr uint32_t kRowBytes = KT * 2;
   constexpr uint32_t kTileBytes = kTcPixTile * kRowBytes;
@@ -455,12 +488,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           }
           const uint32_t aaddr = smem_addr(sA + s * kTileBytes);
           const uint32_t baddr = smem_addr(sB + (size_t)gt * kTcGrainTile * kRowBytes);
-#pragma unroll
-          for (int q = 0; q < KT / 16; ++q) {
-            const uint64_t ad = smem_desc(aaddr + q * 256, 128, KT * 16);
-            const uint64_t bd = smem_desc(baddr + q * 256, 128, KT * 16);
-            mma_bf16(tmem + b * kTcGrainTile, ad, bd, IDESC, q > 0);
-          }
+          mma_terms<KS, KW>(tmem + b * kTcGrainTile, aaddr, KT * 16, false, baddr, KT * 16, IDESC);
           mma_commit(&bar_d_full[b]);
         }
         if (!ok) break;
@@ -630,57 +658,89 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
 }
 
 // ---------------------------------------------------------------------------
-// Pass 2: gradient partials for one grain block and one chunk of tiles.
-// NB pixel-operand stages and NA gradient-operand stages (2 when shared
-// memory holds them, else 1); with NB = 2 the MMA warp issues the logits of
-// tile t+1 before the gradient of tile t, so the tensor cores always have
-// the next tile's logits ready when the consumers finish a tile.
+// Pass 2: gradient partials of one grain block over a contiguous run of
+// tiles (one wave of CTAs per grain block).  NB pixel-operand stages (up to
+// 3) and NA gradient-operand stages (up to 2), as many as shared memory
+// holds.  Two warps issue MMAs: one the logits, as far ahead as the three
+// TMEM logit buffers and the operand stages allow, the other the gradient
+// contractions, so neither waits behind the other.  The consumers pick the
+// next tile's logits up early when they are already there.  The gradient
+// accumulates in TMEM over chunks of kP2ChunkTiles tiles (two buffers,
+// alternating), and each chunk becomes one double partial per grain.
+//
+// Shared-memory operand layouts (all K-major, no swizzle):
+//   sB   pixel rows x KT feature differences; the 8-row groups lie
+//        KT*16 + 16 bytes apart, so that the producers' stores of even and
+//        of odd rows spread over all banks;
+//   sB2  features x 128 pixels (eta transposed); the 8-pixel core matrices
+//        lie 144 bytes apart along K, so that 32 threads storing one 32-bit
+//        word (two adjacent pixels) each hit 32 different banks;
+//   sA2  grains x 128 pixels of c, dense.
 // ---------------------------------------------------------------------------
+template <int DIM, int D, int KS>
+struct Pass2Layout {
+  static constexpr int K = basis_K(DIM, D);
+  static constexpr int KW = (K + 15) / 16 * 16;
+  static constexpr int KT = KW * n_terms(KS);
+  static constexpr int GT = KS == 1 ? 1 : 2;  // gradient terms of c and eta
+  static constexpr int KE = (K + 3) / 4 * 4;  // tile-centre features per stage
+  static constexpr uint32_t kABytes = 128u * KT * 2;             // theta block
+  static constexpr uint32_t kSboB = (uint32_t)KT * 16 + 16;
+  static constexpr uint32_t kBBytes = 16 * kSboB;                // 128 pixel rows
+  static constexpr uint32_t kLbo2 = 144;
+  static constexpr uint32_t kSbo2 = 16 * kLbo2;
+  static constexpr uint32_t kB2Term = (KW / 8) * kSbo2;
+  static constexpr uint32_t kB2Bytes = GT * kB2Term;
+  static constexpr uint32_t kA2Term = 128u * kTcPixTile * 2;     // c: 128 grains x 128 pixels
+  static constexpr uint32_t kA2Bytes = GT * kA2Term;
+  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + KE * 4;
+  static constexpr size_t bytes(int nb, int na) { return kABytes + (size_t)nb * kPerB + (size_t)na * kA2Bytes; }
+};
+
+constexpr int kP2GradWarp = 11;       // pass 2: the gradient MMAs have their own issuing warp
+constexpr int kP2Threads = 12 * 32;   // three warps on every SM sub-partition
+constexpr int kP2LogitBufs = 3;       // logit tiles in flight in TMEM (3 x 128 columns)
+constexpr int kP2ChunkTiles = 32;     // tiles per gradient partial (fp32 accumulation length)
+
 template <int DIM, int D, int KS, int NB, int NA>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kP2Threads, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const float* __restrict__ th32,
-           const float* __restrict__ lse, int64_t tiles_per_chunk, double* __restrict__ part, int* __restrict__ status) {
-  constexpr int K = basis_K(DIM, D);
-  constexpr int KW = (K + 15) / 16 * 16;
-  constexpr int KT = KW * KS;                     // logits operands
+           const float* __restrict__ lse, int64_t n_chunks, double* __restrict__ part, int* __restrict__ status) {
+  using L = Pass2Layout<DIM, D, KS>;
+  constexpr int K = L::K, KW = L::KW, KT = L::KT, GT = L::GT, KE = L::KE;
   constexpr int KP32 = padded_K<float>(K);
-  constexpr int GT = KS == 1 ? 1 : 2;             // gradient terms of c and eta
-  constexpr uint32_t kRowBytes = KT * 2;
-  constexpr uint32_t kABytes = 128 * kRowBytes;   // theta block
-  constexpr uint32_t kBBytes = kTcPixTile * kRowBytes;
-  constexpr uint32_t kB2Term = KW * kTcPixTile * 2;        // eta^T term: rows KW, K = 128 pixels
-  constexpr uint32_t kB2Bytes = GT * kB2Term;
-  constexpr uint32_t kA2Term = 128 * kTcPixTile * 2;       // c term: rows 128 grains, K = 128 pixels
-  constexpr uint32_t kA2Bytes = GT * kA2Term;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
   constexpr uint32_t IDESC2 = idesc_bf16(128, KW);
-  constexpr int D2COL = 2 * kTcPixTile;  // TMEM columns: D1 [0,256) double-buffered, D2 [256, 256+KW)
+  constexpr int D2COL = kP2LogitBufs * kTcPixTile;  // TMEM: D1 ring [0, 384), D2 x 2 from 384
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;                           // theta block image
-  uint8_t* sB = sA + kABytes;                   // NB stages of eta rows
-  uint8_t* sB2 = sB + NB * kBBytes;             // NB stages of eta^T
-  uint8_t* sA2 = sB2 + NB * kB2Bytes;           // NA stages of c
-  float* sLse = reinterpret_cast<float*>(sA2 + NA * kA2Bytes);     // [NB][128]
-  float* sCen = sLse + NB * kTcPixTile;                             // [NB][4] tile centres
-  __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[2], bar_d1_empty[2],
-      bar_a2_full[NA], bar_a2_empty[NA], bar_d2_done;
+  uint8_t* sA = smem;                             // theta block image
+  uint8_t* sB = sA + L::kABytes;                  // NB stages of eta - eta(c) rows
+  uint8_t* sB2 = sB + NB * L::kBBytes;            // NB stages of eta^T
+  uint8_t* sA2 = sB2 + NB * L::kB2Bytes;          // NA stages of c
+  float* sLse = reinterpret_cast<float*>(sA2 + NA * L::kA2Bytes);  // [NB][128] log2 S of the pixels
+  float* sEc = sLse + NB * kTcPixTile;                             // [NB][KE] eta(tile centre)
+  __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[kP2LogitBufs],
+      bar_d1_empty[kP2LogitBufs], bar_a2_full[NA], bar_a2_empty[NA], bar_d2_full[2], bar_d2_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int gb = blockIdx.y;                 // grain block
-  const int64_t t_begin = (int64_t)blockIdx.x * tiles_per_chunk;
-  const int64_t t_end = min(t_begin + tiles_per_chunk, tm.n_tiles);
-  const int n_pt = (int)(t_end - t_begin);
+  const int gb = blockIdx.y;  // grain block
+  // this CTA's chunks of kP2ChunkTiles tiles, a contiguous share of the tiles
+  const int64_t c_begin = (int64_t)blockIdx.x * n_chunks / gridDim.x;
+  const int64_t c_end = (int64_t)(blockIdx.x + 1) * n_chunks / gridDim.x;
+  const int64_t t_begin = c_begin * kP2ChunkTiles;
+  const int n_pt = (int)(min(c_end * kP2ChunkTiles, tm.n_tiles) - t_begin);
+  const int n_items = (int)(c_end - c_begin);
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < NB; ++s) {
       mbar_init(&bar_b_full[s], kTcProducers);
-      mbar_init(&bar_b_empty[s], 1);
+      mbar_init(&bar_b_empty[s], 2);  // both MMA issuers are done with the stage
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kP2LogitBufs; ++b) {
       mbar_init(&bar_d1_full[b], 1);
       mbar_init(&bar_d1_empty[b], kTcConsumers);
     }
@@ -688,7 +748,11 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
       mbar_init(&bar_a2_full[a], kTcConsumers);
       mbar_init(&bar_a2_empty[a], 1);
     }
-    mbar_init(&bar_d2_done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_d2_full[b], 1);
+      mbar_init(&bar_d2_free[b], 128);
+    }
+    mbar_init(&bar_drain, 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kTcMmaWarp) tmem_alloc(&tmem_slot, kTcCols);
@@ -698,92 +762,122 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
   const uint32_t tmem = tmem_slot;
 
   if (warp == kTcMmaWarp) {
+    // logits D1(t) = theta_block . (eta - eta(c))^T, as far ahead of the
+    // consumers as the TMEM ring and the operand stages allow
     if (tid == kTcMmaWarp * 32) {
-      mbar_arrive_expect_tx(&bar_theta, kABytes);
-      bulk_g2s(sA, img + (size_t)gb * kABytes, kABytes, &bar_theta);
+      mbar_arrive_expect_tx(&bar_theta, L::kABytes);
+      bulk_g2s(sA, img + (size_t)gb * L::kABytes, L::kABytes, &bar_theta);
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
-      auto logits = [&](int t) -> bool {
-        const int s = t % NB, b1 = t & 1;
-        if (!mbar_wait(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) return false;
-        if (t >= 2 && !mbar_wait(&bar_d1_empty[b1], (uint32_t)(((t >> 1) - 1) & 1), &abort_flag, status))
-          return false;
+      for (int t = 0; ok && t < n_pt; ++t) {
+        const int s = t % NB, b1 = t % kP2LogitBufs;
+        ok = mbar_wait(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status);
+        if (ok && t >= kP2LogitBufs)
+          ok = mbar_wait(&bar_d1_empty[b1], (uint32_t)(((t / kP2LogitBufs) - 1) & 1), &abort_flag, status);
+        if (!ok) break;
         tc_fence_after();
-        const uint32_t aaddr = smem_addr(sA), baddr = smem_addr(sB + s * kBBytes);
-#pragma unroll
-        for (int q = 0; q < KT / 16; ++q)
-          mma_bf16(tmem + b1 * kTcPixTile, smem_desc(aaddr + q * 256, 128, KT * 16),
-                   smem_desc(baddr + q * 256, 128, KT * 16), IDESC1, q > 0);
+        mma_terms<KS, KW>(tmem + b1 * kTcPixTile, smem_addr(sA), KT * 16, true, smem_addr(sB + s * L::kBBytes),
+                          L::kSboB, IDESC1);
         mma_commit(&bar_d1_full[b1]);
-        return true;
-      };
-      auto grad = [&](int t) -> bool {
+        mma_commit(&bar_b_empty[s]);
+      }
+      mma_commit(&bar_drain);
+      mbar_wait_drain(&bar_drain, 0);
+    }
+    __syncwarp();
+  } else if (warp == kP2GradWarp) {
+    // gradient D2 += C . eta, products (c_h, eta_h), then (c_l, eta_h),
+    // (c_h, eta_l); one D2 accumulation per chunk, alternating between two
+    // TMEM buffers so that the consumers read one while the next fills
+    if (tid == kP2GradWarp * 32) {
+      bool ok = true;
+      for (int t = 0; ok && t < n_pt; ++t) {
         const int s = t % NB, a = t % NA;
-        if (!mbar_wait(&bar_a2_full[a], (uint32_t)((t / NA) & 1), &abort_flag, status)) return false;
+        const int u = t / kP2ChunkTiles, db = u & 1;
+        const bool first = t % kP2ChunkTiles == 0, last = t % kP2ChunkTiles == kP2ChunkTiles - 1 || t == n_pt - 1;
+        if (first && u >= 2) ok = mbar_wait(&bar_d2_free[db], (uint32_t)(((u >> 1) - 1) & 1), &abort_flag, status);
+        if (ok) ok = mbar_wait(&bar_a2_full[a], (uint32_t)((t / NA) & 1), &abort_flag, status);
+        if (!ok) break;
         tc_fence_after();
-        // D2 += C . eta: products (c_h, eta_h), then (c_l, eta_h), (c_h, eta_l)
-        const uint32_t a2 = smem_addr(sA2 + a * kA2Bytes), b2 = smem_addr(sB2 + s * kB2Bytes);
+        const uint32_t a2 = smem_addr(sA2 + a * L::kA2Bytes), b2 = smem_addr(sB2 + s * L::kB2Bytes);
         constexpr int NPROD = GT == 1 ? 1 : 3;
-#pragma unroll
+#pragma unroll 1
         for (int pr = 0; pr < NPROD; ++pr) {
           const int ct = pr == 1 ? 1 : 0, et = pr == 2 ? 1 : 0;
-#pragma unroll
+#pragma unroll 2
           for (int q = 0; q < kTcPixTile / 16; ++q) {
-            const uint64_t ad = smem_desc(a2 + ct * kA2Term + q * 256, 128, kTcPixTile * 16);
-            const uint64_t bd = smem_desc(b2 + et * kB2Term + q * 256, 128, kTcPixTile * 16);
-            mma_bf16(tmem + D2COL, ad, bd, IDESC2, (t > 0 || pr > 0 || q > 0) ? 1u : 0u);
+            const uint64_t ad = smem_desc(a2 + ct * L::kA2Term + q * 256, 128, kTcPixTile * 16);
+            const uint64_t bd = smem_desc(b2 + et * L::kB2Term + q * 2 * L::kLbo2, L::kLbo2, L::kSbo2);
+            mma_bf16(tmem + D2COL + db * KW, ad, bd, IDESC2, (!first || pr > 0 || q > 0) ? 1u : 0u);
           }
         }
         mma_commit(&bar_a2_empty[a]);
         mma_commit(&bar_b_empty[s]);
-        return true;
-      };
-      if (NB == 2) {
-        if (ok && n_pt > 0) ok = logits(0);
-        for (int t = 0; ok && t < n_pt; ++t) {
-          if (t + 1 < n_pt) ok = logits(t + 1);
-          if (ok) ok = grad(t);
-        }
-      } else {
-        for (int t = 0; ok && t < n_pt; ++t) {
-          ok = logits(t);
-          if (ok) ok = grad(t);
-        }
+        if (last) mma_commit(&bar_d2_full[db]);
       }
-      mma_commit(&bar_d2_done);
-      mbar_wait_drain(&bar_d2_done, 0);
+      mma_commit(&bar_drain);
+      mbar_wait_drain(&bar_drain, 0);
     }
     __syncwarp();
   } else if (is_producer(warp)) {
     // pixel operands of every tile: the logit operand rows, the transposed
-    // gradient operand, log2 S of the pixels and the tile centre
-    const int p0 = tid - kTcConsumers;
+    // gradient operand, log2 S of the pixels and the centre features.  A
+    // thread owns two adjacent pixels; the next tile's coordinates and
+    // log2 S are fetched while the current tile is written.
+    const int q2 = 2 * (tid - kTcConsumers);
+    float xn[2][DIM], cn[DIM], lsn[2];
+    auto fetch = [&](int t) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, q2 + u, xn[u], cn);
+        lsn[u] = j >= 0 ? lse[j] : INFINITY;
+      }
+    };
+    if (n_pt > 0) fetch(0);
     for (int t = 0; t < n_pt; ++t) {
       const int s = t % NB;
-      if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
-      for (int p = p0; p < kTcPixTile; p += kTcProducers) {
-      float x[DIM], c[DIM], eta[K], ec[K];
-      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, p, x, c);
-      const bool vj = j >= 0;
-      const float lsev = vj ? lse[j] : INFINITY;
-      legendre_features<DIM, D>(c, ec);
-      legendre_features<DIM, D>(x, eta);
-      float de[K];
+      float xc[2][DIM], cc[DIM];
 #pragma unroll
-      for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
-      store_eta_row<K, KW, KS>(sB + s * kBBytes, p, de);
-      uint8_t* b2 = sB2 + s * kB2Bytes;
+      for (int a = 0; a < DIM; ++a) {
+        xc[0][a] = xn[0][a];
+        xc[1][a] = xn[1][a];
+        cc[a] = cn[a];
+      }
+      const float2 lsc = make_float2(lsn[0], lsn[1]);
+      if (t + 1 < n_pt) fetch(t + 1);
+      if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
+      float ec[K], e0[K], e1[K];
+      legendre_features<DIM, D>(cc, ec);
+      legendre_features<DIM, D>(xc[0], e0);
+      legendre_features<DIM, D>(xc[1], e1);
+      uint8_t* bs = sB + s * L::kBBytes;
+      {
+        float de[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) de[k] = e0[k] - ec[k];
+        store_eta_row<K, KW, KS, L::kSboB>(bs, q2, de);
+#pragma unroll
+        for (int k = 0; k < K; ++k) de[k] = e1[k] - ec[k];
+        store_eta_row<K, KW, KS, L::kSboB>(bs, q2 + 1, de);
+      }
+      // eta^T: one 32-bit word holds the two pixels of a feature (pixels
+      // outside the set have c = 0, so their features need no masking)
+      uint8_t* b2 = sB2 + s * L::kB2Bytes;
 #pragma unroll
       for (int k = 0; k < KW; ++k) {
-        const float v = (k < K && vj) ? eta[k] : 0.f;
-        const uint16_t h = bf16_bits(v);
-        *reinterpret_cast<uint16_t*>(b2 + kmaj(k, p, kTcPixTile)) = h;
-        if (GT == 2) *reinterpret_cast<uint16_t*>(b2 + kB2Term + kmaj(k, p, kTcPixTile)) = bf16_bits(v - bf16_val(h));
+        const float a0 = k < K ? e0[k] : 0.f, a1 = k < K ? e1[k] : 0.f;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+        const uint32_t o = kmaj_s(k, q2, L::kLbo2, L::kSbo2);
+        *reinterpret_cast<uint32_t*>(b2 + o) = *reinterpret_cast<const uint32_t*>(&h);
+        if (GT == 2) {
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
+          *reinterpret_cast<uint32_t*>(b2 + L::kB2Term + o) = *reinterpret_cast<const uint32_t*>(&l);
+        }
       }
-      sLse[s * kTcPixTile + p] = lsev;
-      if (p == 0) {
+      *reinterpret_cast<float2*>(sLse + s * kTcPixTile + q2) = lsc;
+      if (q2 == 0) {
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) sCen[s * 4 + a] = c[a];
-      }
+        for (int k = 0; k < KE; ++k) sEc[s * KE + k] = k < K ? ec[k] : 0.f;
       }
       fence_proxy_async();
       mbar_arrive(&bar_b_full[s]);
@@ -796,108 +890,127 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
     float th[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) th[k] = i < N ? th32[(int64_t)i * KP32 + k] : 0.f;
-    // logits of tile t+1 are loaded from TMEM while tile t is processed
-    // (NB == 2: the MMA warp issues them before the gradient of tile t)
-    uint32_t n0[32], n1[32];
-    bool loaded = false;
-    auto load_logits = [&](int t) -> bool {
-      const int b1 = t & 1;
-      if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t >> 1) & 1), &abort_flag, status)) return false;
+    int n_done = 0;  // chunks whose partial this thread has written (first warpgroup)
+    // the D2 row of chunk u of this CTA: one double partial per grain
+    auto read_chunk = [&](int u) -> bool {
+      const int db = u & 1;
+      if (!mbar_wait_warp(&bar_d2_full[db], (uint32_t)((u >> 1) & 1), &abort_flag, status)) return false;
       tc_fence_after();
-      const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
-      tmem_ld32(tmem + lane_base + col, n0);
-      tmem_ld32(tmem + lane_base + col + 32, n1);
-      loaded = true;
+      uint32_t r[32];
+      if (KW == 16) {
+        tmem_ld16(tmem + lane_base + (uint32_t)(D2COL + db * KW), r);
+      } else {
+        tmem_ld32(tmem + lane_base + (uint32_t)(D2COL + db * KW), r);
+      }
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&bar_d2_free[db]);
+      if (i < N) {
+        double* row = part + ((c_begin + u) * N + i) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) row[k] = (double)__uint_as_float(r[k]);
+      }
+      n_done = u + 1;
       return true;
     };
-    bool ok = true;
-    for (int t = 0; ok && t < n_pt; ++t) {
-      const int s = t % NB, b1 = t & 1, a = t % NA;
-      // sLse and sCen of the stage were written by the producers
-      if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) { ok = false; break; }
-      if (!loaded && !load_logits(t)) { ok = false; break; }
-      tmem_wait_ld();
-      loaded = false;
-      tc_fence_before();
-      mbar_arrive(&bar_d1_empty[b1]);  // the logits are in registers: release the TMEM tile
-      uint32_t r0[32], r1[32];
+    // c = -p for 32 pixels (columns q0 .. q0+31 of this thread's half),
+    // written as hi (+ lo) bf16 pairs, one 16-byte core-matrix row per 8
+    // pixels and term
+    auto emit = [&](const uint32_t(&r)[32], const float* ls, float off, uint8_t* a2, int q0) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        r0[q] = n0[q];
-        r1[q] = n1[q];
+      for (int q8 = 0; q8 < 32; q8 += 8) {
+        const float4 va = *reinterpret_cast<const float4*>(ls + q8);
+        const float4 vb = *reinterpret_cast<const float4*>(ls + q8 + 4);
+        const float lv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          const float c0 = -Arith<float>::ex(__uint_as_float(r[q8 + u]) - (lv[u] - off));
+          const float c1 = -Arith<float>::ex(__uint_as_float(r[q8 + u + 1]) - (lv[u + 1] - off));
+          const __nv_bfloat162 h = __floats2bfloat162_rn(c0, c1);
+          hi[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+          if (GT == 2) {
+            const float2 f = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(c0 - f.x, c1 - f.y);
+            lo[u >> 1] = *reinterpret_cast<const uint32_t*>(&l);
+          }
+        }
+        const uint32_t o = kmaj(gr, q0 + q8, kTcPixTile);
+        *reinterpret_cast<uint4*>(a2 + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if (GT == 2) *reinterpret_cast<uint4*>(a2 + L::kA2Term + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
-      if (NB == 2 && t + 1 < n_pt && !load_logits(t + 1)) { ok = false; break; }
+    };
+    // the two 32-column halves of the thread's logits: the second is loaded
+    // while the first is used, and the first half of the next tile (when the
+    // tensor cores have it ready) while the second is used
+    uint32_t RA[32], RB[32];
+    bool pre = false;
+    bool ok = true;
+    for (int t = 0; t < n_pt; ++t) {
+      const int s = t % NB, b1 = t % kP2LogitBufs, a = t % NA;
+      const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
+      // sLse and sEc of the stage were written by the producers
+      if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) { ok = false; break; }
+      if (!pre) {
+        if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t / kP2LogitBufs) & 1), &abort_flag, status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        tmem_ld32(tmem + lane_base + col, RA);
+      }
+      tmem_wait_ld();
+      tmem_ld32(tmem + lane_base + col + 32, RB);
       // this grain's centre logit for the tile
-      float c[DIM], ec[K];
+      float off = 0.f;
+      {
+        const float4* ec4 = reinterpret_cast<const float4*>(sEc + s * KE);
 #pragma unroll
-      for (int q = 0; q < DIM; ++q) c[q] = sCen[s * 4 + q];
-      legendre_features<DIM, D>(c, ec);
-      const float off = dot_f<K>(th, ec);
+        for (int k4 = 0; k4 < KE / 4; ++k4) {
+          const float4 e = ec4[k4];
+          if (4 * k4 + 0 < K) off = fmaf(th[4 * k4 + 0], e.x, off);
+          if (4 * k4 + 1 < K) off = fmaf(th[4 * k4 + 1], e.y, off);
+          if (4 * k4 + 2 < K) off = fmaf(th[4 * k4 + 2], e.z, off);
+          if (4 * k4 + 3 < K) off = fmaf(th[4 * k4 + 3], e.w, off);
+        }
+      }
       if (t >= NA && !mbar_wait_warp(&bar_a2_empty[a], (uint32_t)(((t / NA) - 1) & 1), &abort_flag, status)) {
         ok = false;
         break;
       }
       const float* ls = sLse + s * kTcPixTile + half * 64;
-      uint8_t* a2 = sA2 + a * kA2Bytes;
-#pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-        const uint32_t* r = h2 ? r1 : r0;
-        uint32_t hi[16], lo[16];
-        float lsv[32];
-#pragma unroll
-        for (int q = 0; q < 32; q += 4) {
-          const float4 v4 = *reinterpret_cast<const float4*>(ls + 32 * h2 + q);
-          lsv[q] = v4.x - off;
-          lsv[q + 1] = v4.y - off;
-          lsv[q + 2] = v4.z - off;
-          lsv[q + 3] = v4.w - off;
-        }
-#pragma unroll
-        for (int q = 0; q < 32; q += 2) {
-          // c = -p; the label term delta_{i G(x)} enters through the grain
-          // moments added at the final reduction
-          const float c0 = -Arith<float>::ex(__uint_as_float(r[q]) - lsv[q]);
-          const float c1 = -Arith<float>::ex(__uint_as_float(r[q + 1]) - lsv[q + 1]);
-          const __nv_bfloat162 h = __floats2bfloat162_rn(c0, c1);
-          hi[q >> 1] = *reinterpret_cast<const uint32_t*>(&h);
-          if (GT == 2) {
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(c0 - hf.x, c1 - hf.y);
-            lo[q >> 1] = *reinterpret_cast<const uint32_t*>(&l);
-          }
-        }
-#pragma unroll
-        for (int q8 = 0; q8 < 32; q8 += 8) {
-          const uint32_t o = kmaj(gr, half * 64 + 32 * h2 + q8, kTcPixTile);
-          *reinterpret_cast<uint4*>(a2 + o) = make_uint4(hi[q8 / 2], hi[q8 / 2 + 1], hi[q8 / 2 + 2], hi[q8 / 2 + 3]);
-          if (GT == 2)
-            *reinterpret_cast<uint4*>(a2 + kA2Term + o) =
-                make_uint4(lo[q8 / 2], lo[q8 / 2 + 1], lo[q8 / 2 + 2], lo[q8 / 2 + 3]);
+      uint8_t* a2 = sA2 + a * L::kA2Bytes;
+      emit(RA, ls, off, a2, half * 64);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&bar_d1_empty[b1]);  // the tile's logits are in registers: release its TMEM columns
+      pre = false;
+      if (t + 1 < n_pt) {
+        const int bn = (t + 1) % kP2LogitBufs;
+        if (__all_sync(0xffffffffu, mbar_peek(&bar_d1_full[bn], (uint32_t)(((t + 1) / kP2LogitBufs) & 1)))) {
+          tc_fence_after();
+          tmem_ld32(tmem + lane_base + (uint32_t)(bn * kTcPixTile + half * 64), RA);
+          pre = true;
         }
       }
+      emit(RB, ls + 32, off, a2, half * 64 + 32);
       fence_proxy_async();
       mbar_arrive(&bar_a2_full[a]);
+      // the first warpgroup writes the previous chunk's partial one tile
+      // into the next chunk, when its gradient MMAs are long done
+      if (half == 0 && t > kP2ChunkTiles && t % kP2ChunkTiles == 1 && !read_chunk(t / kP2ChunkTiles - 1)) {
+        ok = false;
+        break;
+      }
     }
     tmem_wait_ld();  // a prefetched load may be outstanding after an abort
-    // chunk result: D2 row of this grain (first warpgroup)
-    if (ok && n_pt > 0) ok = mbar_wait_warp(&bar_d2_done, 0, &abort_flag, status);
     if (half == 0) {
-      if (ok && n_pt > 0) {
-        tc_fence_after();
-        uint32_t r[32];
-        if (KW == 16) {
-          tmem_ld16(tmem + lane_base + (uint32_t)D2COL, r);
-        } else {
-          tmem_ld32(tmem + lane_base + (uint32_t)D2COL, r);
-        }
-        tmem_wait_ld();
-        if (i < N) {
-#pragma unroll
-          for (int k = 0; k < K; ++k)
-            part[((int64_t)blockIdx.x * N + i) * K + k] = abort_flag ? NAN : (double)__uint_as_float(r[k]);
-        }
-      } else if (i < N) {
-        for (int k = 0; k < K; ++k) part[((int64_t)blockIdx.x * N + i) * K + k] = n_pt > 0 ? NAN : 0.0;
+      // the chunks not yet written: the last one (and, for a one-tile last
+      // chunk, the one before); after an abort the rest become NaN
+      for (int u = n_done; ok && u < n_items; ++u) ok = read_chunk(u);
+      if (!ok && i < N) {
+        for (int u = n_done; u < n_items; ++u)
+          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + i) * K + k] = NAN;
       }
     }
   }
@@ -910,44 +1023,47 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
 }
 
 // ---------------------------------------------------------------------------
-// Label term of eq. (grad): sum_{x in G_i} eta(x) per grain, fp32 features
-// summed exactly in 64-bit fixed point (order independent).
+// Label part of eq. (grad): sum_{x in G_i} eta(x) per grain, at the points
+// of the tile walk of the two passes.  A warp sums the features of each
+// group of equal labels in fp32 (a fixed butterfly order), and lane k adds
+// the group's feature-k sum to the grain's 64-bit fixed-point accumulator,
+// so that the result does not depend on the order of the atomics.
 // ---------------------------------------------------------------------------
 template <int DIM, int D>
-__global__ void k_tc_label_moments(Geom g, const int32_t* __restrict__ labels, int N, double fx_scale,
-                                   unsigned long long* __restrict__ acc) {
+__global__ void __launch_bounds__(256)
+k_tc_label_moments(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, float fx_scale,
+                   unsigned long long* __restrict__ acc) {
   constexpr int K = basis_K(DIM, D);
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = j < g.P;
-  int G = valid ? labels[j] : -1;
-  if (G < 0 || G >= N) G = -1;
-  float x[DIM], eta[K];
-  if (valid) {
-    pixel_coords<DIM>(g, j, x);
-  } else {
+  static_assert(K <= 32, "one lane per feature");
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = q / kTcPixTile;
+  int G = -1;
+  float x[DIM], c[DIM], eta[K];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) x[a] = 0.f;
+  for (int a = 0; a < DIM; ++a) x[a] = 0.f;
+  if (t < tm.n_tiles) {
+    const int64_t j = tile_pixel<DIM>(g, tm, t, (int)(q % kTcPixTile), x, c);
+    if (j >= 0) {
+      G = labels[j];
+      if ((unsigned)G >= (unsigned)N) G = -1;
+    }
   }
   legendre_features<DIM, D>(x, eta);
-  long long fx[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) fx[k] = G >= 0 ? __double2ll_rn((double)eta[k] * fx_scale) : 0ll;
-  // one warp-wide sum (and one atomic per feature) for each distinct label
-  // of the warp: spatially coherent labels make that one or two groups
-  unsigned todo = __ballot_sync(0xffffffffu, G >= 0);
   const int lane = threadIdx.x & 31;
+  unsigned todo = __ballot_sync(0xffffffffu, G >= 0);
   while (todo) {
-    const int leader = __ffs(todo) - 1;
-    const int L = __shfl_sync(0xffffffffu, G, leader);
-    const unsigned grp = __ballot_sync(0xffffffffu, G == L);
+    const int L = __shfl_sync(0xffffffffu, G, __ffs(todo) - 1);
+    const bool mine = G == L;
+    float pick = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      long long v = (G == L) ? fx[k] : 0ll;
+      float v = mine ? eta[k] : 0.f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) atomicAdd(&acc[(int64_t)L * K + k], (unsigned long long)v);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == k) pick = v;
     }
-    todo &= ~grp;
+    if (lane < K) atomicAdd(&acc[(int64_t)L * K + lane], (unsigned long long)__float2ll_rn(pick * fx_scale));
+    todo &= ~__ballot_sync(0xffffffffu, mine);
   }
 }
 
@@ -1001,7 +1117,7 @@ __global__ void k_selftest_timeout(uint64_t limit_ns, int* __restrict__ status) 
 // ---------------------------------------------------------------------------
 template <int DIM>
 TileMap make_tiles(const Geom& g) {
-  TileMap tm{1, 1, 1, 0, 1.0, 1.0, 1.0};
+  TileMap tm{1, 1, 1, 0, 1, 1, 1, 1.f, 1.f, 1.f};
   if (g.coords) {
     tm.n_tiles = (g.P + kTcPixTile - 1) / kTcPixTile;
     return tm;
@@ -1011,9 +1127,12 @@ TileMap make_tiles(const Geom& g) {
   tm.nty = (int)((g.n1 + TS::Y - 1) / TS::Y);
   tm.ntz = DIM == 3 ? (int)((g.n2 + TS::Z - 1) / TS::Z) : 1;
   tm.n_tiles = (int64_t)tm.ntx * tm.nty * tm.ntz;
-  tm.inv0 = 1.0 / (double)g.n0;
-  tm.inv1 = 1.0 / (double)g.n1;
-  tm.inv2 = 1.0 / (double)g.n2;
+  tm.n0 = (int)g.n0;
+  tm.n1 = (int)g.n1;
+  tm.n2 = (int)g.n2;
+  tm.f0 = (float)(1.0 / (double)g.n0);
+  tm.f1 = (float)(1.0 / (double)g.n1);
+  tm.f2 = (float)(1.0 / (double)g.n2);
   return tm;
 }
 
@@ -1021,9 +1140,8 @@ template <int DIM, int D, int KS>
 int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
-  constexpr int KT = KW * KS;
+  constexpr int KT = KW * n_terms(KS);
   constexpr int KP32 = padded_K<float>(K);
-  constexpr int GT = KS == 1 ? 1 : 2;
   const int N = c.N;
   const int64_t P = c.g.P;
   const int Npad = (N + 127) / 128 * 128;
@@ -1033,14 +1151,15 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const size_t smem1 = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
                        2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 + 2 * kTcPixTile * 8;
   constexpr size_t kCap = 220 * 1024;
-  // pass-2 stages: two of each when they fit, else one
-  constexpr size_t kS2Fixed = (size_t)128 * KT * 2;
-  constexpr size_t kS2PerB = (size_t)kTcPixTile * KT * 2 + (size_t)GT * KW * kTcPixTile * 2 + kTcPixTile * 4 + 16;
-  constexpr size_t kS2PerA = (size_t)GT * 128 * kTcPixTile * 2;
-  constexpr int NB = kS2Fixed + 2 * kS2PerB + 2 * kS2PerA <= kCap ? 2 : (kS2Fixed + 2 * kS2PerB + kS2PerA <= kCap ? 2 : 1);
-  constexpr int NA = kS2Fixed + 2 * kS2PerB + 2 * kS2PerA <= kCap ? 2 : 1;
-  const size_t smem2 = kS2Fixed + NB * kS2PerB + NA * kS2PerA;
+  // pass-2 stages: three pixel-operand and two gradient-operand stages
+  // when they fit, else fewer
+  using L2 = Pass2Layout<DIM, D, KS>;
+  constexpr int NB = L2::bytes(3, 2) <= kCap ? 3 : (L2::bytes(2, 1) <= kCap ? 2 : 1);
+  constexpr int NA = L2::bytes(NB, 2) <= kCap ? 2 : 1;
+  const size_t smem2 = L2::bytes(NB, NA);
   if (smem1 > kCap || smem2 > kCap) return PD_ENOTSUP;  // too many grains for a resident image
+  // pixel-centre numerators 2k+1-n stay exact integers in fp32
+  if (!c.g.coords && std::max(c.g.n0, std::max(c.g.n1, c.g.n2)) > (int64_t(1) << 23)) return PD_ENOTSUP;
   // at least 120 KiB of dynamic shared memory per CTA keeps one CTA per SM,
   // which owns all 512 TMEM columns
   const size_t smem1_req = std::max<size_t>(smem1, 120 * 1024);
@@ -1051,19 +1170,17 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t n_tiles = tm.n_tiles;
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
   const int gblocks = Npad / 128;
-  // tile chunks of pass 2: about 4 waves of CTAs, at most 32 tiles per chunk
-  int64_t nch = std::max<int64_t>((int64_t)sms * 4 / gblocks, 1);
-  nch = std::max<int64_t>(nch, (n_tiles + 31) / 32);
-  nch = std::min<int64_t>(nch, n_tiles);
-  const int64_t tpc = (n_tiles + nch - 1) / nch;
-  const int nch_eff = (int)((n_tiles + tpc - 1) / tpc);
+  // pass 2: chunks of kP2ChunkTiles tiles (one gradient partial each),
+  // shared out in contiguous runs over one wave of CTAs per grain block
+  const int64_t n_chunks = (n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles;
+  const int cpg = (int)std::min<int64_t>(n_chunks, std::max(1, sms / gblocks));
 
   Scratch sc(st);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
   float* th32 = sc.get<float>((size_t)N * KP32);
   float* lse = sc.get<float>((size_t)P);
   double* objp = sc.get<double>((size_t)grid1);
-  double* part = c.grad ? sc.get<double>((size_t)nch_eff * N * K) : nullptr;
+  double* part = c.grad ? sc.get<double>((size_t)n_chunks * N * K) : nullptr;
   unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
@@ -1085,24 +1202,26 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   // power-of-two scale that keeps P * scale below 2^62
   int bits = 0;
   while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
-  const double fx = ldexp(1.0, 62 - bits);
+  const float fx = ldexpf(1.f, 62 - bits);
   if (c.grad) {
     if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+    const int64_t nthr = n_tiles * kTcPixTile;
     PD_TIMED(st, "tc_label_moments",
-             (k_tc_label_moments<DIM, D><<<(unsigned)((P + 255) / 256), 256, 0, st>>>(c.g, c.labels, N, fx, lmom)));
+             (k_tc_label_moments<DIM, D><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
+                                                                                       lmom)));
     auto k2 = k_tc_pass2<DIM, D, KS, NB, NA>;
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
-    dim3 grid2(nch_eff, gblocks);
+    dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kTcThreads, smem2_req, st>>>(c.g, tm, N, img, th32, lse, tpc, part, status));
+             k2<<<grid2, kP2Threads, smem2_req, st>>>(c.g, tm, N, img, th32, lse, n_chunks, part, status));
   }
   if (c.obj) PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, grid1, 1.0 / (double)P, c.obj));
   if (c.grad) {
     const int64_t NK = (int64_t)N * K;
     PD_TIMED(st, "reduce_parts",
              k_tc_reduce_grad<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
-                 part, nch_eff, NK, lmom, 1.0 / fx, -1.0 / (c.eps * (double)P), c.grad));
+                 part, (int)n_chunks, NK, lmom, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), c.grad));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }
