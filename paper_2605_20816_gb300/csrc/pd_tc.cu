@@ -269,12 +269,14 @@ __device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float*
 
 // ---------------------------------------------------------------------------
 // Parameter images: rows = grains (padded to Npad with zero rows), K-major
-// no-swizzle, one slice of KW columns per term; plus the float copy used for the
+// no-swizzle, one slice of KW columns per term; plus float copies (grain
+// rows, and transposed K x Npad) used for the centre logits and the
 // label logit of the objective.
 // ---------------------------------------------------------------------------
 template <int KS>
 __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Npad, int K, int KW, double scale,
-                                 uint8_t* __restrict__ img, float* __restrict__ th32, int KP32) {
+                                 uint8_t* __restrict__ img, float* __restrict__ th32, int KP32,
+                                 float* __restrict__ th32t) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (row, k) pairs
   if (q >= (int64_t)Npad * KW) return;
   const int r = (int)(q / KW), k = (int)(q % KW);
@@ -288,6 +290,7 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
   const int KT = KW * n_terms(KS);
   for (int t = 0; t < n_terms(KS); ++t) *reinterpret_cast<uint16_t*>(img + kmaj(r, t * KW + k, KT)) = parts[t];
   if (r < N && k < KP32) th32[(int64_t)r * KP32 + k] = k < K ? (float)t : 0.f;
+  if (k < K) th32t[(int64_t)k * Npad + r] = (float)t;  // transposed, zero rows beyond N
 }
 
 // ---------------------------------------------------------------------------
@@ -411,7 +414,7 @@ constexpr int kP1Bufs = 4;  // logit tiles in flight in TMEM (4 x 128 columns)
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, const uint8_t* __restrict__ img,
-           const float* __restrict__ th32, float* __restrict__ lse_out, double* __restrict__ obj_part,
+           const float* __restrict__ th32t, int th_resident, float* __restrict__ lse_out, double* __restrict__ obj_part,
            int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
@@ -429,6 +432,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);        // 2 stages x 128 starting max
   float* sLGv = sLG + 2 * 128;                                   // 2 stages x 128 label logits
   long long* sJ = reinterpret_cast<long long*>(sLGv + 2 * 128);  // 2 stages x 128 pixel indices
+  float* sTh = reinterpret_cast<float*>(sJ + 2 * 128);           // K x Npad scaled parameters (when resident)
   __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_off_free[2], bar_d_full[kP1Bufs],
       bar_d_empty[kP1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
@@ -464,12 +468,18 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   double racc = 0.0;
   if (warp == kTcMmaWarp) {
     if (tid == kTcMmaWarp * 32) {
-      // parameter image: one bulk copy per 32 KiB
+      // parameter image (and the float parameters when they fit): one bulk
+      // copy per 32 KiB
       const uint32_t total = (uint32_t)Npad * kRowBytes;
-      mbar_arrive_expect_tx(&bar_theta, total);
+      const uint32_t th_bytes = th_resident ? (uint32_t)K * Npad * 4 : 0u;
+      mbar_arrive_expect_tx(&bar_theta, total + th_bytes);
       for (uint32_t off = 0; off < total; off += 32768u) {
         const uint32_t n = total - off < 32768u ? total - off : 32768u;
         bulk_g2s(sB + off, img + off, n, &bar_theta);
+      }
+      for (uint32_t off = 0; off < th_bytes; off += 32768u) {
+        const uint32_t n = th_bytes - off < 32768u ? th_bytes - off : 32768u;
+        bulk_g2s(reinterpret_cast<uint8_t*>(sTh) + off, reinterpret_cast<const uint8_t*>(th32t) + off, n, &bar_theta);
       }
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
       int64_t c = 0;  // grain-tile counter over the whole loop
@@ -500,29 +510,65 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     }
     __syncwarp();
   } else if (is_producer(warp)) {
-    const int p0 = tid - kTcConsumers;  // pixel rows p0 and p0 + 64 of the tile
+    // pixel rows p0 and p0 + 64 of every tile; the next tile's pixel
+    // indices, coordinates and labels are fetched while this one is written
+    const int p0 = tid - kTcConsumers;
+    // feature-major parameters: lanes that read consecutive grains hit
+    // consecutive banks
+    const float* thp = th_resident ? sTh : th32t;
+    auto dot_t = [&](int i, const float* e) {
+      float acc = thp[i] * e[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) acc = fmaf(thp[(int64_t)k * Npad + i], e[k], acc);
+      return acc;
+    };
+    bool ok = !th_resident || mbar_wait_warp(&bar_theta, 0, &abort_flag, status);
+    int64_t jn[2];
+    float xn[2][DIM], cn[DIM];
+    int Gn[2];
+    auto fetch = [&](int64_t t) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        jn[u] = tile_pixel<DIM>(g, tm, t, p0 + 64 * u, xn[u], cn);
+        Gn[u] = jn[u] >= 0 ? labels[jn[u]] : -1;
+      }
+    };
+    if (ok && blockIdx.x < n_tiles) fetch(blockIdx.x);
     int it = 0;
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
       const int s = it & 1, use = it >> 1;
+      int64_t jc[2];
+      float xc[2][DIM], cc[DIM];
+      int Gc[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        jc[u] = jn[u];
+        Gc[u] = Gn[u];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) xc[u][a] = xn[u][a];
+      }
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) cc[a] = cn[a];
+      if (t + gridDim.x < n_tiles) fetch(t + gridDim.x);
       if (use >= 1 && (!mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status) ||
                        !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)))
         break;
-      float c[DIM], ec[K];
-      for (int p = p0; p < kTcPixTile; p += kTcProducers) {
-        float x[DIM], eta[K];
-        const int64_t j = tile_pixel<DIM>(g, tm, t, p, x, c);
-        legendre_features<DIM, D>(c, ec);
-        legendre_features<DIM, D>(x, eta);
+      float ec[K];
+      legendre_features<DIM, D>(cc, ec);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int p = p0 + 64 * u;
+        float eta[K];
+        legendre_features<DIM, D>(xc[u], eta);
         float de[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
         store_eta_row<K, KW, KS>(sA + s * kTileBytes, p, de);
         float start = -INFINITY, lg = 0.f;
-        if (j >= 0) {
-          const int G = labels[j];
+        if (jc[u] >= 0) {
+          const int G = Gc[u];
           if ((unsigned)G < (unsigned)N) {
-            const float* rowp = th32 + (int64_t)G * KP32;
-            lg = dot_f<K>(rowp, ec) + dot_f<K>(rowp, de);
+            lg = dot_t(G, ec) + dot_t(G, de);
             start = lg;
           } else {
             lg = NAN;
@@ -530,10 +576,9 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         }
         sLG[s * 128 + p] = start;
         sLGv[s * 128 + p] = lg;
-        sJ[s * 128 + p] = (long long)j;
+        sJ[s * 128 + p] = (long long)jc[u];
       }
-      for (int i = p0; i < Npad; i += kTcProducers)
-        sOff[s * Npad + i] = i < N ? dot_f<K>(th32 + (int64_t)i * KP32, ec) : 0.f;
+      for (int i = p0; i < Npad; i += kTcProducers) sOff[s * Npad + i] = i < N ? dot_t(i, ec) : 0.f;
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
     }
@@ -541,6 +586,36 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
     const int row = quad * 32 + lane;  // pixel row of the tile == TMEM lane
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    // online log-sum-exp over 32 logits (grains cbase .. cbase+31, nv of
+    // them valid); the running max starts at the label logit (a lower bound
+    // of the max, usually the max itself), so most chunks of far-away grains
+    // lie more than 127 below it: their exponentials underflow to exactly
+    // zero in ex2.approx.ftz and the whole chunk is skipped
+    auto chunk = [&](const uint32_t(&r)[32], const float* off, int nv, float& m, float& ssum) {
+      if (nv <= 0) return;
+      float v[32];
+      const float4* off4 = reinterpret_cast<const float4*>(off);  // 16-byte aligned: cbase is a multiple of 32
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        const float4 o = off4[q >> 2];
+        v[q] = q < nv ? __uint_as_float(r[q]) + o.x : -INFINITY;
+        v[q + 1] = q + 1 < nv ? __uint_as_float(r[q + 1]) + o.y : -INFINITY;
+        v[q + 2] = q + 2 < nv ? __uint_as_float(r[q + 2]) + o.z : -INFINITY;
+        v[q + 3] = q + 3 < nv ? __uint_as_float(r[q + 3]) + o.w : -INFINITY;
+      }
+      const float cm = tree_max32(v);
+      if (__all_sync(0xffffffffu, cm < m - 127.f)) return;
+      const float mn = fmaxf(m, cm);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = Arith<float>::ex(v[q] - mn);
+      ssum = fmaf(ssum, Arith<float>::ex(m - mn), tree_sum32(v));
+      m = mn;
+    };
+    // the two 32-column halves of the thread's logits: the second is loaded
+    // while the first is used, and the first half of the next grain tile
+    // (when the tensor cores have it ready) while the second is used
+    uint32_t RA[32], RB[32];
+    bool pre = false;
     int it = 0;
     int64_t c = 0;
     bool ok = true;
@@ -549,60 +624,35 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       // the stage's operands and per-row values come from the producers
       ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
       if (!ok) break;
-      // the running max starts at the label logit (a lower bound of the max,
-      // usually the max itself), so most chunks of far-away grains lie more
-      // than 127 below it: their exponentials underflow to exactly zero in
-      // ex2.approx.ftz and the whole chunk is skipped
       float m = sLG[s * 128 + row], ssum = 0.f;
-      // logits of grain tile gt are loaded while tile gt-1 is processed
-      uint32_t n0[32], n1[32];
-      {
-        const int b = (int)(c % kP1Bufs);
-        ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 64);
-        tmem_ld32(tmem + lane_base + col, n0);
-        tmem_ld32(tmem + lane_base + col + 32, n1);
-      }
+      const bool more_tiles = t + gridDim.x < n_tiles;
       for (int gt = 0; gt < n_gt; ++gt, ++c) {
         const int b = (int)(c % kP1Bufs);
+        const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 64);
+        if (!pre) {
+          ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
+          if (!ok) break;
+          tc_fence_after();
+          tmem_ld32(tmem + lane_base + col, RA);
+        }
+        tmem_wait_ld();
+        tmem_ld32(tmem + lane_base + col + 32, RB);
+        const int cbase = gt * kTcGrainTile + half * 64;
+        const float* off = sOff + s * Npad + cbase;
+        chunk(RA, off, N - cbase, m, ssum);
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
-        uint32_t r0[32], r1[32];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          r0[q] = n0[q];
-          r1[q] = n1[q];
-        }
-        if (gt + 1 < n_gt) {
+        pre = false;
+        if (gt + 1 < n_gt || more_tiles) {
           const int bn = (int)((c + 1) % kP1Bufs);
-          ok = mbar_wait_warp(&bar_d_full[bn], (uint32_t)(((c + 1) / kP1Bufs) & 1), &abort_flag, status);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t col = (uint32_t)(bn * kTcGrainTile + half * 64);
-          tmem_ld32(tmem + lane_base + col, n0);
-          tmem_ld32(tmem + lane_base + col + 32, n1);
+          if (__all_sync(0xffffffffu, mbar_peek(&bar_d_full[bn], (uint32_t)(((c + 1) / kP1Bufs) & 1)))) {
+            tc_fence_after();
+            tmem_ld32(tmem + lane_base + (uint32_t)(bn * kTcGrainTile + half * 64), RA);
+            pre = true;
+          }
         }
-        const int cbase = gt * kTcGrainTile + half * 64;
-        const float* off = sOff + s * Npad + cbase;
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int nv = N - (cbase + 32 * h2);
-          if (nv <= 0) break;
-          const uint32_t* r = h2 ? r1 : r0;
-          float v[32];
-#pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = q < nv ? __uint_as_float(r[q]) + off[32 * h2 + q] : -INFINITY;
-          const float cm = tree_max32(v);
-          if (__all_sync(0xffffffffu, cm < m - 127.f)) continue;
-          const float mn = fmaxf(m, cm);
-#pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = Arith<float>::ex(v[q] - mn);
-          ssum = fmaf(ssum, Arith<float>::ex(m - mn), tree_sum32(v));
-          m = mn;
-        }
+        chunk(RB, off + 32, N - cbase - 32, m, ssum);
       }
       if (!ok) break;
       // combine the two column halves of each pixel (bounded mbarrier
@@ -1146,11 +1196,15 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t P = c.g.P;
   const int Npad = (N + 127) / 128 * 128;
   const size_t row_bytes = (size_t)KT * 2;
+  constexpr size_t kCap = 220 * 1024;
   // image, 2 operand stages, 2 x centre logits, 2 x (max, sum), 2 x start,
   // 2 x label logit, 2 x pixel index
-  const size_t smem1 = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
-                       2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 + 2 * kTcPixTile * 8;
-  constexpr size_t kCap = 220 * 1024;
+  const size_t smem1_base = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
+                            2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 + 2 * kTcPixTile * 8;
+  // the float parameters join the image in shared memory when they fit
+  const size_t th_bytes = (size_t)K * Npad * 4;
+  const int th_resident = smem1_base + th_bytes <= kCap ? 1 : 0;
+  const size_t smem1 = smem1_base + (th_resident ? th_bytes : 0);
   // pass-2 stages: three pixel-operand and two gradient-operand stages
   // when they fit, else fewer
   using L2 = Pass2Layout<DIM, D, KS>;
@@ -1178,6 +1232,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   Scratch sc(st);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
   float* th32 = sc.get<float>((size_t)N * KP32);
+  float* th32t = sc.get<float>((size_t)K * Npad);
   float* lse = sc.get<float>((size_t)P);
   double* objp = sc.get<double>((size_t)grid1);
   double* part = c.grad ? sc.get<double>((size_t)n_chunks * N * K) : nullptr;
@@ -1191,13 +1246,14 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const int64_t n = (int64_t)Npad * KW;
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, Npad, K, KW, scale, img,
-                                                                                th32, KP32));
+                                                                                th32, KP32, th32t));
   }
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
   PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
-           k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, img, th32, lse, objp, status));
+           k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, img, th32t, th_resident, lse, objp,
+                                                    status));
   // |eta| <= 1, so a grain's label sum is bounded by P: the largest
   // power-of-two scale that keeps P * scale below 2^62
   int bits = 0;
