@@ -33,8 +33,12 @@
 // PD_BF16X3 splits every operand into three bf16 terms (hi + mid + lo,
 // about 24 significant bits) and forms the six products whose size is at
 // least 2^-16 of the leading one (hh, hm, mh, hl, mm, lh), which gives
-// float-level logits; the gradient uses two-term splits (hh, lh, hl).
-// PD_BF16 uses one term everywhere.  An operand row stores each term once,
+// float-level logits.  PD_BF16 uses one term for the logits.  The gradient
+// contraction takes c = -p in fp16 (11 significant bits, round to nearest)
+// against the features in fp16, split hi + lo for PD_BF16X3 (one MMA of
+// N = 2 KW per 16 pixels, the two column blocks added at the read-out) and
+// hi only for PD_BF16; its relative error stays near 1e-5 of the gradient,
+// below that of float logits at small eps.  An operand row stores each term once,
 // as KW-column slices side by side; a product is a run of MMAs whose two
 // descriptors start at the slices of its terms.
 //
@@ -47,6 +51,7 @@
 // becomes NaN), raises a CTA-wide abort flag so that the other waits give up
 // at once, and the CTA still frees its TMEM before it returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "pd_simt_kernels.cuh"
 
@@ -198,6 +203,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // Instruction descriptor, kind::f16: fp32 D, bf16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// The same with fp16 A and B.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 // Byte offset of element (row r, column k) of a K-major no-swizzle operand
 // whose core matrices lie lbo bytes apart along K and sbo bytes apart along
@@ -710,7 +719,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
 // ---------------------------------------------------------------------------
 // Pass 2: gradient partials of one grain block over a contiguous run of
 // tiles (one wave of CTAs per grain block).  NB pixel-operand stages (up to
-// 3) and NA gradient-operand stages (up to 2), as many as shared memory
+// 4) and NA gradient-operand stages (up to 2), as many as shared memory
 // holds.  Two warps issue MMAs: one the logits, as far ahead as the three
 // TMEM logit buffers and the operand stages allow, the other the gradient
 // contractions, so neither waits behind the other.  The consumers pick the
@@ -732,7 +741,8 @@ struct Pass2Layout {
   static constexpr int K = basis_K(DIM, D);
   static constexpr int KW = (K + 15) / 16 * 16;
   static constexpr int KT = KW * n_terms(KS);
-  static constexpr int GT = KS == 1 ? 1 : 2;  // gradient terms of c and eta
+  static constexpr int ET = KS == 1 ? 1 : 2;  // fp16 terms of eta in the gradient contraction
+  static constexpr int N2 = ET * KW;           // its MMA N: eta_h (and eta_l) columns
   static constexpr int KE = (K + 3) / 4 * 4;  // tile-centre features per stage
   static constexpr uint32_t kABytes = 128u * KT * 2;             // theta block
   static constexpr uint32_t kSboB = (uint32_t)KT * 16 + 16;
@@ -740,9 +750,8 @@ struct Pass2Layout {
   static constexpr uint32_t kLbo2 = 144;
   static constexpr uint32_t kSbo2 = 16 * kLbo2;
   static constexpr uint32_t kB2Term = (KW / 8) * kSbo2;
-  static constexpr uint32_t kB2Bytes = GT * kB2Term;
-  static constexpr uint32_t kA2Term = 128u * kTcPixTile * 2;     // c: 128 grains x 128 pixels
-  static constexpr uint32_t kA2Bytes = GT * kA2Term;
+  static constexpr uint32_t kB2Bytes = ET * kB2Term;           // rows: eta_h features, then eta_l
+  static constexpr uint32_t kA2Bytes = 128u * kTcPixTile * 2;    // c: 128 grains x 128 pixels, fp16
   static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + KE * 4;
   static constexpr size_t bytes(int nb, int na) { return kABytes + (size_t)nb * kPerB + (size_t)na * kA2Bytes; }
 };
@@ -757,11 +766,12 @@ __global__ void __launch_bounds__(kP2Threads, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const float* __restrict__ th32,
            const float* __restrict__ lse, int64_t n_chunks, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
-  constexpr int K = L::K, KW = L::KW, KT = L::KT, GT = L::GT, KE = L::KE;
+  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2, KE = L::KE;
   constexpr int KP32 = padded_K<float>(K);
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
-  constexpr uint32_t IDESC2 = idesc_bf16(128, KW);
+  constexpr uint32_t IDESC2 = idesc_f16(128, N2);
   constexpr int D2COL = kP2LogitBufs * kTcPixTile;  // TMEM: D1 ring [0, 384), D2 x 2 from 384
+  static_assert(D2COL + 2 * N2 <= kTcCols, "TMEM columns");
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                             // theta block image
@@ -835,9 +845,9 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
     }
     __syncwarp();
   } else if (warp == kP2GradWarp) {
-    // gradient D2 += C . eta, products (c_h, eta_h), then (c_l, eta_h),
-    // (c_h, eta_l); one D2 accumulation per chunk, alternating between two
-    // TMEM buffers so that the consumers read one while the next fills
+    // gradient D2 += C . [eta_h | eta_l], fp16; one D2 accumulation per
+    // chunk, alternating between two TMEM buffers so that the consumers
+    // read one while the next fills
     if (tid == kP2GradWarp * 32) {
       bool ok = true;
       for (int t = 0; ok && t < n_pt; ++t) {
@@ -849,16 +859,11 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
         if (!ok) break;
         tc_fence_after();
         const uint32_t a2 = smem_addr(sA2 + a * L::kA2Bytes), b2 = smem_addr(sB2 + s * L::kB2Bytes);
-        constexpr int NPROD = GT == 1 ? 1 : 3;
-#pragma unroll 1
-        for (int pr = 0; pr < NPROD; ++pr) {
-          const int ct = pr == 1 ? 1 : 0, et = pr == 2 ? 1 : 0;
 #pragma unroll 2
-          for (int q = 0; q < kTcPixTile / 16; ++q) {
-            const uint64_t ad = smem_desc(a2 + ct * L::kA2Term + q * 256, 128, kTcPixTile * 16);
-            const uint64_t bd = smem_desc(b2 + et * L::kB2Term + q * 2 * L::kLbo2, L::kLbo2, L::kSbo2);
-            mma_bf16(tmem + D2COL + db * KW, ad, bd, IDESC2, (!first || pr > 0 || q > 0) ? 1u : 0u);
-          }
+        for (int q = 0; q < kTcPixTile / 16; ++q) {
+          const uint64_t ad = smem_desc(a2 + q * 256, 128, kTcPixTile * 16);
+          const uint64_t bd = smem_desc(b2 + q * 2 * L::kLbo2, L::kLbo2, L::kSbo2);
+          mma_bf16(tmem + D2COL + db * N2, ad, bd, IDESC2, (!first || q > 0) ? 1u : 0u);
         }
         mma_commit(&bar_a2_empty[a]);
         mma_commit(&bar_b_empty[s]);
@@ -909,18 +914,19 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
         for (int k = 0; k < K; ++k) de[k] = e1[k] - ec[k];
         store_eta_row<K, KW, KS, L::kSboB>(bs, q2 + 1, de);
       }
-      // eta^T: one 32-bit word holds the two pixels of a feature (pixels
-      // outside the set have c = 0, so their features need no masking)
+      // eta^T in fp16 (hi, and lo for PD_BF16X3): one 32-bit word holds the
+      // two pixels of a feature (pixels outside the set have c = 0, so their
+      // features need no masking)
       uint8_t* b2 = sB2 + s * L::kB2Bytes;
 #pragma unroll
       for (int k = 0; k < KW; ++k) {
         const float a0 = k < K ? e0[k] : 0.f, a1 = k < K ? e1[k] : 0.f;
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+        const __half2 h = __floats2half2_rn(a0, a1);
         const uint32_t o = kmaj_s(k, q2, L::kLbo2, L::kSbo2);
         *reinterpret_cast<uint32_t*>(b2 + o) = *reinterpret_cast<const uint32_t*>(&h);
-        if (GT == 2) {
-          const float2 hf = __bfloat1622float2(h);
-          const __nv_bfloat162 l = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
+        if (ET == 2) {
+          const float2 hf = __half22float2(h);
+          const __half2 l = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
           *reinterpret_cast<uint32_t*>(b2 + L::kB2Term + o) = *reinterpret_cast<const uint32_t*>(&l);
         }
       }
@@ -946,11 +952,13 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
       const int db = u & 1;
       if (!mbar_wait_warp(&bar_d2_full[db], (uint32_t)((u >> 1) & 1), &abort_flag, status)) return false;
       tc_fence_after();
-      uint32_t r[32];
-      if (KW == 16) {
-        tmem_ld16(tmem + lane_base + (uint32_t)(D2COL + db * KW), r);
+      uint32_t r[N2 < 32 ? 32 : N2];
+      const uint32_t base = tmem + lane_base + (uint32_t)(D2COL + db * N2);
+      if (N2 == 16) {
+        tmem_ld16(base, r);
       } else {
-        tmem_ld32(tmem + lane_base + (uint32_t)(D2COL + db * KW), r);
+#pragma unroll
+        for (int c0 = 0; c0 < N2; c0 += 32) tmem_ld32(base + c0, r + c0);
       }
       tmem_wait_ld();
       tc_fence_before();
@@ -958,36 +966,29 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
       if (i < N) {
         double* row = part + ((c_begin + u) * N + i) * K;
 #pragma unroll
-        for (int k = 0; k < K; ++k) row[k] = (double)__uint_as_float(r[k]);
+        for (int k = 0; k < K; ++k)
+          row[k] = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
       }
       n_done = u + 1;
       return true;
     };
     // c = -p for 32 pixels (columns q0 .. q0+31 of this thread's half),
-    // written as hi (+ lo) bf16 pairs, one 16-byte core-matrix row per 8
-    // pixels and term
+    // written as fp16 pairs, one 16-byte core-matrix row per 8 pixels
     auto emit = [&](const uint32_t(&r)[32], const float* ls, float off, uint8_t* a2, int q0) {
 #pragma unroll
       for (int q8 = 0; q8 < 32; q8 += 8) {
         const float4 va = *reinterpret_cast<const float4*>(ls + q8);
         const float4 vb = *reinterpret_cast<const float4*>(ls + q8 + 4);
         const float lv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-        uint32_t hi[4], lo[4];
+        uint32_t hw[4];
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
           const float c0 = -Arith<float>::ex(__uint_as_float(r[q8 + u]) - (lv[u] - off));
           const float c1 = -Arith<float>::ex(__uint_as_float(r[q8 + u + 1]) - (lv[u + 1] - off));
-          const __nv_bfloat162 h = __floats2bfloat162_rn(c0, c1);
-          hi[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
-          if (GT == 2) {
-            const float2 f = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(c0 - f.x, c1 - f.y);
-            lo[u >> 1] = *reinterpret_cast<const uint32_t*>(&l);
-          }
+          const __half2 h = __floats2half2_rn(c0, c1);
+          hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
         }
-        const uint32_t o = kmaj(gr, q0 + q8, kTcPixTile);
-        *reinterpret_cast<uint4*>(a2 + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        if (GT == 2) *reinterpret_cast<uint4*>(a2 + L::kA2Term + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<uint4*>(a2 + kmaj(gr, q0 + q8, kTcPixTile)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
       }
     };
     // the two 32-column halves of the thread's logits: the second is loaded
@@ -1205,10 +1206,10 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const size_t th_bytes = (size_t)K * Npad * 4;
   const int th_resident = smem1_base + th_bytes <= kCap ? 1 : 0;
   const size_t smem1 = smem1_base + (th_resident ? th_bytes : 0);
-  // pass-2 stages: three pixel-operand and two gradient-operand stages
-  // when they fit, else fewer
+  // pass-2 stages: four pixel-operand and two gradient-operand stages when
+  // they fit, else fewer
   using L2 = Pass2Layout<DIM, D, KS>;
-  constexpr int NB = L2::bytes(3, 2) <= kCap ? 3 : (L2::bytes(2, 1) <= kCap ? 2 : 1);
+  constexpr int NB = L2::bytes(4, 2) <= kCap ? 4 : (L2::bytes(3, 2) <= kCap ? 3 : (L2::bytes(2, 1) <= kCap ? 2 : 1));
   constexpr int NA = L2::bytes(NB, 2) <= kCap ? 2 : 1;
   const size_t smem2 = L2::bytes(NB, NA);
   if (smem1 > kCap || smem2 > kCap) return PD_ENOTSUP;  // too many grains for a resident image

@@ -1,8 +1,9 @@
 """Parity of the tensor-core (tcgen05) evaluation with the FP64 oracle.
 
-PD_BF16X3 splits operands into three bf16 terms (about 24 significant
-bits) for the logits and two terms for the gradient contraction: it must
-meet the FP32 tolerances (Phi 1e-5 relative, gradient 1e-4 in norm).
+PD_BF16X3 splits the logit operands into three bf16 terms (about 24
+significant bits) and contracts the gradient with fp16 c against fp16
+hi + lo features: it must meet the FP32 tolerances (Phi 1e-5 relative,
+gradient 1e-4 in norm).
 PD_BF16 rounds every operand to bf16 (8 significant bits): its logit error
 is about |theta| / eps * 2^-9, so it is checked at a loose bound scaled to
 that, and its error is reported by the benchmark.
