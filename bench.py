@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"],
+                    help="bf16x3 (default): tcgen05 logits with three-term bf16 operands, fp32 accumulation and "
+                         "log-sum-exp, fp16 gradient operands, double final reductions; fp32: CUDA-core path")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU oracle sample")
@@ -343,6 +345,14 @@ def run_ours(args):
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured MUFU ex2 throughput (pd_microbench)"}
+    # the whole evaluation against its binding unit: one exponential per
+    # pixel-grain pair is the method's algorithmic minimum (the logits and
+    # gradient contractions need 4K flop per pair, far below the tensor or
+    # FMA peaks), so the step is measured in exponentials per second
+    step_ex2 = P * N / (ms_step * 1e-3) / 1e12
+    roof["step"] = {"achieved": step_ex2, "peak": units["ex2_per_s"] / 1e12, "unit": "Tex2/s",
+                    "frac": step_ex2 / (units["ex2_per_s"] / 1e12),
+                    "basis": "one ex2 per pixel-grain pair per evaluation over ms_per_step"}
     cpu = cpu_oracle_rate(args.cpu_seconds) if world == 1 or rank == 0 else None
     line = {
         "metric": "pixel*grain objective+gradient evaluations per second",
@@ -449,14 +459,18 @@ def run_fit(args):
     t_ref = time.perf_counter() - t
     target = ref["phi"] - 1e-8 * abs(ref["phi"])
     rows = {"fp64_plain": {"seconds": t_ref, "iters": ref["iters"], "evals": ref["evals"], "phi": ref["phi"]}}
-    for name, prec in (("fp32_then_fp64", pd.PD_FP32), ("bf16x3_then_fp64", pd.PD_BF16X3)):
+    for name, prec in (("fp32_then_fp64", pd.PD_FP32), ("bf16x3_then_fp64", pd.PD_BF16X3),
+                       ("bf16_then_fp64", pd.PD_BF16)):
         t = time.perf_counter()
         _, rep = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=1000, prec=prec, refine_iter=1000, target_phi=target,
                            switch_rtol=1e-7)
         rows[name] = {"seconds": time.perf_counter() - t, "iters": rep["iters"], "iters_phase1": rep["iters_phase1"],
                       "evals": rep["evals"], "phi": rep["phi"], "reached": rep["phi"] >= target}
-    line = {"metric": "time to the FP64 plain-fit objective (<=1e-8 relative)", "value": rows["fp32_then_fp64"]["seconds"],
-            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+    best = min(("bf16x3_then_fp64", "bf16_then_fp64"),
+               key=lambda k: rows[k]["seconds"] if rows[k]["reached"] else float("inf"))
+    line = {"metric": "time to the FP64 plain-fit objective (<=1e-8 relative)", "value": rows[best]["seconds"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "schedule": best,
+            "speedup_vs_fp32_then_fp64": rows["fp32_then_fp64"]["seconds"] / rows[best]["seconds"],
             "config": {"workload": WORKLOAD, "reference": "FP64 plain fit, 1000 L-BFGS iterations from theta=0",
                        "phi_ref": ref["phi"]}, "runs": rows}
     print(json.dumps(line))

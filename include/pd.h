@@ -200,7 +200,10 @@ typedef struct pd_fit_opts {
   int prec;           /* precision of the first phase (PD_FP64 ...)        */
   int refine_iter;    /* FP64 iterations after the first phase (0: none)   */
   double gtol;        /* stop a phase when ||grad Phi||_2 <= gtol          */
-  double target_phi;  /* stop when Phi >= target_phi (-inf: never)         */
+  double target_phi;  /* stop when Phi >= target_phi (-inf: never); with
+                         refine_iter > 0 a target met in a reduced-
+                         precision phase must hold in FP64, else the FP64
+                         phase continues                                  */
   double switch_rtol; /* leave the first phase when the relative Phi gain
                          of an iteration is below this (0: never)          */
 } pd_fit_opts;

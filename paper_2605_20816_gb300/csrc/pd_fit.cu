@@ -356,6 +356,14 @@ int fit_run(Evaluator& ev, const Vec& th, int N, int K, const pd_fit_opts& o, Fi
     rc = newton_phase(ev, prec, cur, o.max_iter, o.max_cg, o.gtol, target, &r1);
   if (rc) return rc;
   int status = r1.status;
+  // a target reached in reduced precision counts only once the FP64
+  // objective confirms it; otherwise the FP64 refinement continues
+  if (o.refine_iter > 0 && status == 3 && prec != PD_FP64) {
+    prec = PD_FP64;
+    rc = ev.eval(cur.x, prec, &cur.f, &cur.g);
+    if (rc) return rc;
+    if (!(-cur.f >= target)) status = 0;
+  }
   if (o.refine_iter > 0 && status != 3) {
     if (prec != PD_FP64) {
       prec = PD_FP64;
