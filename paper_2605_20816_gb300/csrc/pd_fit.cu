@@ -28,10 +28,18 @@
 
 namespace pd {
 
+// Eight interleaved partial sums, combined in a fixed order: the same
+// result on every call, and eight independent add chains instead of one
+// (a single running sum over tens of thousands of terms is bound by the
+// add latency and dominated the host side of an L-BFGS iteration).
 double dot(const Vec& a, const Vec& b) {
-  double s = 0.0;
-  for (size_t q = 0; q < a.size(); ++q) s += a[q] * b[q];
-  return s;
+  const size_t n = a.size();
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  size_t q = 0;
+  for (; q + 8 <= n; q += 8)
+    for (int u = 0; u < 8; ++u) s[u] += a[q + u] * b[q + u];
+  for (int u = 0; q < n; ++q, ++u) s[u] += a[q] * b[q];
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
 namespace {
@@ -48,28 +56,39 @@ class Problem : public Evaluator {
     d_obj_ = sc_.get<double>(1);
     d_mis_ = sc_.get<int64_t>(1);
     d_lab_ = sc_.get<int32_t>((size_t)(g.P > 0 ? g.P : 1));
-    h_theta_.assign((size_t)N * K_, 0.0);
-    h_grad_.assign((size_t)N * K_, 0.0);
+    // pinned staging: the uploads run asynchronously, and the one
+    // synchronisation per evaluation (after the read-back) also orders
+    // them before the next overwrite of these buffers
+    const size_t nk = (size_t)N * K_;
+    if (cudaMallocHost((void**)&h_theta_, sizeof(double) * nk) != cudaSuccess) h_theta_ = nullptr;
+    if (cudaMallocHost((void**)&h_v_, sizeof(double) * nk) != cudaSuccess) h_v_ = nullptr;
+    if (cudaMallocHost((void**)&h_grad_, sizeof(double) * (nk + 1)) != cudaSuccess) h_grad_ = nullptr;
   }
-  bool ok() const { return sc_.ok(); }
+  ~Problem() override {
+    if (h_theta_) cudaFreeHost(h_theta_);
+    if (h_v_) cudaFreeHost(h_v_);
+    if (h_grad_) cudaFreeHost(h_grad_);
+  }
+  bool ok() const { return sc_.ok() && h_theta_ && h_v_ && h_grad_; }
   int n_free() const override { return (N_ - 1) * K_; }
   int K() const { return K_; }
 
   // f = -Phi, gf = -grad Phi on the free blocks
   int eval(const Vec& x, int prec, double* f, Vec* gf) override {
-    int rc = upload(x, d_theta_);
+    int rc = upload(x, d_theta_, h_theta_);
     if (rc) return rc;
     EvalCall c{g_, grid_->dim, d_, N_, prec, eps_, labels_, d_theta_, nullptr, d_obj_, gf ? d_grad_ : nullptr,
                nullptr};
     rc = (prec == PD_BF16 || prec == PD_BF16X3) ? eval_tc(c, st_) : eval_simt(c, st_);
     if (rc) return rc;
-    double phi = 0.0;
-    if (cudaMemcpyAsync(&phi, d_obj_, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess) return PD_ECUDA;
-    if (gf && cudaMemcpyAsync(h_grad_.data(), d_grad_, sizeof(double) * h_grad_.size(), cudaMemcpyDeviceToHost,
-                              st_) != cudaSuccess)
+    const size_t nk = (size_t)N_ * K_;
+    double* h_phi = h_grad_ + nk;
+    if (cudaMemcpyAsync(h_phi, d_obj_, sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess) return PD_ECUDA;
+    if (gf && cudaMemcpyAsync(h_grad_, d_grad_, sizeof(double) * nk, cudaMemcpyDeviceToHost, st_) != cudaSuccess)
       return PD_ECUDA;
     if (cudaStreamSynchronize(st_) != cudaSuccess) return PD_ECUDA;
     ++evals;
+    const double phi = *h_phi;
     *f = -phi;
     if (gf) {
       gf->resize(n_free());
@@ -80,15 +99,15 @@ class Problem : public Evaluator {
 
   // out = (Hessian of -Phi) v on the free blocks
   int hvp(const Vec& x, const Vec& v, int prec, Vec* out) override {
-    int rc = upload(x, d_theta_);
+    int rc = upload(x, d_theta_, h_theta_);
     if (rc) return rc;
-    rc = upload(v, d_v_);
+    rc = upload(v, d_v_, h_v_);
     if (rc) return rc;
     EvalCall c{g_, grid_->dim, d_, N_, prec == PD_FP64 ? PD_FP64 : PD_FP32, eps_, labels_, d_theta_, d_v_,
                nullptr, nullptr, d_grad_};
     rc = eval_simt(c, st_);
     if (rc) return rc;
-    if (cudaMemcpyAsync(h_grad_.data(), d_grad_, sizeof(double) * h_grad_.size(), cudaMemcpyDeviceToHost, st_) !=
+    if (cudaMemcpyAsync(h_grad_, d_grad_, sizeof(double) * (size_t)N_ * K_, cudaMemcpyDeviceToHost, st_) !=
         cudaSuccess)
       return PD_ECUDA;
     if (cudaStreamSynchronize(st_) != cudaSuccess) return PD_ECUDA;
@@ -99,7 +118,7 @@ class Problem : public Evaluator {
   }
 
   int mismatch(const Vec& x, int64_t* miss) {
-    int rc = upload(x, d_theta_);
+    int rc = upload(x, d_theta_, h_theta_);
     if (rc) return rc;
     rc = assign_simt(g_, grid_->dim, d_, N_, d_theta_, d_lab_, nullptr, labels_, d_mis_, st_);
     if (rc) return rc;
@@ -108,24 +127,24 @@ class Problem : public Evaluator {
   }
 
   int write_theta(const Vec& x, double* dst) {
-    int rc = upload(x, d_theta_);
+    int rc = upload(x, d_theta_, h_theta_);
     if (rc) return rc;
-    if (cudaMemcpyAsync(dst, d_theta_, sizeof(double) * h_theta_.size(), cudaMemcpyDeviceToDevice, st_) !=
+    if (cudaMemcpyAsync(dst, d_theta_, sizeof(double) * (size_t)N_ * K_, cudaMemcpyDeviceToDevice, st_) !=
         cudaSuccess)
       return PD_ECUDA;
     return cudaStreamSynchronize(st_) == cudaSuccess ? PD_OK : PD_ECUDA;
   }
 
  private:
-  // free blocks x -> full [N][K] with the last block zero
-  int upload(const Vec& x, double* dst) {
-    for (int q = 0; q < n_free(); ++q) h_theta_[q] = x[q];
-    for (int k = 0; k < K_; ++k) h_theta_[(size_t)(N_ - 1) * K_ + k] = 0.0;
-    if (cudaMemcpyAsync(dst, h_theta_.data(), sizeof(double) * h_theta_.size(), cudaMemcpyHostToDevice, st_) !=
-        cudaSuccess)
-      return PD_ECUDA;
-    // the host staging buffer is reused by the next upload
-    return cudaStreamSynchronize(st_) == cudaSuccess ? PD_OK : PD_ECUDA;
+  // free blocks x -> full [N][K] with the last block zero, through the
+  // pinned staging buffer h (asynchronous: every caller synchronises the
+  // stream before it returns, so h is not rewritten while in flight)
+  int upload(const Vec& x, double* dst, double* h) {
+    for (int q = 0; q < n_free(); ++q) h[q] = x[q];
+    for (int k = 0; k < K_; ++k) h[(size_t)(N_ - 1) * K_ + k] = 0.0;
+    return cudaMemcpyAsync(dst, h, sizeof(double) * (size_t)N_ * K_, cudaMemcpyHostToDevice, st_) == cudaSuccess
+               ? PD_OK
+               : PD_ECUDA;
   }
 
   const pd_grid* grid_;
@@ -138,7 +157,9 @@ class Problem : public Evaluator {
   double *d_theta_, *d_grad_, *d_v_, *d_obj_;
   int64_t* d_mis_;
   int32_t* d_lab_;
-  Vec h_theta_, h_grad_;
+  double* h_theta_ = nullptr;  // pinned [N][K]
+  double* h_v_ = nullptr;      // pinned [N][K]
+  double* h_grad_ = nullptr;   // pinned [N][K] + 1 (objective)
 };
 
 // Safeguarded cubic step between (a, fa, ga) and (b, fb, gb).
