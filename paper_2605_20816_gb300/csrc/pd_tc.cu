@@ -15,7 +15,7 @@
 //       threads from the in-register Legendre recurrence;
 //   B = all grains' scaled parameters -theta*log2(e)/eps (rows) x K, copied
 //       once per CTA from a prepared global image by a bulk (TMA) copy;
-//   D = A B^T, 128 pixels x 128 grains per MMA group, double-buffered in
+//   D = A B^T, 128 pixels x 256 grains per MMA group, double-buffered in
 //       TMEM; the epilogue warps read their pixel row of logits and keep an
 //       online log-sum-exp; out: log2 S(x) per pixel and per-CTA objective
 //       partials.
@@ -64,7 +64,7 @@ constexpr int kTcProducers = 64;                  // warps 8..9: pixel-operand p
 constexpr int kTcMmaWarp = 10;                    // TMEM allocation and MMA issue
 constexpr int kTcThreads = 11 * 32;               // at most 3 warps per SM sub-partition
 constexpr int kTcCols = 512;                      // TMEM columns per CTA (one CTA per SM)
-constexpr int kTcGrainTile = 128;                 // pass-1 grains per MMA group
+constexpr int kTcGrainTile = 256;                 // pass-1 grains per MMA group (N of the MMA)
 constexpr int kTcPixTile = 128;                   // pixels per tile (both passes)
 
 // ---------------------------------------------------------------------------
@@ -418,7 +418,7 @@ __device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp
 // ---------------------------------------------------------------------------
 // Pass 1: log2 S(x) per pixel and objective partials.
 // ---------------------------------------------------------------------------
-constexpr int kP1Bufs = 4;  // logit tiles in flight in TMEM (4 x 128 columns)
+constexpr int kP1Bufs = 2;  // logit tiles in flight in TMEM (2 x 256 columns)
 
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -637,18 +637,26 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       const bool more_tiles = t + gridDim.x < n_tiles;
       for (int gt = 0; gt < n_gt; ++gt, ++c) {
         const int b = (int)(c % kP1Bufs);
-        const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 64);
+        const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 128);
         if (!pre) {
           ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
           if (!ok) break;
           tc_fence_after();
           tmem_ld32(tmem + lane_base + col, RA);
         }
+        // the thread's 128 columns in four 32-column chunks, each loaded
+        // while the one before is used
+        const int cbase = gt * kTcGrainTile + half * 128;
+        const float* off = sOff + s * Npad + cbase;
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 32, RB);
-        const int cbase = gt * kTcGrainTile + half * 64;
-        const float* off = sOff + s * Npad + cbase;
         chunk(RA, off, N - cbase, m, ssum);
+        tmem_wait_ld();
+        tmem_ld32(tmem + lane_base + col + 64, RA);
+        chunk(RB, off + 32, N - cbase - 32, m, ssum);
+        tmem_wait_ld();
+        tmem_ld32(tmem + lane_base + col + 96, RB);
+        chunk(RA, off + 64, N - cbase - 64, m, ssum);
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
@@ -657,11 +665,11 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           const int bn = (int)((c + 1) % kP1Bufs);
           if (__all_sync(0xffffffffu, mbar_peek(&bar_d_full[bn], (uint32_t)(((c + 1) / kP1Bufs) & 1)))) {
             tc_fence_after();
-            tmem_ld32(tmem + lane_base + (uint32_t)(bn * kTcGrainTile + half * 64), RA);
+            tmem_ld32(tmem + lane_base + (uint32_t)(bn * kTcGrainTile + half * 128), RA);
             pre = true;
           }
         }
-        chunk(RB, off + 32, N - cbase - 32, m, ssum);
+        chunk(RB, off + 96, N - cbase - 96, m, ssum);
       }
       if (!ok) break;
       // combine the two column halves of each pixel (bounded mbarrier
@@ -1195,7 +1203,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   constexpr int KP32 = padded_K<float>(K);
   const int N = c.N;
   const int64_t P = c.g.P;
-  const int Npad = (N + 127) / 128 * 128;
+  const int Npad = (N + kTcGrainTile - 1) / kTcGrainTile * kTcGrainTile;  // parameter image rows
   const size_t row_bytes = (size_t)KT * 2;
   constexpr size_t kCap = 220 * 1024;
   // image, 2 operand stages, 2 x centre logits, 2 x (max, sum), 2 x start,
@@ -1224,7 +1232,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int sms = device_sm_count();
   const int64_t n_tiles = tm.n_tiles;
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
-  const int gblocks = Npad / 128;
+  const int gblocks = (N + 127) / 128;  // pass-2 grain blocks
   // pass 2: chunks of kP2ChunkTiles tiles (one gradient partial each),
   // shared out in contiguous runs over one wave of CTAs per grain block
   const int64_t n_chunks = (n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles;
