@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU oracle sample")
-    ap.add_argument("--workload", default="config2", choices=["config2", "batched", "fit"],
+    ap.add_argument("--workload", default="config2", choices=["config2", "batched", "fit", "config3"],
                     help="config2: the headline line; batched: 256 maps in one persistent launch vs per-map "
-                         "launches; fit: time to the FP64 objective for the precision schedules")
+                         "launches; fit: time to the FP64 objective for the precision schedules; config3: "
+                         "the 256^3 workload per degree and precision")
     return ap.parse_args()
 
 
@@ -501,6 +502,61 @@ def run_fit(args):
     return 0
 
 
+def run_config3(args):
+    """The 3-D workload: 256^3 voxels, N = 2000 grains requested from a seeded
+    anisotropic power diagram (compacted to the non-empty grains), fit degree
+    2 (K = 10) and 3 (K = 20), eps = 1e-3: device time of one objective+
+    gradient evaluation per precision (L2 flushed between steps), and the
+    relative difference of the reduced-precision objectives from FP64."""
+    import torch
+
+    from paper_2605_20816_gb300 import pd
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    shape, n0, eps = (256, 256, 256), 2000, 1e-3
+    y, w, A = synth.apd_params(synth.SEED_BASE + 2, n0, dim=3)
+    th2 = pd.pd_theta_from_apd(3, 2, y, w, A).cuda()
+    grid = pd.Grid(shape)
+    lab, _, _ = pd.pd_assign(grid, n0, 2, th2)
+    lab_np, N, used = synth.compact(lab.cpu().numpy())
+    lab = torch.from_numpy(lab_np.astype(np.int32)).cuda()
+    th2 = th2[torch.from_numpy(used).cuda()].contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    P = grid.P
+    rows = {}
+    for d in (2, 3):
+        K = pd.pd_K(3, d)
+        th = torch.zeros((N, K), dtype=torch.float64, device="cuda")
+        th[:, :10] = th2
+        phi64 = pd.pd_objective_grad(grid, lab, N, th, d, eps, prec=pd.PD_FP64, want_grad=False)[0].item()
+        for name in ("fp32", "bf16x3"):
+            prec = pd.PREC[name]
+            try:
+                pd.pd_objective_grad(grid, lab, N, th, d, eps, prec=prec)
+            except pd.PdError as e:
+                rows["d%d_%s" % (d, name)] = {"unsupported": str(e)}
+                continue
+            steps = max(3, min(args.steps, 10))
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            stream = torch.cuda.current_stream()
+            obj = None
+            for q in range(steps):
+                flush.fill_(q & 0xFF)
+                ev[q][0].record(stream)
+                obj, _ = pd.pd_objective_grad(grid, lab, N, th, d, eps, prec=prec)
+                ev[q][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            rows["d%d_%s" % (d, name)] = {"ms_per_eval": ms, "pixel_grain_per_s": P * N / (ms * 1e-3),
+                                          "phi_rel_vs_fp64": abs(obj.item() - phi64) / abs(phi64)}
+    line = {"metric": "pixel*grain objective+gradient evaluations per second (3-D)", "unit": "pixel*grain/s",
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "3D 256^3 voxels, N=2000 requested (anisotropic power diagram), eps=1e-3",
+                       "voxels": P, "grains": N, "l2": "flushed between steps"},
+            "runs": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -509,6 +565,8 @@ def main():
         return run_batched(args)
     if args.workload == "fit":
         return run_fit(args)
+    if args.workload == "config3":
+        return run_config3(args)
     return run_ours(args)
 
 

@@ -72,10 +72,12 @@ extern "C" {
                       terms (hi+mid+lo), which recovers float-level accuracy
                       on the tensor cores                                     */
 /* The tensor-core precisions serve the objective and gradient (not the HVP)
- * for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid sides <= 2^23, and keep
- * every grain's parameters resident in one SM's shared memory: about
- * 104 bytes a grain (rounded up to 128 grains) at K <= 16 in PD_BF16X3,
- * which allows N <= 1792; other combinations return PD_ENOTSUP.           */
+ * for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid sides <= 2^23; other
+ * combinations return PD_ENOTSUP.  The log-sum-exp pass keeps the grains'
+ * parameters resident in one SM's shared memory (about 104 bytes a grain
+ * at K <= 16 in PD_BF16X3, up to 1792 grains); more grains are processed
+ * in groups whose partial sums are merged, with a scratch buffer of
+ * 8 bytes per pixel and group.                                          */
 
 /* ---- supported sizes --------------------------------------------------- */
 #define PD_MAX_DEGREE_2D 7
@@ -84,7 +86,10 @@ extern "C" {
 /* Pixel set Omega (Sec. 2.1).  coords == NULL: structured grid n[0..dim-1]
  * with P = n[0]*n[1](*n[2]).  coords != NULL: an explicit device point list
  * [P][dim] of doubles in [-1,1]^dim (the paper's "any finite set of sample
- * points"); n is then ignored. */
+ * points"); n is then ignored.  The tensor-core precisions take 128
+ * consecutive points as one tile and split each logit at the tile's first
+ * point, so their accuracy needs a list ordered along space (e.g. a
+ * z-curve order); Phi and its gradient do not depend on the order. */
 typedef struct pd_grid {
   int dim;              /* 2 or 3 */
   int64_t n[3];

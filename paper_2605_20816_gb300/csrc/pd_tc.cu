@@ -422,9 +422,10 @@ constexpr int kP1Bufs = 2;  // logit tiles in flight in TMEM (2 x 256 columns)
 
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, const uint8_t* __restrict__ img,
-           const float* __restrict__ th32t, int th_resident, float* __restrict__ lse_out, double* __restrict__ obj_part,
-           int* __restrict__ status) {
+k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng,
+           const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
+           float* __restrict__ lse_out, double* __restrict__ obj_part, float2* __restrict__ ms_out,
+           float* __restrict__ lg_out, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
@@ -434,14 +435,14 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   constexpr uint32_t IDESC = idesc_bf16(128, kTcGrainTile);
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sB = smem;                                            // Npad x KT
-  uint8_t* sA = smem + (size_t)Npad * kRowBytes;                 // 2 stages x 128 x KT
-  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Npad centre logits
-  float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Npad);   // 2 stages x 128 (max, sum) of half 1
+  uint8_t* sB = smem;                                            // Ng x KT (this launch's grains)
+  uint8_t* sA = smem + (size_t)Ng * kRowBytes;                   // 2 stages x 128 x KT
+  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Ng centre logits
+  float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Ng);     // 2 stages x 128 (max, sum) of half 1
   float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);        // 2 stages x 128 starting max
   float* sLGv = sLG + 2 * 128;                                   // 2 stages x 128 label logits
   long long* sJ = reinterpret_cast<long long*>(sLGv + 2 * 128);  // 2 stages x 128 pixel indices
-  float* sTh = reinterpret_cast<float*>(sJ + 2 * 128);           // K x Npad scaled parameters (when resident)
+  float* sTh = reinterpret_cast<float*>(sJ + 2 * 128);           // K x Ng scaled parameters (when resident)
   __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_off_free[2], bar_d_full[kP1Bufs],
       bar_d_empty[kP1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
@@ -449,7 +450,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   __shared__ double sred[kTcThreads / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int n_gt = Npad / kTcGrainTile;
+  const int n_gt = Ng / kTcGrainTile;
   const int64_t n_tiles = tm.n_tiles;
   if (tid == 0) {
     abort_flag = 0;
@@ -479,16 +480,19 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     if (tid == kTcMmaWarp * 32) {
       // parameter image (and the float parameters when they fit): one bulk
       // copy per 32 KiB
-      const uint32_t total = (uint32_t)Npad * kRowBytes;
-      const uint32_t th_bytes = th_resident ? (uint32_t)K * Npad * 4 : 0u;
-      mbar_arrive_expect_tx(&bar_theta, total + th_bytes);
+      const uint32_t total = (uint32_t)Ng * kRowBytes;
+      const uint32_t row_t = (uint32_t)Ng * 4;  // one feature row of the float parameters
+      mbar_arrive_expect_tx(&bar_theta, total + (th_resident ? (uint32_t)K * row_t : 0u));
+      const uint8_t* src = img + (size_t)g0 * kRowBytes;
       for (uint32_t off = 0; off < total; off += 32768u) {
         const uint32_t n = total - off < 32768u ? total - off : 32768u;
-        bulk_g2s(sB + off, img + off, n, &bar_theta);
+        bulk_g2s(sB + off, src + off, n, &bar_theta);
       }
-      for (uint32_t off = 0; off < th_bytes; off += 32768u) {
-        const uint32_t n = th_bytes - off < 32768u ? th_bytes - off : 32768u;
-        bulk_g2s(reinterpret_cast<uint8_t*>(sTh) + off, reinterpret_cast<const uint8_t*>(th32t) + off, n, &bar_theta);
+      for (int k = 0; th_resident && k < K; ++k) {
+        const uint8_t* rsrc = reinterpret_cast<const uint8_t*>(th32t + (size_t)k * Npad + g0);
+        uint8_t* rdst = reinterpret_cast<uint8_t*>(sTh + (size_t)k * Ng);
+        for (uint32_t off = 0; off < row_t; off += 32768u)
+          bulk_g2s(rdst + off, rsrc + off, row_t - off < 32768u ? row_t - off : 32768u, &bar_theta);
       }
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
       int64_t c = 0;  // grain-tile counter over the whole loop
@@ -523,12 +527,21 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     // indices, coordinates and labels are fetched while this one is written
     const int p0 = tid - kTcConsumers;
     // feature-major parameters: lanes that read consecutive grains hit
-    // consecutive banks
-    const float* thp = th_resident ? sTh : th32t;
+    // consecutive banks; grain i of this launch (global g0 + i)
+    const float* thp = th_resident ? sTh : th32t + g0;
+    const int ldt = th_resident ? Ng : Npad;
     auto dot_t = [&](int i, const float* e) {
       float acc = thp[i] * e[0];
 #pragma unroll
-      for (int k = 1; k < K; ++k) acc = fmaf(thp[(int64_t)k * Npad + i], e[k], acc);
+      for (int k = 1; k < K; ++k) acc = fmaf(thp[(int64_t)k * ldt + i], e[k], acc);
+      return acc;
+    };
+    // any grain (the label may lie outside this launch's grains)
+    auto dot_g = [&](int G, const float* e) {
+      if (G >= g0 && G < g0 + Ng) return dot_t(G - g0, e);
+      float acc = th32t[G] * e[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) acc = fmaf(th32t[(int64_t)k * Npad + G], e[k], acc);
       return acc;
     };
     bool ok = !th_resident || mbar_wait_warp(&bar_theta, 0, &abort_flag, status);
@@ -577,17 +590,19 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         if (jc[u] >= 0) {
           const int G = Gc[u];
           if ((unsigned)G < (unsigned)N) {
-            lg = dot_t(G, ec) + dot_t(G, de);
+            lg = dot_g(G, ec) + dot_g(G, de);
             start = lg;
           } else {
             lg = NAN;
           }
+          // one of the launches owns the label logit of a grain-split pass
+          if (lg_out && (G >= g0 && G < g0 + Ng || ((unsigned)G >= (unsigned)N && g0 == 0))) lg_out[jc[u]] = lg;
         }
         sLG[s * 128 + p] = start;
         sLGv[s * 128 + p] = lg;
         sJ[s * 128 + p] = (long long)jc[u];
       }
-      for (int i = p0; i < Npad; i += kTcProducers) sOff[s * Npad + i] = i < N ? dot_t(i, ec) : 0.f;
+      for (int i = p0; i < Ng; i += kTcProducers) sOff[s * Ng + i] = g0 + i < N ? dot_t(i, ec) : 0.f;
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
     }
@@ -647,16 +662,17 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         // the thread's 128 columns in four 32-column chunks, each loaded
         // while the one before is used
         const int cbase = gt * kTcGrainTile + half * 128;
-        const float* off = sOff + s * Npad + cbase;
+        const float* off = sOff + s * Ng + cbase;
+        const int nrem = N - g0 - cbase;  // valid grains from this chunk on
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 32, RB);
-        chunk(RA, off, N - cbase, m, ssum);
+        chunk(RA, off, nrem, m, ssum);
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 64, RA);
-        chunk(RB, off + 32, N - cbase - 32, m, ssum);
+        chunk(RB, off + 32, nrem - 32, m, ssum);
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 96, RB);
-        chunk(RA, off + 64, N - cbase - 64, m, ssum);
+        chunk(RA, off + 64, nrem - 64, m, ssum);
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
@@ -669,7 +685,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
             pre = true;
           }
         }
-        chunk(RB, off + 96, N - cbase - 96, m, ssum);
+        chunk(RB, off + 96, nrem - 96, m, ssum);
       }
       if (!ok) break;
       // combine the two column halves of each pixel (bounded mbarrier
@@ -692,9 +708,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         if (j >= 0) {
           const float mm = fmaxf(m, o.x);
           const float sum = ssum * Arith<float>::ex(m - mm) + o.y * Arith<float>::ex(o.x - mm);
-          const float lse = mm + Arith<float>::lg(sum);
-          lse_out[j] = lse;
-          racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
+          if (ms_out) {
+            ms_out[j] = make_float2(mm, sum);  // this launch's grains only: merged later
+          } else {
+            const float lse = mm + Arith<float>::lg(sum);
+            lse_out[j] = lse;
+            racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
+          }
         }
       }
       mbar_arrive(&bar_off_free[s]);
@@ -1082,6 +1102,40 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
 }
 
 // ---------------------------------------------------------------------------
+// Log-sum-exp of a grain-split pass 1: the (max, sum) of every group of
+// grains per pixel combine into log2 S(x); the objective terms l_G - log2 S
+// are summed per block in a fixed order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float* __restrict__ lg,
+               float* __restrict__ lse_out, double* __restrict__ obj_part, const int* __restrict__ status) {
+  __shared__ double sred[8];
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  double r = 0.0;
+  if (j < P) {
+    float m = -INFINITY;
+    for (int q = 0; q < n_grp; ++q) m = fmaxf(m, ms[(int64_t)q * P + j].x);
+    float sum = 0.f;
+    for (int q = 0; q < n_grp; ++q) {
+      const float2 v = ms[(int64_t)q * P + j];
+      if (v.y > 0.f) sum = fmaf(v.y, Arith<float>::ex(v.x - m), sum);
+    }
+    const float l = m + Arith<float>::lg(sum);
+    lse_out[j] = l;
+    r = (double)(lg[j] - l) * Arith<float>::to_nat;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sred[w];
+    obj_part[blockIdx.x] = *status ? NAN : t;  // a pass-1 launch gave up
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Label part of eq. (grad): sum_{x in G_i} eta(x) per grain, at the points
 // of the tile walk of the two passes.  A warp sums the features of each
 // group of equal labels in fp32 (a fixed butterfly order), and lane k adds
@@ -1206,21 +1260,30 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int Npad = (N + kTcGrainTile - 1) / kTcGrainTile * kTcGrainTile;  // parameter image rows
   const size_t row_bytes = (size_t)KT * 2;
   constexpr size_t kCap = 220 * 1024;
-  // image, 2 operand stages, 2 x centre logits, 2 x (max, sum), 2 x start,
-  // 2 x label logit, 2 x pixel index
-  const size_t smem1_base = (size_t)Npad * row_bytes + 2 * kTcPixTile * row_bytes + 2 * (size_t)Npad * 4 +
-                            2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 + 2 * kTcPixTile * 8;
-  // the float parameters join the image in shared memory when they fit
-  const size_t th_bytes = (size_t)K * Npad * 4;
-  const int th_resident = smem1_base + th_bytes <= kCap ? 1 : 0;
-  const size_t smem1 = smem1_base + (th_resident ? th_bytes : 0);
+  // pass 1 keeps the image of ng grains resident: image, 2 operand stages,
+  // 2 x centre logits, 2 x (max, sum), 2 x start, 2 x label logit, 2 x pixel
+  // index, and the float parameters when they fit too.  More grains than
+  // one SM holds are split into groups of ng, one launch each, whose
+  // (max, sum) per pixel are merged afterwards.
+  auto p1_bytes = [&](size_t ng, bool th_res) {
+    return ng * row_bytes + 2 * kTcPixTile * row_bytes + 2 * ng * 4 + 2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 +
+           2 * kTcPixTile * 8 + (th_res ? (size_t)K * ng * 4 : 0);
+  };
+  int n_grp = 1, Ng = Npad;
+  while (p1_bytes((size_t)Ng, false) > kCap && Ng > kTcGrainTile) {
+    ++n_grp;
+    Ng = ((Npad + n_grp - 1) / n_grp + kTcGrainTile - 1) / kTcGrainTile * kTcGrainTile;
+  }
+  n_grp = (Npad + Ng - 1) / Ng;
+  const int th_resident = p1_bytes((size_t)Ng, true) <= kCap ? 1 : 0;
+  const size_t smem1 = p1_bytes((size_t)Ng, th_resident != 0);
   // pass-2 stages: four pixel-operand and two gradient-operand stages when
   // they fit, else fewer
   using L2 = Pass2Layout<DIM, D, KS>;
   constexpr int NB = L2::bytes(4, 2) <= kCap ? 4 : (L2::bytes(3, 2) <= kCap ? 3 : (L2::bytes(2, 1) <= kCap ? 2 : 1));
   constexpr int NA = L2::bytes(NB, 2) <= kCap ? 2 : 1;
   const size_t smem2 = L2::bytes(NB, NA);
-  if (smem1 > kCap || smem2 > kCap) return PD_ENOTSUP;  // too many grains for a resident image
+  if (smem1 > kCap || smem2 > kCap) return PD_ENOTSUP;
   // pixel-centre numerators 2k+1-n stay exact integers in fp32
   if (!c.g.coords && std::max(c.g.n0, std::max(c.g.n1, c.g.n2)) > (int64_t(1) << 23)) return PD_ENOTSUP;
   // at least 120 KiB of dynamic shared memory per CTA keeps one CTA per SM,
@@ -1232,6 +1295,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int sms = device_sm_count();
   const int64_t n_tiles = tm.n_tiles;
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
+  const int gridm = (int)((P + 255) / 256);  // merge blocks of a grain-split pass 1
   const int gblocks = (N + 127) / 128;  // pass-2 grain blocks
   // pass 2: chunks of kP2ChunkTiles tiles (one gradient partial each),
   // shared out in contiguous runs over one wave of CTAs per grain block
@@ -1243,7 +1307,9 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   float* th32 = sc.get<float>((size_t)N * KP32);
   float* th32t = sc.get<float>((size_t)K * Npad);
   float* lse = sc.get<float>((size_t)P);
-  double* objp = sc.get<double>((size_t)grid1);
+  double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
+  float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
+  float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
   double* part = c.grad ? sc.get<double>((size_t)n_chunks * N * K) : nullptr;
   unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   int* status = sc.get<int>(1);
@@ -1260,9 +1326,14 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
-  PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
-           k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, img, th32t, th_resident, lse, objp,
-                                                    status));
+  for (int q = 0; q < n_grp; ++q) {
+    const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
+    PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
+             k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, lse,
+                                                      objp, ms ? ms + (size_t)q * P : nullptr, lgb, status));
+  }
+  if (n_grp > 1)
+    PD_TIMED(st, "tc_merge_lse", k_tc_merge_lse<<<gridm, 256, 0, st>>>(ms, n_grp, P, lgb, lse, objp, status));
   // |eta| <= 1, so a grain's label sum is bounded by P: the largest
   // power-of-two scale that keeps P * scale below 2^62
   int bits = 0;
@@ -1281,7 +1352,9 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
              k2<<<grid2, kP2Threads, smem2_req, st>>>(c.g, tm, N, img, th32, lse, n_chunks, part, status));
   }
-  if (c.obj) PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, grid1, 1.0 / (double)P, c.obj));
+  if (c.obj)
+    PD_TIMED(st, "reduce_obj",
+             k_reduce_obj<<<1, 1024, 0, st>>>(objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P, c.obj));
   if (c.grad) {
     const int64_t NK = (int64_t)N * K;
     PD_TIMED(st, "reduce_parts",

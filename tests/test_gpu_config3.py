@@ -36,6 +36,17 @@ def centres(idx):
     return np.stack([c(k0), c(k1), c(k2)], 1)
 
 
+def morton(idx):
+    """Z-curve key of linear voxel indices (bits of x, y, z interleaved)."""
+    n = SHAPE[0]
+    k = [idx % n, (idx // n) % n, idx // (n * n)]
+    key = np.zeros_like(idx)
+    for b in range(8):
+        for a in range(3):
+            key |= ((k[a] >> b) & 1) << (3 * b + a)
+    return key
+
+
 @pytest.fixture(scope="module")
 def apd():
     y, w, A = synth.apd_params(synth.SEED_BASE + 2, N0, dim=3)
@@ -67,6 +78,23 @@ def test_subsample_matches_oracle(apd, d):
     assert abs(obj32.item() - phi_o) <= 1e-5 * abs(phi_o)
     assert rel(grad32.cpu().numpy(), grad_o) <= 1e-3
     if d == 2:
+        # tensor cores: their tiles are 128 consecutive points of the list
+        # and every logit is split at the tile's first point, so a point
+        # list must be ordered along space; Phi and its gradient do not
+        # depend on the order, so the same voxels in Morton (z-curve) order
+        # are compared with the same oracle values.  At this density (one
+        # voxel in 256) a tile still spans about 32^3 voxels, and the fp32
+        # accumulation of the tensor cores acts on logit parts 8x larger
+        # than on the full grid's 8x4x4 tiles: the bound is 5e-4 here, 1e-5
+        # on the full grid (test_full_grid_properties)
+        order = np.argsort(morton(idx), kind="stable")
+        gm = pd.Grid(coords=torch.from_numpy(np.ascontiguousarray(pts[order])).cuda())
+        dlm = torch.from_numpy(np.ascontiguousarray(lab[order]).astype(np.int32)).cuda()
+        obj3, grad3 = pd.pd_objective_grad(gm, dlm, N, dth, d, EPS, prec=pd.PD_BF16X3)
+        print("3-D d=2 point list (z-order): bf16x3 rel err phi %.2e grad %.2e" % (
+            abs(obj3.item() - phi_o) / abs(phi_o), rel(grad3.cpu().numpy(), grad_o)))
+        assert abs(obj3.item() - phi_o) <= 5e-4 * abs(phi_o)
+        assert rel(grad3.cpu().numpy(), grad_o) <= 2e-3
         v = synth.random_theta(synth.SEED_BASE + 40, N, K, 1e-3)
         hv_o = O.hvp(g, lab, N, d, EPS, th, v)
         hv = pd.pd_hvp(grid, dl, N, dth, torch.from_numpy(v).cuda(), d, EPS, prec=pd.PD_FP64)
@@ -89,6 +117,11 @@ def test_full_grid_properties(apd):
     # gauge invariance
     c = torch.from_numpy(synth.random_theta(5, 1, 10, 0.3)).cuda()
     o1, g1 = pd.pd_objective_grad(grid, lab, N, th_true, d, EPS, prec=pd.PD_FP64)
+    # the tensor cores on the full grid (8 x 4 x 4 voxel tiles) against FP64
+    o3, g3 = pd.pd_objective_grad(grid, lab, N, th_true, d, EPS, prec=pd.PD_BF16X3)
+    print("3-D full grid d=2: bf16x3 rel err vs fp64: phi %.2e grad %.2e" % (
+        abs(o3.item() - o1.item()) / abs(o1.item()), rel(g3.cpu().numpy(), g1.cpu().numpy())))
+    assert abs(o3.item() - o1.item()) <= 1e-5 * abs(o1.item())
     o2, g2 = pd.pd_objective_grad(grid, lab, N, th_true + c, d, EPS, prec=pd.PD_FP64)
     assert abs(o1.item() - o2.item()) <= 1e-9 * abs(o1.item())
     assert rel(g2.cpu().numpy(), g1.cpu().numpy()) <= 1e-8

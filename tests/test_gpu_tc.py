@@ -85,29 +85,27 @@ def test_tc_unsupported_shapes():
     with pytest.raises(pd.PdError) as e:
         pd.pd_objective_grad(grid, lab, 3, th, 7, 0.1, prec=pd.PD_BF16X3)   # K = 36 > 32
     assert e.value.code == pd.PD_ENOTSUP
-    # the resident parameter image of 1000 grains at K = 28 (bf16x3: three
-    # 32-column terms, 192 bytes a grain) exceeds shared memory
-    th = torch.zeros((1000, 28), dtype=torch.float64, device="cuda")
+    th = torch.zeros((3, 15), dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(th)
     with pytest.raises(pd.PdError) as e:
-        pd.pd_objective_grad(grid, lab, 1000, th, 6, 0.1, prec=pd.PD_BF16X3)
+        pd.pd_hvp(grid, lab, 3, th, v, 4, 0.1, prec=pd.PD_BF16X3)          # no tensor-core HVP
     assert e.value.code == pd.PD_ENOTSUP
 
 
-def test_tc_largest_resident_image():
-    # K = 15 in bf16x3: 1792 grains is the largest parameter image that
-    # stays resident in shared memory; one more grain block is refused
-    shape, N, d, eps = (64, 48), 1792, 4, 2e-2
+@pytest.mark.parametrize("N,d", [(1792, 4), (1793, 4), (2300, 4), (1000, 6)])
+def test_tc_grain_groups(N, d):
+    # K = 15 in bf16x3: 1792 grains is the largest parameter image one SM
+    # holds; beyond it (and at K = 28 from about 700 grains) pass 1 runs in
+    # groups of grains whose log-sum-exp parts are merged
+    shape, eps = (64, 48), 2e-2
     g = O.Grid(shape)
+    K = O.K(2, d)
     lab = synth.random_labels(37, g.P, N)
-    th = synth.random_theta(38, N, 15, 0.02)
+    th = synth.random_theta(38, N, K, 0.02)
     phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
     phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
     assert abs(phi - phi_o) <= 1e-5 * abs(phi_o), (phi, phi_o)
     assert rel(grad, grad_o) <= 1e-4, rel(grad, grad_o)
-    th2 = torch.zeros((1793, 15), dtype=torch.float64, device="cuda")
-    with pytest.raises(pd.PdError) as e:
-        pd.pd_objective_grad(pd.Grid(shape), dev(lab), 1793, th2, d, eps, prec=pd.PD_BF16X3)
-    assert e.value.code == pd.PD_ENOTSUP
 
 
 @pytest.mark.slow
