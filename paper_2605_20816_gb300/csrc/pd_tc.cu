@@ -619,19 +619,38 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       if (nv <= 0) return;
       float v[32];
       const float4* off4 = reinterpret_cast<const float4*>(off);  // 16-byte aligned: cbase is a multiple of 32
+      if (nv >= 32) {  // (warp-uniform) a full chunk: packed adds, no masking
 #pragma unroll
-      for (int q = 0; q < 32; q += 4) {
-        const float4 o = off4[q >> 2];
-        v[q] = q < nv ? __uint_as_float(r[q]) + o.x : -INFINITY;
-        v[q + 1] = q + 1 < nv ? __uint_as_float(r[q + 1]) + o.y : -INFINITY;
-        v[q + 2] = q + 2 < nv ? __uint_as_float(r[q + 2]) + o.z : -INFINITY;
-        v[q + 3] = q + 3 < nv ? __uint_as_float(r[q + 3]) + o.w : -INFINITY;
+        for (int q = 0; q < 32; q += 4) {
+          const float4 o = off4[q >> 2];
+          const float2 a = __fadd2_rn(make_float2(__uint_as_float(r[q]), __uint_as_float(r[q + 1])), make_float2(o.x, o.y));
+          const float2 b =
+              __fadd2_rn(make_float2(__uint_as_float(r[q + 2]), __uint_as_float(r[q + 3])), make_float2(o.z, o.w));
+          v[q] = a.x;
+          v[q + 1] = a.y;
+          v[q + 2] = b.x;
+          v[q + 3] = b.y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
+          const float4 o = off4[q >> 2];
+          v[q] = q < nv ? __uint_as_float(r[q]) + o.x : -INFINITY;
+          v[q + 1] = q + 1 < nv ? __uint_as_float(r[q + 1]) + o.y : -INFINITY;
+          v[q + 2] = q + 2 < nv ? __uint_as_float(r[q + 2]) + o.z : -INFINITY;
+          v[q + 3] = q + 3 < nv ? __uint_as_float(r[q + 3]) + o.w : -INFINITY;
+        }
       }
       const float cm = tree_max32(v);
       if (__all_sync(0xffffffffu, cm < m - 127.f)) return;
       const float mn = fmaxf(m, cm);
+      const float2 nmn = make_float2(-mn, -mn);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] = Arith<float>::ex(v[q] - mn);
+      for (int q = 0; q < 32; q += 2) {
+        const float2 a = __fadd2_rn(make_float2(v[q], v[q + 1]), nmn);
+        v[q] = Arith<float>::ex(a.x);
+        v[q + 1] = Arith<float>::ex(a.y);
+      }
       ssum = fmaf(ssum, Arith<float>::ex(m - mn), tree_sum32(v));
       m = mn;
     };
@@ -1011,9 +1030,10 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
         uint32_t hw[4];
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
-          const float c0 = -Arith<float>::ex(__uint_as_float(r[q8 + u]) - (lv[u] - off));
-          const float c1 = -Arith<float>::ex(__uint_as_float(r[q8 + u + 1]) - (lv[u + 1] - off));
-          const __half2 h = __floats2half2_rn(c0, c1);
+          // l - log2 S = r + (off - lv), two pixels per packed fp32 add
+          const float2 t = __fadd2_rn(make_float2(off, off), make_float2(-lv[u], -lv[u + 1]));
+          const float2 x = __fadd2_rn(make_float2(__uint_as_float(r[q8 + u]), __uint_as_float(r[q8 + u + 1])), t);
+          const __half2 h = __floats2half2_rn(-Arith<float>::ex(x.x), -Arith<float>::ex(x.y));
           hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
         }
         *reinterpret_cast<uint4*>(a2 + kmaj(gr, q0 + q8, kTcPixTile)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
