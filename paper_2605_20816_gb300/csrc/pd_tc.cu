@@ -86,6 +86,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_addr(b)) : "memory");
   (void)state;
 }
+// Adds bytes to the transaction count of the current phase (no arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
   uint64_t state;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
@@ -284,8 +288,7 @@ __device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float*
 // ---------------------------------------------------------------------------
 template <int KS>
 __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Npad, int K, int KW, double scale,
-                                 uint8_t* __restrict__ img, float* __restrict__ th32, int KP32,
-                                 float* __restrict__ th32t) {
+                                 uint8_t* __restrict__ img, float* __restrict__ th32t) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (row, k) pairs
   if (q >= (int64_t)Npad * KW) return;
   const int r = (int)(q / KW), k = (int)(q % KW);
@@ -298,7 +301,6 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
   const uint16_t parts[3] = {h, m, l};
   const int KT = KW * n_terms(KS);
   for (int t = 0; t < n_terms(KS); ++t) *reinterpret_cast<uint16_t*>(img + kmaj(r, t * KW + k, KT)) = parts[t];
-  if (r < N && k < KP32) th32[(int64_t)r * KP32 + k] = k < K ? (float)t : 0.f;
   if (k < K) th32t[(int64_t)k * Npad + r] = (float)t;  // transposed, zero rows beyond N
 }
 
@@ -416,6 +418,30 @@ __device__ __forceinline__ bool is_consumer(int warp) { return warp < 8; }
 __device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp < kTcMmaWarp; }
 
 // ---------------------------------------------------------------------------
+// Centre logits theta'_i . eta(c_t) of every tile t and grain i, the fp32
+// part of the split logits of both passes (zero for padding grains); one
+// block per tile.  The same fma order as a per-grain fp32 dot product.
+// ---------------------------------------------------------------------------
+template <int DIM, int D>
+__global__ void __launch_bounds__(256)
+k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, int Npad, float* __restrict__ off) {
+  constexpr int K = basis_K(DIM, D);
+  const int64_t t = blockIdx.x;
+  float x[DIM], c[DIM], ec[K];
+  tile_pixel<DIM>(g, tm, t, 0, x, c);
+  legendre_features<DIM, D>(c, ec);
+  for (int i = threadIdx.x; i < Npad; i += blockDim.x) {
+    float acc = 0.f;
+    if (i < N) {
+      acc = th32t[i] * ec[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) acc = fmaf(th32t[(int64_t)k * Npad + i], ec[k], acc);
+    }
+    off[t * Npad + i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Pass 1: log2 S(x) per pixel and objective partials.
 // ---------------------------------------------------------------------------
 constexpr int kP1Bufs = 2;  // logit tiles in flight in TMEM (2 x 256 columns)
@@ -424,12 +450,11 @@ template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng,
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
-           float* __restrict__ lse_out, double* __restrict__ obj_part, float2* __restrict__ ms_out,
-           float* __restrict__ lg_out, int* __restrict__ status) {
+           const float* __restrict__ offg, float* __restrict__ lse_out, double* __restrict__ obj_part,
+           float2* __restrict__ ms_out, float* __restrict__ lg_out, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
-  constexpr int KP32 = padded_K<float>(K);
   constexpr uint32_t kRowBytes = KT * 2;
   constexpr uint32_t kTileBytes = kTcPixTile * kRowBytes;
   constexpr uint32_t IDESC = idesc_bf16(128, kTcGrainTile);
@@ -437,7 +462,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;                                            // Ng x KT (this launch's grains)
   uint8_t* sA = smem + (size_t)Ng * kRowBytes;                   // 2 stages x 128 x KT
-  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Ng centre logits
+  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Ng centre logits (bulk copied)
   float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Ng);     // 2 stages x 128 (max, sum) of half 1
   float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);        // 2 stages x 128 starting max
   float* sLGv = sLG + 2 * 128;                                   // 2 stages x 128 label logits
@@ -575,6 +600,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       if (use >= 1 && (!mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status) ||
                        !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)))
         break;
+      if (p0 == 0) {
+        // the tile's centre logits of this launch's grains, by one bulk copy
+        // that the stage's barrier also waits for
+        fence_proxy_async();
+        mbar_expect_tx(&bar_a_full[s], (uint32_t)Ng * 4);
+        bulk_g2s(sOff + s * Ng, offg + t * Npad + g0, (uint32_t)Ng * 4, &bar_a_full[s]);
+      }
       float ec[K];
       legendre_features<DIM, D>(cc, ec);
 #pragma unroll
@@ -602,7 +634,6 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         sLGv[s * 128 + p] = lg;
         sJ[s * 128 + p] = (long long)jc[u];
       }
-      for (int i = p0; i < Ng; i += kTcProducers) sOff[s * Ng + i] = g0 + i < N ? dot_t(i, ec) : 0.f;
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
     }
@@ -790,7 +821,7 @@ struct Pass2Layout {
   static constexpr int KT = KW * n_terms(KS);
   static constexpr int ET = KS == 1 ? 1 : 2;  // fp16 terms of eta in the gradient contraction
   static constexpr int N2 = ET * KW;           // its MMA N: eta_h (and eta_l) columns
-  static constexpr int KE = (K + 3) / 4 * 4;  // tile-centre features per stage
+
   static constexpr uint32_t kABytes = 128u * KT * 2;             // theta block
   static constexpr uint32_t kSboB = (uint32_t)KT * 16 + 16;
   static constexpr uint32_t kBBytes = 16 * kSboB;                // 128 pixel rows
@@ -799,7 +830,7 @@ struct Pass2Layout {
   static constexpr uint32_t kB2Term = (KW / 8) * kSbo2;
   static constexpr uint32_t kB2Bytes = ET * kB2Term;           // rows: eta_h features, then eta_l
   static constexpr uint32_t kA2Bytes = 128u * kTcPixTile * 2;    // c: 128 grains x 128 pixels, fp16
-  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + KE * 4;
+  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + 128 * 4;
   static constexpr size_t bytes(int nb, int na) { return kABytes + (size_t)nb * kPerB + (size_t)na * kA2Bytes; }
 };
 
@@ -810,11 +841,10 @@ constexpr int kP2ChunkTiles = 32;     // tiles per gradient partial (fp32 accumu
 
 template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2Threads, 1)
-k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const float* __restrict__ th32,
+k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
            const float* __restrict__ lse, int64_t n_chunks, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
-  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2, KE = L::KE;
-  constexpr int KP32 = padded_K<float>(K);
+  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
   constexpr uint32_t IDESC2 = idesc_f16(128, N2);
   constexpr int D2COL = kP2LogitBufs * kTcPixTile;  // TMEM: D1 ring [0, 384), D2 x 2 from 384
@@ -826,7 +856,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
   uint8_t* sB2 = sB + NB * L::kBBytes;            // NB stages of eta^T
   uint8_t* sA2 = sB2 + NB * L::kB2Bytes;          // NA stages of c
   float* sLse = reinterpret_cast<float*>(sA2 + NA * L::kA2Bytes);  // [NB][128] log2 S of the pixels
-  float* sEc = sLse + NB * kTcPixTile;                             // [NB][KE] eta(tile centre)
+  float* sOffP = sLse + NB * kTcPixTile;                           // [NB][128] centre logits of the block
   __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[kP2LogitBufs],
       bar_d1_empty[kP2LogitBufs], bar_a2_full[NA], bar_a2_empty[NA], bar_d2_full[2], bar_d2_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
@@ -947,6 +977,13 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
       const float2 lsc = make_float2(lsn[0], lsn[1]);
       if (t + 1 < n_pt) fetch(t + 1);
       if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
+      if (q2 == 0) {
+        // the block's centre logits for this tile, by one bulk copy that the
+        // stage's barrier also waits for
+        fence_proxy_async();
+        mbar_expect_tx(&bar_b_full[s], 128 * 4);
+        bulk_g2s(sOffP + s * 128, offg + (t_begin + t) * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
+      }
       float ec[K], e0[K], e1[K];
       legendre_features<DIM, D>(cc, ec);
       legendre_features<DIM, D>(xc[0], e0);
@@ -978,10 +1015,6 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
         }
       }
       *reinterpret_cast<float2*>(sLse + s * kTcPixTile + q2) = lsc;
-      if (q2 == 0) {
-#pragma unroll
-        for (int k = 0; k < KE; ++k) sEc[s * KE + k] = k < K ? ec[k] : 0.f;
-      }
       fence_proxy_async();
       mbar_arrive(&bar_b_full[s]);
     }
@@ -990,9 +1023,6 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
     const int gr = quad * 32 + lane;        // grain row of the block == TMEM lane
     const int i = gb * 128 + gr;            // this thread's grain
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    float th[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) th[k] = i < N ? th32[(int64_t)i * KP32 + k] : 0.f;
     int n_done = 0;  // chunks whose partial this thread has written (first warpgroup)
     // the D2 row of chunk u of this CTA: one double partial per grain
     auto read_chunk = [&](int u) -> bool {
@@ -1048,7 +1078,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
     for (int t = 0; t < n_pt; ++t) {
       const int s = t % NB, b1 = t % kP2LogitBufs, a = t % NA;
       const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
-      // sLse and sEc of the stage were written by the producers
+      // sLse and sOffP of the stage were written by the producers
       if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) { ok = false; break; }
       if (!pre) {
         if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t / kP2LogitBufs) & 1), &abort_flag, status)) {
@@ -1061,18 +1091,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, const uint8_t* __restrict__ img, const flo
       tmem_wait_ld();
       tmem_ld32(tmem + lane_base + col + 32, RB);
       // this grain's centre logit for the tile
-      float off = 0.f;
-      {
-        const float4* ec4 = reinterpret_cast<const float4*>(sEc + s * KE);
-#pragma unroll
-        for (int k4 = 0; k4 < KE / 4; ++k4) {
-          const float4 e = ec4[k4];
-          if (4 * k4 + 0 < K) off = fmaf(th[4 * k4 + 0], e.x, off);
-          if (4 * k4 + 1 < K) off = fmaf(th[4 * k4 + 1], e.y, off);
-          if (4 * k4 + 2 < K) off = fmaf(th[4 * k4 + 2], e.z, off);
-          if (4 * k4 + 3 < K) off = fmaf(th[4 * k4 + 3], e.w, off);
-        }
-      }
+      const float off = sOffP[s * 128 + gr];
       if (t >= NA && !mbar_wait_warp(&bar_a2_empty[a], (uint32_t)(((t / NA) - 1) & 1), &abort_flag, status)) {
         ok = false;
         break;
@@ -1274,7 +1293,6 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
-  constexpr int KP32 = padded_K<float>(K);
   const int N = c.N;
   const int64_t P = c.g.P;
   const int Npad = (N + kTcGrainTile - 1) / kTcGrainTile * kTcGrainTile;  // parameter image rows
@@ -1324,8 +1342,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
 
   Scratch sc(st);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
-  float* th32 = sc.get<float>((size_t)N * KP32);
   float* th32t = sc.get<float>((size_t)K * Npad);
+  float* offg = sc.get<float>((size_t)n_tiles * Npad);  // centre logits [tile][grain]
   float* lse = sc.get<float>((size_t)P);
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
@@ -1341,16 +1359,18 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const int64_t n = (int64_t)Npad * KW;
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, Npad, K, KW, scale, img,
-                                                                                th32, KP32, th32t));
+                                                                                th32t));
   }
+  PD_TIMED(st, "tc_centre_logits",
+           (k_tc_centre_logits<DIM, D><<<(unsigned)n_tiles, 256, 0, st>>>(c.g, tm, th32t, N, Npad, offg)));
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
   for (int q = 0; q < n_grp; ++q) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
-             k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, lse,
-                                                      objp, ms ? ms + (size_t)q * P : nullptr, lgb, status));
+             k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, offg,
+                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, status));
   }
   if (n_grp > 1)
     PD_TIMED(st, "tc_merge_lse", k_tc_merge_lse<<<gridm, 256, 0, st>>>(ms, n_grp, P, lgb, lse, objp, status));
@@ -1370,7 +1390,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
       return PD_ECUDA;
     dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kP2Threads, smem2_req, st>>>(c.g, tm, N, img, th32, lse, n_chunks, part, status));
+             k2<<<grid2, kP2Threads, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, n_chunks, part, status));
   }
   if (c.obj)
     PD_TIMED(st, "reduce_obj",
