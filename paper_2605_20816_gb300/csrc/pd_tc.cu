@@ -419,25 +419,39 @@ __device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp
 
 // ---------------------------------------------------------------------------
 // Centre logits theta'_i . eta(c_t) of every tile t and grain i, the fp32
-// part of the split logits of both passes (zero for padding grains); one
-// block per tile.  The same fma order as a per-grain fp32 dot product.
+// part of the split logits of both passes (zero for padding grains).  A
+// block takes 256 grains (parameters in registers) and kCentreTiles tiles
+// (centre features in shared memory); the same fma order as a per-grain
+// fp32 dot product.
 // ---------------------------------------------------------------------------
+constexpr int kCentreTiles = 32;
+
 template <int DIM, int D>
 __global__ void __launch_bounds__(256)
 k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, int Npad, float* __restrict__ off) {
   constexpr int K = basis_K(DIM, D);
-  const int64_t t = blockIdx.x;
-  float x[DIM], c[DIM], ec[K];
-  tile_pixel<DIM>(g, tm, t, 0, x, c);
-  legendre_features<DIM, D>(c, ec);
-  for (int i = threadIdx.x; i < Npad; i += blockDim.x) {
-    float acc = 0.f;
-    if (i < N) {
-      acc = th32t[i] * ec[0];
+  __shared__ float sec[kCentreTiles][K];
+  const int i = blockIdx.x * 256 + threadIdx.x;  // < Npad
+  float th[K];
 #pragma unroll
-      for (int k = 1; k < K; ++k) acc = fmaf(th32t[(int64_t)k * Npad + i], ec[k], acc);
+  for (int k = 0; k < K; ++k) th[k] = i < N ? th32t[(int64_t)k * Npad + i] : 0.f;
+  for (int64_t t0 = (int64_t)blockIdx.y * kCentreTiles; t0 < tm.n_tiles; t0 += (int64_t)gridDim.y * kCentreTiles) {
+    const int nt = (int)min((int64_t)kCentreTiles, tm.n_tiles - t0);
+    __syncthreads();  // the previous group's features are used up
+    if (threadIdx.x < nt) {
+      float x[DIM], c[DIM], ec[K];
+      tile_pixel<DIM>(g, tm, t0 + threadIdx.x, 0, x, c);
+      legendre_features<DIM, D>(c, ec);
+#pragma unroll
+      for (int k = 0; k < K; ++k) sec[threadIdx.x][k] = ec[k];
     }
-    off[t * Npad + i] = acc;
+    __syncthreads();
+    for (int q = 0; q < nt; ++q) {
+      float acc = th[0] * sec[q][0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) acc = fmaf(th[k], sec[q][k], acc);
+      off[(t0 + q) * Npad + i] = acc;
+    }
   }
 }
 
@@ -1362,7 +1376,10 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
                                                                                 th32t));
   }
   PD_TIMED(st, "tc_centre_logits",
-           (k_tc_centre_logits<DIM, D><<<(unsigned)n_tiles, 256, 0, st>>>(c.g, tm, th32t, N, Npad, offg)));
+           (k_tc_centre_logits<DIM, D><<<dim3((unsigned)(Npad / 256),
+                                              (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles,
+                                                                          4096)),
+                                         256, 0, st>>>(c.g, tm, th32t, N, Npad, offg)));
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
