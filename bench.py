@@ -226,6 +226,26 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# replicas (one process per GPU, no data-path collective): the timing rule
+# ---------------------------------------------------------------------------
+def job_ms(ms_local: float, world: int, device) -> float:
+    """Whole-job time of the timed region: the maximum over the ranks."""
+    if world <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, pixels: int, grains: int, ms_step: float) -> float:
+    """Pixel-grain pairs per second of all replicas (each evaluates the whole
+    workload once per step: weak scaling)."""
+    return world * pixels * grains / (ms_step * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -275,14 +295,10 @@ def run_ours(args):
     sampler.mark(False)
     if world > 1:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_ms(sum(a.elapsed_time(b) for a, b in ev), world, "cuda")
     clocks = sampler.stop() if not args.no_clocks else None
     ms_step = ms / args.steps
-    value = world * P * N / (ms_step * 1e-3)
+    value = job_value(world, P, N, ms_step)
 
     # traced pass: per-kernel device time of the same steps
     pd.pd_prof_enable(True)
