@@ -158,7 +158,9 @@ def make_workload_gpu(pd, torch):
 
 def oracle_band(rows: int):
     """A band of `rows` grid rows of the same workload, as an explicit point
-    list, labelled by the oracle (only the CPU legs call this)."""
+    list, labelled by the oracle (only the CPU legs call this).  Every
+    generated grain stays in the objective (the band alone would empty most
+    of them), so the cost per pixel is that of the whole workload."""
     import oracle as O
     n1, n2 = SHAPE
     r0 = (n2 - rows) // 2
@@ -171,8 +173,7 @@ def oracle_band(rows: int):
     th[:, 3:] = z[:, 3:]
     lab, _ = O.assign(g, N_GRAINS, DEG, th)
     lab = synth.boundary_noise(lab, (n1, rows), NOISE, SEED + 7)
-    lab, n_eff, used = synth.compact(lab)
-    return O, g, lab.astype(np.int32), n_eff, np.ascontiguousarray(th[used])
+    return O, g, lab.astype(np.int32), N_GRAINS, np.ascontiguousarray(th)
 
 
 def cpu_oracle_rate(target_s: float):
