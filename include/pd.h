@@ -71,9 +71,9 @@ extern "C" {
 #define PD_BF16X3 3 /* as PD_BF16 with every operand split into three bf16
                       terms (hi+mid+lo), which recovers float-level accuracy
                       on the tensor cores                                     */
-/* The tensor-core precisions serve the objective and gradient (not the HVP)
- * for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid sides <= 2^23; other
- * combinations return PD_ENOTSUP.  The log-sum-exp pass keeps the grains'
+/* The tensor-core precisions serve the objective, the gradient and the
+ * Hessian-vector product for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid
+ * sides <= 2^23; other combinations return PD_ENOTSUP.  The log-sum-exp pass keeps the grains'
  * parameters resident in one SM's shared memory (about 104 bytes a grain
  * at K <= 16 in PD_BF16X3, up to 1792 grains); more grains are processed
  * in groups whose partial sums are merged, with a scratch buffer of
@@ -139,7 +139,8 @@ int pd_objective_grad(const pd_grid* grid, const int32_t* labels, int N,
  *   (H v)_i = -(1/(eps^2 P)) sum_x p_i(x) (u_i(x) - sum_k p_k(x) u_k(x)) eta(x),
  * u_i(x) = v_i . eta(x).  v, hv_out: device double[N][K].  labels are not
  * used by the Hessian but keep the call shape of pd_objective_grad (may be
- * NULL).  prec: PD_FP64 or PD_FP32. */
+ * NULL).  prec: any; the tensor-core precisions scale v by a power of two
+ * internally (their fp16 operands need |v| <= 1) and undo it exactly. */
 int pd_hvp(const pd_grid* grid, const int32_t* labels, int N,
            const double* theta, const double* v, const pd_eval_opts* opts,
            double* hv_out, void* stream);

@@ -229,9 +229,9 @@ int pd_hvp(const pd_grid* grid, const int32_t* labels, int N, const double* thet
   int rc = check_eval(grid, N, theta, opts, &g);
   if (rc) return rc;
   if (!v || !hv_out) return PD_EINVAL;
-  if (opts->prec != PD_FP64 && opts->prec != PD_FP32) return PD_ENOTSUP;
   device_sm_count();
   EvalCall c{g, grid->dim, opts->d, N, opts->prec, opts->eps, labels, theta, v, nullptr, nullptr, hv_out};
+  if (opts->prec == PD_BF16 || opts->prec == PD_BF16X3) return eval_tc(c, (cudaStream_t)stream);
   return eval_simt(c, (cudaStream_t)stream);
 }
 

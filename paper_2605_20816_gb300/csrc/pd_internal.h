@@ -89,6 +89,7 @@ int check_labels_simt(const int32_t* labels, int64_t P, int N, int* bad_dev, cud
 
 // pd_tc.cu (tensor-core evaluation); PD_ENOTSUP where a shape is not covered
 int eval_tc(const EvalCall& c, cudaStream_t st);
+int eval_tc_hvp(const EvalCall& c, cudaStream_t st);  // pd_tc_hvp.cu
 int selftest_wait_timeout(double seconds, int* status_out, cudaStream_t st);
 
 // pd_capi.cu

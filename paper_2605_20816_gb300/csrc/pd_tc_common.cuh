@@ -1,0 +1,514 @@
+// pd_tc_common.cuh -- building blocks of the tensor-core (tcgen05) passes:
+// PTX wrappers for mbarriers, TMEM, MMAs and bulk copies, the operand layouts,
+// the parameter images, the pixel tiles and the centre logits; included by
+// the objective/gradient passes (pd_tc.cu) and the Hessian-vector passes
+// (pd_tc_hvp.cu), each of which gets its own internal copy.
+//
+// Operands use the canonical K-major layout without swizzle: 8-row x
+// 16-byte core matrices, adjacent along K at 128 bytes (LBO) and along the
+// rows at KT*16 bytes (SBO), KT = the operand's total K width.
+//
+// Every wait on an mbarrier is bounded by a 1 s timeout on the global timer:
+// a wait that gives up sets PD_ETIMEOUT in a status word (the result then
+// becomes NaN), raises a CTA-wide abort flag so that the other waits give up
+// at once, and the CTA still frees its TMEM before it returns.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pd_simt_kernels.cuh"
+
+namespace pd {
+namespace {
+
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+constexpr int kTcConsumers = 256;                 // warps 0..7: TMEM consumers
+constexpr int kTcProducers = 64;                  // warps 8..9: pixel-operand producers, 2 pixels each
+constexpr int kTcMmaWarp = 10;                    // TMEM allocation and MMA issue
+constexpr int kTcThreads = 11 * 32;               // at most 3 warps per SM sub-partition
+constexpr int kTcCols = 512;                      // TMEM columns per CTA (one CTA per SM)
+constexpr int kTcGrainTile = 256;                 // pass-1 grains per MMA group (N of the MMA)
+constexpr int kTcPixTile = 128;                   // pixels per tile (both passes)
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_addr(b)) : "memory");
+  (void)state;
+}
+// Adds bytes to the transaction count of the current phase (no arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+  (void)state;
+}
+// Non-blocking probe of the phase (test_wait never suspends the thread).
+__device__ __forceinline__ bool mbar_peek(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the completion of the phase with the given parity.  Returns false
+// when the CTA aborted or the wait timed out (then the abort flag is raised
+// and PD_ETIMEOUT recorded).
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* status) {
+  if (mbar_test(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      if (status) atomicCAS(status, 0, PD_ETIMEOUT);
+      return false;
+    }
+  }
+}
+// Warp-uniform variant for the epilogue warps: the tcgen05.ld that follow a
+// wait are .sync.aligned, so the whole warp must agree on the outcome.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* status) {
+  const bool ok = mbar_wait(b, parity, abort_flag, status);
+  return __all_sync(0xffffffffu, ok);
+}
+// Bounded wait that ignores the abort flag: used once before TMEM is freed,
+// so that no MMA still writes the columns being released.
+__device__ __noinline__ void mbar_wait_drain(uint64_t* b, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_test(b, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) return;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] . B[smem]^T, both K-major, bf16 in, fp32 accumulate.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive once on the mbarrier when all previously issued MMAs of this
+// thread have completed.
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(b))
+               : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns: thread t of the warp reads
+// lane (base lane + t), columns col .. col+31 of the address.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+}
+
+
+// Shared-memory matrix descriptor, K-major, no swizzle (layout type 0),
+// descriptor version 1; lbo/sbo in bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: fp32 D, bf16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// The same with fp16 A and B.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Byte offset of element (row r, column k) of a K-major no-swizzle operand
+// whose core matrices lie lbo bytes apart along K and sbo bytes apart along
+// the rows.
+__host__ __device__ constexpr uint32_t kmaj_s(int r, int k, uint32_t lbo, uint32_t sbo) {
+  return (uint32_t)((r >> 3) * sbo + (k >> 3) * lbo + (r & 7) * 16 + (k & 7) * 2);
+}
+// The dense case: rows KT elements wide.
+__host__ __device__ constexpr uint32_t kmaj(int r, int k, int KT) { return kmaj_s(r, k, 128u, (uint32_t)KT * 16u); }
+
+
+// Term split of the operands.  KS is the number of products per logit (1
+// for PD_BF16, 6 for PD_BF16X3); n_terms(KS) the bf16 terms stored per
+// value.  Product s pairs parameter term theta_term(s) with feature term
+// eta_term(s): hh, hm, mh, hl, mm, lh.
+__host__ __device__ constexpr int n_terms(int KS) { return KS == 1 ? 1 : 3; }
+__host__ __device__ constexpr int theta_term(int s) { return s == 2 || s == 4 ? 1 : (s == 5 ? 2 : 0); }
+__host__ __device__ constexpr int eta_term(int s) { return s == 1 || s == 4 ? 1 : (s == 3 ? 2 : 0); }
+
+// The KS products of a logit chain: MMAs of K = 16 whose A and B
+// descriptors start at the term slices of the two operands (rows of KT
+// columns: slice t at column t*KW).  kind::f16, M = 128, N from idesc.
+template <int KS, int KW>
+__device__ __forceinline__ void mma_terms(uint32_t d, uint32_t aaddr, uint32_t a_sbo, bool a_theta, uint32_t baddr,
+                                          uint32_t b_sbo, uint32_t idesc) {
+#pragma unroll 1
+  for (int s = 0; s < KS; ++s) {
+    const int ta = KS == 1 ? 0 : (a_theta ? theta_term(s) : eta_term(s));
+    const int tb = KS == 1 ? 0 : (a_theta ? eta_term(s) : theta_term(s));
+#pragma unroll
+    for (int q = 0; q < KW / 16; ++q) {
+      const uint64_t ad = smem_desc(aaddr + (uint32_t)(ta * KW * 16 + q * 256), 128, a_sbo);
+      const uint64_t bd = smem_desc(baddr + (uint32_t)(tb * KW * 16 + q * 256), 128, b_sbo);
+      mma_bf16(d, ad, bd, idesc, (s > 0 || q > 0) ? 1u : 0u);
+    }
+  }
+}
+
+// Writes the terms of a feature row (pixel r) into a K-major operand.
+template <int K, int KW, int KS, uint32_t SBO = (uint32_t)KW * n_terms(KS) * 16>
+__device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float* eta) {
+  // hi, mid, lo bf16 terms (round to nearest, each of the remainder of the
+  // previous ones), two adjacent columns per 32-bit word
+  constexpr int NT = n_terms(KS);
+  uint32_t w[NT][KW / 2];
+#pragma unroll
+  for (int k = 0; k < KW; k += 2) {
+    float v0 = k < K ? eta[k] : 0.f, v1 = k + 1 < K ? eta[k + 1] : 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      w[t][k >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+      if (t + 1 < NT) {
+        const float2 f = __bfloat1622float2(h);
+        v0 -= f.x;
+        v1 -= f.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+#pragma unroll
+    for (int k8 = 0; k8 < KW; k8 += 8) {
+      const uint4 v = make_uint4(w[t][k8 / 2], w[t][k8 / 2 + 1], w[t][k8 / 2 + 2], w[t][k8 / 2 + 3]);
+      *reinterpret_cast<uint4*>(base + kmaj_s(r, t * KW + k8, 128u, SBO)) = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parameter images: rows = grains (padded to Npad with zero rows), K-major
+// no-swizzle, one slice of KW columns per term; plus float copies (grain
+// rows, and transposed K x Npad) used for the centre logits and the
+// label logit of the objective.
+// ---------------------------------------------------------------------------
+template <int KS>
+__global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Npad, int K, int KW, double scale,
+                                 const double* __restrict__ dscale, uint8_t* __restrict__ img,
+                                 float* __restrict__ th32t) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (row, k) pairs
+  if (q >= (int64_t)Npad * KW) return;
+  const int r = (int)(q / KW), k = (int)(q % KW);
+  const double t = (r < N && k < K) ? theta[(int64_t)r * K + k] * (dscale ? scale * *dscale : scale) : 0.0;
+  const uint16_t h = __bfloat16_as_ushort(__double2bfloat16(t));
+  const double r1 = t - (double)__bfloat162float(__ushort_as_bfloat16(h));
+  const uint16_t m = __bfloat16_as_ushort(__double2bfloat16(r1));
+  const double r2 = r1 - (double)__bfloat162float(__ushort_as_bfloat16(m));
+  const uint16_t l = __bfloat16_as_ushort(__double2bfloat16(r2));
+  const uint16_t parts[3] = {h, m, l};
+  const int KT = KW * n_terms(KS);
+  for (int t = 0; t < n_terms(KS); ++t) *reinterpret_cast<uint16_t*>(img + kmaj(r, t * KW + k, KT)) = parts[t];
+  if (k < K) th32t[(int64_t)k * Npad + r] = (float)t;  // transposed, zero rows beyond N
+}
+
+// ---------------------------------------------------------------------------
+// Pixel tiles.  A tile is 128 pixels that are close in space: a 16 x 8 block
+// of a 2-D grid or an 8 x 4 x 4 block of a 3-D grid (128 consecutive points
+// of a point list).  Every logit is split at the tile centre c,
+//   l_i(x) = theta'_i . eta(c) + theta'_i . (eta(x) - eta(c)),
+// the first part (one per grain and tile) on the CUDA cores in fp32 and the
+// second, small part on the tensor cores.  The tensor cores accumulate with
+// truncation, whose error is biased; keeping their operand small (|x - c|
+// is a few pixels) keeps that bias far below the float rounding of the
+// logits, which is unbiased.
+// ---------------------------------------------------------------------------
+struct TileMap {
+  int ntx, nty, ntz;      // tiles per axis (structured grids)
+  int64_t n_tiles;
+  int n0, n1, n2;         // grid sides
+  float f0, f1, f2;       // 1 / n_a rounded to float
+};
+
+template <int DIM>
+struct TileShape {
+  static constexpr int X = DIM == 2 ? 16 : 8;
+  static constexpr int Y = DIM == 2 ? 8 : 4;
+  static constexpr int Z = DIM == 2 ? 1 : 4;
+};
+
+// Pixel index of row r of tile t (or -1 outside the pixel set), its
+// coordinates x and the coordinates of the tile centre c.  Only 32-bit
+// integer arithmetic and fp32: a centre -1 + (2k+1)/n is formed as the exact
+// integer 2k+1-n times the float 1/n (exact when n is a power of two, else
+// within an ulp of the rounded value); both passes use this same function,
+// so the log-sum-exp of pass 1 belongs to the very points of pass 2.
+template <int DIM>
+__device__ __forceinline__ int64_t tile_pixel(const Geom& g, const TileMap& tm, int64_t t, int r, float* x,
+                                              float* c) {
+  if (g.coords) {
+    const int64_t j0 = t * kTcPixTile;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) c[a] = (float)g.coords[j0 * DIM + a];
+    const int64_t j = j0 + r;
+    if (j >= g.P) {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) x[a] = c[a];
+      return -1;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = (float)g.coords[j * DIM + a];
+    return j;
+  }
+  using TS = TileShape<DIM>;
+  const unsigned tt = (unsigned)t;
+  const unsigned tx = tt % (unsigned)tm.ntx;
+  const unsigned rest = tt / (unsigned)tm.ntx;
+  const int ty = (int)(rest % (unsigned)tm.nty);
+  const int tz = (int)(rest / (unsigned)tm.nty);
+  const int px = (int)tx * TS::X + (r % TS::X);
+  const int py = ty * TS::Y + ((r / TS::X) % TS::Y);
+  const int pz = tz * TS::Z + (r / (TS::X * TS::Y));
+  c[0] = (float)(2 * ((int)tx * TS::X + TS::X / 2) + 1 - tm.n0) * tm.f0;
+  c[1] = (float)(2 * (ty * TS::Y + TS::Y / 2) + 1 - tm.n1) * tm.f1;
+  if (DIM == 3) c[2] = (float)(2 * (tz * TS::Z + TS::Z / 2) + 1 - tm.n2) * tm.f2;
+  x[0] = (float)(2 * px + 1 - tm.n0) * tm.f0;
+  x[1] = (float)(2 * py + 1 - tm.n1) * tm.f1;
+  if (DIM == 3) x[2] = (float)(2 * pz + 1 - tm.n2) * tm.f2;
+  if (px >= tm.n0 || py >= tm.n1 || (DIM == 3 && pz >= tm.n2)) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = c[a];
+    return -1;
+  }
+  return DIM == 2 ? px + (int64_t)tm.n0 * py : px + (int64_t)tm.n0 * (py + (int64_t)tm.n1 * pz);
+}
+
+template <int K>
+__device__ __forceinline__ float dot_f(const float* __restrict__ a, const float* __restrict__ b) {
+  float acc = a[0] * b[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) acc = fmaf(a[k], b[k], acc);
+  return acc;
+}
+
+__device__ __forceinline__ float tree_max32(const float* v) {
+  float a[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = fmaxf(v[q], v[q + 16]);
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) a[q] = fmaxf(a[q], a[q + w]);
+  return a[0];
+}
+__device__ __forceinline__ float tree_sum32(const float* v) {
+  float a[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = v[q] + v[q + 16];
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) a[q] = a[q] + a[q + w];
+  return a[0];
+}
+
+// ---------------------------------------------------------------------------
+// Warp roles (both passes): warps 0..7 consume TMEM (warp w reads lanes
+// 32 (w mod 4) .. +31, the access rule of tcgen05.ld, and the column half
+// w / 4 of each 128-column tile); warps 8..9 produce the pixel-side
+// operands of upcoming tiles (two pixels per thread); warp 10 allocates
+// TMEM and one of its threads issues every MMA.  Eleven warps keep at most
+// three on each SM sub-partition, which leaves 168 registers per thread.  Producers run ahead of the
+// consumers by the number of operand stages, so their global loads and
+// feature arithmetic overlap the consumers' work.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_consumer(int warp) { return warp < 8; }
+__device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp < kTcMmaWarp; }
+
+// ---------------------------------------------------------------------------
+// Centre logits theta'_i . eta(c_t) of every tile t and grain i, the fp32
+// part of the split logits of both passes (zero for padding grains).  A
+// block takes 256 grains (parameters in registers) and kCentreTiles tiles
+// (centre features in shared memory); the same fma order as a per-grain
+// fp32 dot product.
+// ---------------------------------------------------------------------------
+constexpr int kCentreTiles = 32;
+
+template <int DIM, int D>
+__global__ void __launch_bounds__(256)
+k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, int Npad, float* __restrict__ off) {
+  constexpr int K = basis_K(DIM, D);
+  __shared__ float sec[kCentreTiles][K];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const bool live = i < Npad;  // (every thread takes part in the barriers)
+  float th[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) th[k] = i < N ? th32t[(int64_t)k * Npad + i] : 0.f;
+  for (int64_t t0 = (int64_t)blockIdx.y * kCentreTiles; t0 < tm.n_tiles; t0 += (int64_t)gridDim.y * kCentreTiles) {
+    const int nt = (int)min((int64_t)kCentreTiles, tm.n_tiles - t0);
+    __syncthreads();  // the previous group's features are used up
+    if (threadIdx.x < nt) {
+      float x[DIM], c[DIM], ec[K];
+      tile_pixel<DIM>(g, tm, t0 + threadIdx.x, 0, x, c);
+      legendre_features<DIM, D>(c, ec);
+#pragma unroll
+      for (int k = 0; k < K; ++k) sec[threadIdx.x][k] = ec[k];
+    }
+    __syncthreads();
+    for (int q = 0; live && q < nt; ++q) {
+      float acc = th[0] * sec[q][0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) acc = fmaf(th[k], sec[q][k], acc);
+      off[(t0 + q) * Npad + i] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: gradient partials of one grain block over a contiguous run of
+// tiles (one wave of CTAs per grain block).  NB pixel-operand stages (up to
+// 4) and NA gradient-operand stages (up to 2), as many as shared memory
+// holds.  Two warps issue MMAs: one the logits, as far ahead as the three
+// TMEM logit buffers and the operand stages allow, the other the gradient
+// contractions, so neither waits behind the other.  The consumers pick the
+// next tile's logits up early when they are already there.  The gradient
+// accumulates in TMEM over chunks of kP2ChunkTiles tiles (two buffers,
+// alternating), and each chunk becomes one double partial per grain.
+//
+// Shared-memory operand layouts (all K-major, no swizzle):
+//   sB   pixel rows x KT feature differences; the 8-row groups lie
+//        KT*16 + 16 bytes apart, so that the producers' stores of even and
+//        of odd rows spread over all banks;
+//   sB2  features x 128 pixels (eta transposed); the 8-pixel core matrices
+//        lie 144 bytes apart along K, so that 32 threads storing one 32-bit
+//        word (two adjacent pixels) each hit 32 different banks;
+//   sA2  grains x 128 pixels of c, dense.
+// ---------------------------------------------------------------------------
+template <int DIM, int D, int KS>
+struct Pass2Layout {
+  static constexpr int K = basis_K(DIM, D);
+  static constexpr int KW = (K + 15) / 16 * 16;
+  static constexpr int KT = KW * n_terms(KS);
+  static constexpr int ET = KS == 1 ? 1 : 2;  // fp16 terms of eta in the gradient contraction
+  static constexpr int N2 = ET * KW;           // its MMA N: eta_h (and eta_l) columns
+
+  static constexpr uint32_t kABytes = 128u * KT * 2;             // theta block
+  static constexpr uint32_t kSboB = (uint32_t)KT * 16 + 16;
+  static constexpr uint32_t kBBytes = 16 * kSboB;                // 128 pixel rows
+  static constexpr uint32_t kLbo2 = 144;
+  static constexpr uint32_t kSbo2 = 16 * kLbo2;
+  static constexpr uint32_t kB2Term = (KW / 8) * kSbo2;
+  static constexpr uint32_t kB2Bytes = ET * kB2Term;           // rows: eta_h features, then eta_l
+  static constexpr uint32_t kA2Bytes = 128u * kTcPixTile * 2;    // c: 128 grains x 128 pixels, fp16
+  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + 128 * 4;
+  static constexpr size_t bytes(int nb, int na) { return kABytes + (size_t)nb * kPerB + (size_t)na * kA2Bytes; }
+};
+
+constexpr int kP2GradWarp = 11;       // pass 2: the gradient MMAs have their own issuing warp
+constexpr int kP2Threads = 12 * 32;   // three warps on every SM sub-partition
+constexpr int kP2LogitBufs = 3;       // logit tiles in flight in TMEM (3 x 128 columns)
+constexpr int kP2ChunkTiles = 32;     // tiles per gradient partial (fp32 accumulation length)
+
+// out[q] = scale * mul * (base[q] / fx + sum_c part[c][q]), fixed order;
+// base (fixed-point label moments) and mul (a device-side factor) optional
+__global__ void __launch_bounds__(32 * kRedPhases)
+k_tc_reduce_grad(const double* __restrict__ part, int nchunks, int64_t NK, const unsigned long long* __restrict__ base,
+                 double inv_fx, double scale, const double* __restrict__ mul, double* __restrict__ out) {
+  __shared__ double ssum[kRedPhases][32];
+  const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  double s = 0.0;
+  if (q < NK)
+    for (int c = threadIdx.y; c < nchunks; c += kRedPhases) s += part[(int64_t)c * NK + q];
+  ssum[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && q < NK) {
+    double t = base ? (double)(long long)base[q] * inv_fx : 0.0;
+#pragma unroll
+    for (int y = 0; y < kRedPhases; ++y) t += ssum[y][threadIdx.x];
+    out[q] = t * (mul ? scale * *mul : scale);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <int DIM>
+TileMap make_tiles(const Geom& g) {
+  TileMap tm{1, 1, 1, 0, 1, 1, 1, 1.f, 1.f, 1.f};
+  if (g.coords) {
+    tm.n_tiles = (g.P + kTcPixTile - 1) / kTcPixTile;
+    return tm;
+  }
+  using TS = TileShape<DIM>;
+  tm.ntx = (int)((g.n0 + TS::X - 1) / TS::X);
+  tm.nty = (int)((g.n1 + TS::Y - 1) / TS::Y);
+  tm.ntz = DIM == 3 ? (int)((g.n2 + TS::Z - 1) / TS::Z) : 1;
+  tm.n_tiles = (int64_t)tm.ntx * tm.nty * tm.ntz;
+  tm.n0 = (int)g.n0;
+  tm.n1 = (int)g.n1;
+  tm.n2 = (int)g.n2;
+  tm.f0 = (float)(1.0 / (double)g.n0);
+  tm.f1 = (float)(1.0 / (double)g.n1);
+  tm.f2 = (float)(1.0 / (double)g.n2);
+  return tm;
+}
+
+}  // namespace
+}  // namespace pd

@@ -85,10 +85,9 @@ def test_tc_unsupported_shapes():
     with pytest.raises(pd.PdError) as e:
         pd.pd_objective_grad(grid, lab, 3, th, 7, 0.1, prec=pd.PD_BF16X3)   # K = 36 > 32
     assert e.value.code == pd.PD_ENOTSUP
-    th = torch.zeros((3, 15), dtype=torch.float64, device="cuda")
     v = torch.zeros_like(th)
     with pytest.raises(pd.PdError) as e:
-        pd.pd_hvp(grid, lab, 3, th, v, 4, 0.1, prec=pd.PD_BF16X3)          # no tensor-core HVP
+        pd.pd_hvp(grid, lab, 3, th, v, 7, 0.1, prec=pd.PD_BF16X3)
     assert e.value.code == pd.PD_ENOTSUP
 
 
@@ -106,6 +105,32 @@ def test_tc_grain_groups(N, d):
     phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
     assert abs(phi - phi_o) <= 1e-5 * abs(phi_o), (phi, phi_o)
     assert rel(grad, grad_o) <= 1e-4, rel(grad, grad_o)
+
+
+HVP_CASES = [
+    ((64, 64), 8, 2, 1e-2, 0.02),
+    ((37, 29), 131, 3, 5e-2, 0.05),
+    ((9, 7, 5), 3, 2, 2e-2, 0.02),
+    ((13, 11, 6), 40, 3, 5e-2, 0.05),
+    ((200, 190), 300, 4, 1e-2, 0.01),
+    ((64, 48), 1793, 4, 2e-2, 0.02),     # pass 1 in three grain groups
+]
+
+
+@pytest.mark.parametrize("shape,N,d,eps,scale", HVP_CASES)
+def test_bf16x3_hvp_matches_oracle(shape, N, d, eps, scale):
+    # the Hessian-vector product on the tensor cores: float-level logits and
+    # u, c = p (u - ubar) and the features in fp16 (hi + lo for eta)
+    g = O.Grid(shape)
+    K = O.K(len(shape), d)
+    lab = synth.random_labels(41, g.P, N)
+    th = synth.random_theta(42, N, K, scale)
+    v = synth.random_theta(43, N, K, 3.0)          # magnitude above 1: exercises the scaling of v
+    hv_o = O.hvp(g, lab, N, d, eps, th, v)
+    hv = pd.pd_hvp(pd.Grid(shape), dev(lab), N, dev(th), dev(v), d, eps, prec=pd.PD_BF16X3)
+    err = rel(hv.cpu().numpy(), hv_o)
+    print("hvp bf16x3 %s N=%d d=%d: rel err %.2e" % (shape, N, d, err))
+    assert err <= 1e-3, err
 
 
 @pytest.mark.slow
