@@ -103,9 +103,8 @@ class Problem : public Evaluator {
     if (rc) return rc;
     rc = upload(v, d_v_, h_v_);
     if (rc) return rc;
-    EvalCall c{g_, grid_->dim, d_, N_, prec == PD_FP64 ? PD_FP64 : PD_FP32, eps_, labels_, d_theta_, d_v_,
-               nullptr, nullptr, d_grad_};
-    rc = eval_simt(c, st_);
+    EvalCall c{g_, grid_->dim, d_, N_, prec, eps_, labels_, d_theta_, d_v_, nullptr, nullptr, d_grad_};
+    rc = (prec == PD_BF16 || prec == PD_BF16X3) ? eval_tc(c, st_) : eval_simt(c, st_);
     if (rc) return rc;
     if (cudaMemcpyAsync(h_grad_, d_grad_, sizeof(double) * (size_t)N_ * K_, cudaMemcpyDeviceToHost, st_) !=
         cudaSuccess)

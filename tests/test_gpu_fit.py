@@ -89,6 +89,7 @@ def nonsep():
     (pd.PD_METHOD_LBFGS, pd.PD_BF16X3, 400),
     (pd.PD_METHOD_LBFGS, pd.PD_BF16, 400),
     (pd.PD_METHOD_NEWTON_CG, pd.PD_FP64, 0),
+    (pd.PD_METHOD_NEWTON_CG, pd.PD_BF16X3, 100),   # tensor-core gradients and HVPs, then FP64
 ])
 def test_reaches_unique_optimum(nonsep, method, prec, refine):
     shape, g, lab, N, d, eps, phi_star = nonsep
