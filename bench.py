@@ -563,8 +563,20 @@ def run_config3(args):
                 ev[q][1].record(stream)
             torch.cuda.synchronize()
             ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-            rows["d%d_%s" % (d, name)] = {"ms_per_eval": ms, "pixel_grain_per_s": P * N / (ms * 1e-3),
-                                          "phi_rel_vs_fp64": abs(obj.item() - phi64) / abs(phi64)}
+            row = {"ms_per_eval": ms, "pixel_grain_per_s": P * N / (ms * 1e-3),
+                   "phi_rel_vs_fp64": abs(obj.item() - phi64) / abs(phi64)}
+            if d == 2:
+                # one Hessian-vector product (the inner step of Newton-CG)
+                v = torch.from_numpy(synth.random_theta(synth.SEED_BASE + 50, N, K, 1.0)).cuda()
+                pd.pd_hvp(grid, lab, N, th, v, d, eps, prec=prec)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    pd.pd_hvp(grid, lab, N, th, v, d, eps, prec=prec)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row["hvp_ms"] = e0.elapsed_time(e1) / 3
+            rows["d%d_%s" % (d, name)] = row
     line = {"metric": "pixel*grain objective+gradient evaluations per second (3-D)", "unit": "pixel*grain/s",
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "3D 256^3 voxels, N=2000 requested (anisotropic power diagram), eps=1e-3",
