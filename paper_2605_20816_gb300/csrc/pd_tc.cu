@@ -400,7 +400,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
 }
 
 template <int DIM, int D, int KS, int NB, int NA>
-__global__ void __launch_bounds__(kP2Threads, 1)
+__global__ void __launch_bounds__(kP2ThreadsG, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
            const float* __restrict__ lse, int64_t n_chunks, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
@@ -434,7 +434,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < NB; ++s) {
-      mbar_init(&bar_b_full[s], kTcProducers);
+      mbar_init(&bar_b_full[s], kP2Producers);
       mbar_init(&bar_b_empty[s], 2);  // both MMA issuers are done with the stage
     }
     for (int b = 0; b < kP2LogitBufs; ++b) {
@@ -452,16 +452,16 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     mbar_init(&bar_drain, 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kTcMmaWarp) tmem_alloc(&tmem_slot, kTcCols);
+  if (warp == kP2MmaWarp) tmem_alloc(&tmem_slot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == kTcMmaWarp) {
+  if (warp == kP2MmaWarp) {
     // logits D1(t) = theta_block . (eta - eta(c))^T, as far ahead of the
     // consumers as the TMEM ring and the operand stages allow
-    if (tid == kTcMmaWarp * 32) {
+    if (tid == kP2MmaWarp * 32) {
       mbar_arrive_expect_tx(&bar_theta, L::kABytes);
       bulk_g2s(sA, img + (size_t)gb * L::kABytes, L::kABytes, &bar_theta);
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
@@ -481,11 +481,11 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       mbar_wait_drain(&bar_drain, 0);
     }
     __syncwarp();
-  } else if (warp == kP2GradWarp) {
+  } else if (warp == kP2GradWarpG) {
     // gradient D2 += C . [eta_h | eta_l], fp16; one D2 accumulation per
     // chunk, alternating between two TMEM buffers so that the consumers
     // read one while the next fills
-    if (tid == kP2GradWarp * 32) {
+    if (tid == kP2GradWarpG * 32) {
       bool ok = true;
       for (int t = 0; ok && t < n_pt; ++t) {
         const int s = t % NB, a = t % NA;
@@ -510,71 +510,58 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       mbar_wait_drain(&bar_drain, 0);
     }
     __syncwarp();
-  } else if (is_producer(warp)) {
-    // pixel operands of every tile: the logit operand rows, the transposed
-    // gradient operand, log2 S of the pixels and the centre features.  A
-    // thread owns two adjacent pixels; the next tile's coordinates and
-    // log2 S are fetched while the current tile is written.
-    const int q2 = 2 * (tid - kTcConsumers);
-    float xn[2][DIM], cn[DIM], lsn[2];
+  } else if (warp >= kP2ProdWarp0 && warp < kP2MmaWarp) {
+    // pixel operands of every tile: the logit operand row, the transposed
+    // gradient operand, log2 S of the pixel and (first thread) the block's
+    // centre logits.  A thread owns one pixel row; the next tile's
+    // coordinates and log2 S are fetched while the current tile is written.
+    const int p = tid - kTcConsumers;
+    float xn[DIM], cn[DIM], lsn = INFINITY;
     auto fetch = [&](int t) {
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, q2 + u, xn[u], cn);
-        lsn[u] = j >= 0 ? lse[j] : INFINITY;
-      }
+      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, p, xn, cn);
+      lsn = j >= 0 ? lse[j] : INFINITY;
     };
     if (n_pt > 0) fetch(0);
     for (int t = 0; t < n_pt; ++t) {
       const int s = t % NB;
-      float xc[2][DIM], cc[DIM];
+      float xc[DIM], cc[DIM];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        xc[0][a] = xn[0][a];
-        xc[1][a] = xn[1][a];
+        xc[a] = xn[a];
         cc[a] = cn[a];
       }
-      const float2 lsc = make_float2(lsn[0], lsn[1]);
+      const float lsc = lsn;
       if (t + 1 < n_pt) fetch(t + 1);
       if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
-      if (q2 == 0) {
+      if (p == 0) {
         // the block's centre logits for this tile, by one bulk copy that the
         // stage's barrier also waits for
         fence_proxy_async();
         mbar_expect_tx(&bar_b_full[s], 128 * 4);
         bulk_g2s(sOffP + s * 128, offg + (t_begin + t) * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
       }
-      float ec[K], e0[K], e1[K];
+      float ec[K], e0[K];
       legendre_features<DIM, D>(cc, ec);
-      legendre_features<DIM, D>(xc[0], e0);
-      legendre_features<DIM, D>(xc[1], e1);
-      uint8_t* bs = sB + s * L::kBBytes;
+      legendre_features<DIM, D>(xc, e0);
       {
         float de[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) de[k] = e0[k] - ec[k];
-        store_eta_row<K, KW, KS, L::kSboB>(bs, q2, de);
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = e1[k] - ec[k];
-        store_eta_row<K, KW, KS, L::kSboB>(bs, q2 + 1, de);
+        store_eta_row<K, KW, KS, L::kSboB>(sB + s * L::kBBytes, p, de);
       }
-      // eta^T in fp16 (hi, and lo for PD_BF16X3): one 32-bit word holds the
-      // two pixels of a feature (pixels outside the set have c = 0, so their
-      // features need no masking)
+      // eta^T in fp16 (hi, and lo for PD_BF16X3); neighbouring threads fill
+      // the two halves of one 32-bit word (pixels outside the set have
+      // c = 0, so their features need no masking)
       uint8_t* b2 = sB2 + s * L::kB2Bytes;
 #pragma unroll
       for (int k = 0; k < KW; ++k) {
-        const float a0 = k < K ? e0[k] : 0.f, a1 = k < K ? e1[k] : 0.f;
-        const __half2 h = __floats2half2_rn(a0, a1);
-        const uint32_t o = kmaj_s(k, q2, L::kLbo2, L::kSbo2);
-        *reinterpret_cast<uint32_t*>(b2 + o) = *reinterpret_cast<const uint32_t*>(&h);
-        if (ET == 2) {
-          const float2 hf = __half22float2(h);
-          const __half2 l = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
-          *reinterpret_cast<uint32_t*>(b2 + L::kB2Term + o) = *reinterpret_cast<const uint32_t*>(&l);
-        }
+        const float a0 = k < K ? e0[k] : 0.f;
+        const __half h = __float2half_rn(a0);
+        const uint32_t o = kmaj_s(k, p, L::kLbo2, L::kSbo2);
+        *reinterpret_cast<__half*>(b2 + o) = h;
+        if (ET == 2) *reinterpret_cast<__half*>(b2 + L::kB2Term + o) = __float2half_rn(a0 - __half2float(h));
       }
-      *reinterpret_cast<float2*>(sLse + s * kTcPixTile + q2) = lsc;
+      sLse[s * kTcPixTile + p] = lsc;
       fence_proxy_async();
       mbar_arrive(&bar_b_full[s]);
     }
@@ -694,7 +681,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == kTcMmaWarp) {
+  if (warp == kP2MmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTcCols);
   }
@@ -910,7 +897,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
       return PD_ECUDA;
     dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kP2Threads, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, n_chunks, part, status));
+             k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, n_chunks, part, status));
   }
   if (c.obj)
     PD_TIMED(st, "reduce_obj",

@@ -463,6 +463,14 @@ struct Pass2Layout {
 
 constexpr int kP2GradWarp = 11;       // pass 2: the gradient MMAs have their own issuing warp
 constexpr int kP2Threads = 12 * 32;   // three warps on every SM sub-partition
+// The gradient pass of pd_tc.cu: 8 epilogue warps, 4 producer warps (one
+// pixel a thread, one warp on every SM sub-partition), one warp for the
+// logit MMAs (and TMEM), one for the gradient MMAs.
+constexpr int kP2ProdWarp0 = 8;
+constexpr int kP2Producers = 128;
+constexpr int kP2MmaWarp = 12;
+constexpr int kP2GradWarpG = 13;
+constexpr int kP2ThreadsG = 14 * 32;
 constexpr int kP2LogitBufs = 3;       // logit tiles in flight in TMEM (3 x 128 columns)
 constexpr int kP2ChunkTiles = 32;     // tiles per gradient partial (fp32 accumulation length)
 
