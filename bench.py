@@ -227,6 +227,15 @@ def run_reference(args):
     return 0
 
 
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
+# capture of the current code each (profiles/ summaries); None for kernels
+# without a capture of their current version
+NCU_TRAFFIC = {
+    "tc_bf16x3_grad_pass2": (21.0752e6 + 5.12e3, "profiles/tc_bf16x3_passes_config2.md"),
+    "simt_grad_pass2": (8.44e6, "profiles/simt_grad_pass2_config2_fp32.md"),
+}
+
+
 # ---------------------------------------------------------------------------
 # replicas (one process per GPU, no data-path collective): the timing rule
 # ---------------------------------------------------------------------------
@@ -351,7 +360,8 @@ def run_ours(args):
         peak = 2 * (units["ffma_per_s"] if args.prec == "fp32" else units["dfma_per_s"]) / 1e12
         achieved = algo / avg_s / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name, (None, None))[0],
+                "traffic_source": NCU_TRAFFIC.get(name, (None, None))[1],
                 "peak_source": "measured %s FMA throughput x 2 flop (pd_microbench)" % args.prec.upper()}
     else:
         # tensor-core passes: the contractions run on tcgen05; each pass
@@ -361,7 +371,8 @@ def run_ours(args):
         peak = units["ex2_per_s"] / 1e12
         achieved = algo / avg_s / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name, (None, None))[0],
+                "traffic_source": NCU_TRAFFIC.get(name, (None, None))[1],
                 "peak_source": "measured MUFU ex2 throughput (pd_microbench)"}
     # the whole evaluation against its binding unit: one exponential per
     # pixel-grain pair is the method's algorithmic minimum (the logits and
