@@ -11,15 +11,16 @@
 // is split at the tile centre (see TileMap below).
 //
 // pass 1  (one CTA per SM, persistent over 128-pixel tiles)
-//   A = features of 128 pixels (rows) x K, written by the 128 epilogue
+//   A = features of 128 pixels (rows) x K, written by 128 producer
 //       threads from the in-register Legendre recurrence;
 //   B = all grains' scaled parameters -theta*log2(e)/eps (rows) x K, copied
 //       once per CTA from a prepared global image by a bulk (TMA) copy;
 //   D = A B^T, 128 pixels x 256 grains per MMA group, double-buffered in
 //       TMEM; the epilogue warps read their pixel row of logits and keep an
 //       online log-sum-exp; out: log2 S(x) per pixel and per-CTA objective
-//       partials.
-// pass 2  (CTA = 128 grains x a run of pixel tiles)
+//       partials, and one bit per (tile, 128-grain block): whether any
+//       probability of the block on the tile reaches 2^-26.
+// pass 2  (CTA = 128 grains x a share of the tiles whose bit is set)
 //   D1 = theta_block (128 grains x K) . eta(tile)^T (128 pixels): the
 //       logits transposed, so that a thread owns one grain's row;
 //   the thread forms c = -ex2(l - log2 S(x)) = -p_i(x) for its grain and
@@ -29,6 +30,13 @@
 //       over a chunk of tiles, then written as one double partial per
 //       grain and chunk.  The label part sum_{x in G_i} eta(x) comes from
 //       a separate pass over the pixels (k_tc_label_moments).
+//   A (tile, block) pair whose bit is clear would only add zeros: every
+//   c = -p of it is below 2^-26 and rounds to zero in the fp16 operand, so
+//   leaving it out drops only exact zeros.  To make such pairs
+//   common, the parameter image lists the grains in the Morton order of
+//   their label centroids (k_tc_grain_order), so that a block of 128
+//   grains is a compact region and most tiles lie far from most blocks;
+//   the gradient partials go back to the caller's grain order.
 //
 // PD_BF16X3 splits every operand into three bf16 terms (hi + mid + lo,
 // about 24 significant bits) and forms the six products whose size is at
@@ -52,11 +60,12 @@ namespace {
 constexpr int kP1Bufs = 2;  // logit tiles in flight in TMEM (2 x 256 columns)
 
 template <int DIM, int D, int KS>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kP1Threads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng,
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
            const float* __restrict__ offg, float* __restrict__ lse_out, double* __restrict__ obj_part,
-           float2* __restrict__ ms_out, float* __restrict__ lg_out, int* __restrict__ status) {
+           float2* __restrict__ ms_out, float* __restrict__ lg_out, const int* __restrict__ rank,
+           uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
@@ -72,12 +81,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);        // 2 stages x 128 starting max
   float* sLGv = sLG + 2 * 128;                                   // 2 stages x 128 label logits
   long long* sJ = reinterpret_cast<long long*>(sLGv + 2 * 128);  // 2 stages x 128 pixel indices
-  float* sTh = reinterpret_cast<float*>(sJ + 2 * 128);           // K x Ng scaled parameters (when resident)
+  float* sBm = reinterpret_cast<float*>(sJ + 2 * 128);           // 2 stages x Ng/128 x 128 block maxima
+  float* sTh = sBm + 2 * Ng;                                     // K x Ng scaled parameters (when resident)
   __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_off_free[2], bar_d_full[kP1Bufs],
       bar_d_empty[kP1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  __shared__ double sred[kTcThreads / 32];
+  __shared__ double sred[kP1Threads / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n_gt = Ng / kTcGrainTile;
@@ -86,7 +96,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&bar_a_full[s], kTcProducers);
+      mbar_init(&bar_a_full[s], kP1Producers);
       mbar_init(&bar_a_empty[s], 1);
       mbar_init(&bar_off_free[s], kTcConsumers);
       mbar_init(&bar_part_full[s], 128);
@@ -99,15 +109,15 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     mbar_init(&bar_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kTcMmaWarp) tmem_alloc(&tmem_slot, kTcCols);
+  if (warp == kP1MmaWarp) tmem_alloc(&tmem_slot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
   double racc = 0.0;
-  if (warp == kTcMmaWarp) {
-    if (tid == kTcMmaWarp * 32) {
+  if (warp == kP1MmaWarp) {
+    if (tid == kP1MmaWarp * 32) {
       // parameter image (and the float parameters when they fit): one bulk
       // copy per 32 KiB
       const uint32_t total = (uint32_t)Ng * kRowBytes;
@@ -152,9 +162,10 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       mbar_wait_drain(&bar_drain, 0);
     }
     __syncwarp();
-  } else if (is_producer(warp)) {
-    // pixel rows p0 and p0 + 64 of every tile; the next tile's pixel
-    // indices, coordinates and labels are fetched while this one is written
+  } else if (warp >= kTcConsumers / 32 && warp < kP1MmaWarp) {
+    // pixel row p0 of every tile (a producer warp on each SM sub-partition);
+    // the next tile's pixel index, coordinates and label are fetched while
+    // this one is written
     const int p0 = tid - kTcConsumers;
     // feature-major parameters: lanes that read consecutive grains hit
     // consecutive banks; grain i of this launch (global g0 + i)
@@ -175,25 +186,27 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       return acc;
     };
     bool ok = !th_resident || mbar_wait_warp(&bar_theta, 0, &abort_flag, status);
-    int64_t jn[2];
-    float xn[2][DIM], cn[DIM];
-    int Gn[2];
+    int64_t jn[kP1PixPerThread];
+    float xn[kP1PixPerThread][DIM], cn[DIM];
+    int Gn[kP1PixPerThread];
     auto fetch = [&](int64_t t) {
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        jn[u] = tile_pixel<DIM>(g, tm, t, p0 + 64 * u, xn[u], cn);
+      for (int u = 0; u < kP1PixPerThread; ++u) {
+        jn[u] = tile_pixel<DIM>(g, tm, t, p0 + kP1Producers * u, xn[u], cn);
         Gn[u] = jn[u] >= 0 ? labels[jn[u]] : -1;
+        // the label's row in the (reordered) parameter image
+        if (rank && (unsigned)Gn[u] < (unsigned)N) Gn[u] = rank[Gn[u]];
       }
     };
     if (ok && blockIdx.x < n_tiles) fetch(blockIdx.x);
     int it = 0;
     for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
       const int s = it & 1, use = it >> 1;
-      int64_t jc[2];
-      float xc[2][DIM], cc[DIM];
-      int Gc[2];
+      int64_t jc[kP1PixPerThread];
+      float xc[kP1PixPerThread][DIM], cc[DIM];
+      int Gc[kP1PixPerThread];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kP1PixPerThread; ++u) {
         jc[u] = jn[u];
         Gc[u] = Gn[u];
 #pragma unroll
@@ -215,8 +228,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       float ec[K];
       legendre_features<DIM, D>(cc, ec);
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int p = p0 + 64 * u;
+      for (int u = 0; u < kP1PixPerThread; ++u) {
+        const int p = p0 + kP1Producers * u;
         float eta[K];
         legendre_features<DIM, D>(xc[u], eta);
         float de[K];
@@ -251,8 +264,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     // of the max, usually the max itself), so most chunks of far-away grains
     // lie more than 127 below it: their exponentials underflow to exactly
     // zero in ex2.approx.ftz and the whole chunk is skipped
-    auto chunk = [&](const uint32_t(&r)[32], const float* off, int nv, float& m, float& ssum) {
-      if (nv <= 0) return;
+    auto chunk = [&](const uint32_t(&r)[32], const float* off, int nv, float& m, float& ssum) -> float {
+      if (nv <= 0) return -INFINITY;
       float v[32];
       const float4* off4 = reinterpret_cast<const float4*>(off);  // 16-byte aligned: cbase is a multiple of 32
       if (nv >= 32) {  // (warp-uniform) a full chunk: packed adds, no masking
@@ -278,7 +291,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         }
       }
       const float cm = tree_max32(v);
-      if (__all_sync(0xffffffffu, cm < m - 127.f)) return;
+      if (__all_sync(0xffffffffu, cm < m - 127.f)) return cm;
       const float mn = fmaxf(m, cm);
       const float2 nmn = make_float2(-mn, -mn);
 #pragma unroll
@@ -289,6 +302,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       }
       ssum = fmaf(ssum, Arith<float>::ex(m - mn), tree_sum32(v));
       m = mn;
+      return cm;
     };
     // the two 32-column halves of the thread's logits: the second is loaded
     // while the first is used, and the first half of the next grain tile
@@ -321,13 +335,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         const int nrem = N - g0 - cbase;  // valid grains from this chunk on
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 32, RB);
-        chunk(RA, off, nrem, m, ssum);
+        float bm = chunk(RA, off, nrem, m, ssum);
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 64, RA);
-        chunk(RB, off + 32, nrem - 32, m, ssum);
+        bm = fmaxf(bm, chunk(RB, off + 32, nrem - 32, m, ssum));
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 96, RB);
-        chunk(RA, off + 64, nrem - 64, m, ssum);
+        bm = fmaxf(bm, chunk(RA, off + 64, nrem - 64, m, ssum));
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
@@ -340,7 +354,9 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
             pre = true;
           }
         }
-        chunk(RB, off + 96, nrem - 96, m, ssum);
+        bm = fmaxf(bm, chunk(RB, off + 96, nrem - 96, m, ssum));
+        // the largest logit of this pixel in the thread's 128-grain block
+        sBm[(s * n_gt + gt) * 256 + half * 128 + row] = bm;
       }
       if (!ok) break;
       // combine the two column halves of each pixel (bounded mbarrier
@@ -360,15 +376,27 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         const float2 o = sPart[s * 128 + row];
         mbar_arrive(&bar_part_free[s]);
         const int64_t j = sJ[s * 128 + row];
+        float lse = NAN;
         if (j >= 0) {
           const float mm = fmaxf(m, o.x);
           const float sum = ssum * Arith<float>::ex(m - mm) + o.y * Arith<float>::ex(o.x - mm);
           if (ms_out) {
             ms_out[j] = make_float2(mm, sum);  // this launch's grains only: merged later
           } else {
-            const float lse = mm + Arith<float>::lg(sum);
+            lse = mm + Arith<float>::lg(sum);
             lse_out[j] = lse;
             racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
+          }
+        }
+        if (need_bits) {
+          // a 128-grain block is needed by the gradient pass on this tile
+          // unless every probability in it is below 2^-26: the fp16
+          // gradient operand would round all of them to zero
+          for (int q = 0; q < 2 * n_gt; ++q) {
+            const bool nd = j >= 0 && !(sBm[s * Ng + q * 128 + row] < lse - 26.f);
+            const uint32_t bal = __ballot_sync(0xffffffffu, nd);
+            if (lane == 0 && bal)
+              atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
           }
         }
       }
@@ -393,7 +421,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     if (abort_flag) sum = NAN;
     obj_part[blockIdx.x] = sum;
   }
-  if (warp == kTcMmaWarp) {
+  if (warp == kP1MmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTcCols);
   }
@@ -402,7 +430,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
 template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2ThreadsG, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
-           const float* __restrict__ lse, int64_t n_chunks, double* __restrict__ part, int* __restrict__ status) {
+           const float* __restrict__ lse, const int* __restrict__ kept, const int* __restrict__ n_kept_gb,
+           const int* __restrict__ perm, int slots, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
   constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
@@ -424,12 +453,17 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int gb = blockIdx.y;  // grain block
-  // this CTA's chunks of kP2ChunkTiles tiles, a contiguous share of the tiles
-  const int64_t c_begin = (int64_t)blockIdx.x * n_chunks / gridDim.x;
-  const int64_t c_end = (int64_t)(blockIdx.x + 1) * n_chunks / gridDim.x;
-  const int64_t t_begin = c_begin * kP2ChunkTiles;
-  const int n_pt = (int)(min(c_end * kP2ChunkTiles, tm.n_tiles) - t_begin);
-  const int n_items = (int)(c_end - c_begin);
+  // this CTA's share of the tiles on which the grain block has a
+  // non-negligible probability (all tiles without the lists), in tile
+  // order; chunks of kP2ChunkTiles of them give one gradient partial each
+  const int64_t n_list = kept ? (int64_t)n_kept_gb[gb] : tm.n_tiles;
+  const int64_t k_lo = n_list * blockIdx.x / gridDim.x;
+  const int n_kept = (int)(n_list * (blockIdx.x + 1) / gridDim.x - k_lo);
+  const int* klist = kept ? kept + (int64_t)gb * tm.n_tiles + k_lo : nullptr;
+  auto tile_of = [&](int t) -> int64_t { return klist ? (int64_t)klist[t] : k_lo + t; };
+  const int64_t c_begin = (int64_t)blockIdx.x * slots;
+  const int n_items = slots;                                          // chunk slots of this CTA
+  const int n_used = (n_kept + kP2ChunkTiles - 1) / kP2ChunkTiles;  // slots with a partial
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
@@ -465,7 +499,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       mbar_arrive_expect_tx(&bar_theta, L::kABytes);
       bulk_g2s(sA, img + (size_t)gb * L::kABytes, L::kABytes, &bar_theta);
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
-      for (int t = 0; ok && t < n_pt; ++t) {
+      for (int t = 0; ok && t < n_kept; ++t) {
         const int s = t % NB, b1 = t % kP2LogitBufs;
         ok = mbar_wait(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status);
         if (ok && t >= kP2LogitBufs)
@@ -487,10 +521,10 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     // read one while the next fills
     if (tid == kP2GradWarpG * 32) {
       bool ok = true;
-      for (int t = 0; ok && t < n_pt; ++t) {
+      for (int t = 0; ok && t < n_kept; ++t) {
         const int s = t % NB, a = t % NA;
         const int u = t / kP2ChunkTiles, db = u & 1;
-        const bool first = t % kP2ChunkTiles == 0, last = t % kP2ChunkTiles == kP2ChunkTiles - 1 || t == n_pt - 1;
+        const bool first = t % kP2ChunkTiles == 0, last = t % kP2ChunkTiles == kP2ChunkTiles - 1 || t == n_kept - 1;
         if (first && u >= 2) ok = mbar_wait(&bar_d2_free[db], (uint32_t)(((u >> 1) - 1) & 1), &abort_flag, status);
         if (ok) ok = mbar_wait(&bar_a2_full[a], (uint32_t)((t / NA) & 1), &abort_flag, status);
         if (!ok) break;
@@ -518,11 +552,11 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     const int p = tid - kTcConsumers;
     float xn[DIM], cn[DIM], lsn = INFINITY;
     auto fetch = [&](int t) {
-      const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, p, xn, cn);
+      const int64_t j = tile_pixel<DIM>(g, tm, tile_of(t), p, xn, cn);
       lsn = j >= 0 ? lse[j] : INFINITY;
     };
-    if (n_pt > 0) fetch(0);
-    for (int t = 0; t < n_pt; ++t) {
+    if (n_kept > 0) fetch(0);
+    for (int t = 0; t < n_kept; ++t) {
       const int s = t % NB;
       float xc[DIM], cc[DIM];
 #pragma unroll
@@ -531,14 +565,15 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
         cc[a] = cn[a];
       }
       const float lsc = lsn;
-      if (t + 1 < n_pt) fetch(t + 1);
+      const int64_t tc = tile_of(t);
+      if (t + 1 < n_kept) fetch(t + 1);
       if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
       if (p == 0) {
         // the block's centre logits for this tile, by one bulk copy that the
         // stage's barrier also waits for
         fence_proxy_async();
         mbar_expect_tx(&bar_b_full[s], 128 * 4);
-        bulk_g2s(sOffP + s * 128, offg + (t_begin + t) * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
+        bulk_g2s(sOffP + s * 128, offg + tc * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
       }
       float ec[K], e0[K];
       legendre_features<DIM, D>(cc, ec);
@@ -568,7 +603,8 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
   } else {
     const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
     const int gr = quad * 32 + lane;        // grain row of the block == TMEM lane
-    const int i = gb * 128 + gr;            // this thread's grain
+    const int i = gb * 128 + gr;            // this thread's row of the parameter image
+    const int gi = perm ? perm[i] : (i < N ? i : -1);  // its grain (-1: padding)
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     int n_done = 0;  // chunks whose partial this thread has written (first warpgroup)
     // the D2 row of chunk u of this CTA: one double partial per grain
@@ -587,8 +623,8 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(&bar_d2_free[db]);
-      if (i < N) {
-        double* row = part + ((c_begin + u) * N + i) * K;
+      if (gi >= 0) {
+        double* row = part + ((c_begin + u) * N + gi) * K;
 #pragma unroll
         for (int k = 0; k < K; ++k)
           row[k] = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
@@ -622,7 +658,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     uint32_t RA[32], RB[32];
     bool pre = false;
     bool ok = true;
-    for (int t = 0; t < n_pt; ++t) {
+    for (int t = 0; t < n_kept; ++t) {
       const int s = t % NB, b1 = t % kP2LogitBufs, a = t % NA;
       const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
       // sLse and sOffP of the stage were written by the producers
@@ -650,7 +686,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       tc_fence_before();
       mbar_arrive(&bar_d1_empty[b1]);  // the tile's logits are in registers: release its TMEM columns
       pre = false;
-      if (t + 1 < n_pt) {
+      if (t + 1 < n_kept) {
         const int bn = (t + 1) % kP2LogitBufs;
         if (__all_sync(0xffffffffu, mbar_peek(&bar_d1_full[bn], (uint32_t)(((t + 1) / kP2LogitBufs) & 1)))) {
           tc_fence_after();
@@ -671,11 +707,12 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     tmem_wait_ld();  // a prefetched load may be outstanding after an abort
     if (half == 0) {
       // the chunks not yet written: the last one (and, for a one-tile last
-      // chunk, the one before); after an abort the rest become NaN
-      for (int u = n_done; ok && u < n_items; ++u) ok = read_chunk(u);
-      if (!ok && i < N) {
+      // chunk, the one before); after an abort the rest become NaN.  Chunk
+      // slots beyond the kept tiles' chunks hold zero.
+      for (int u = n_done; ok && u < n_used; ++u) ok = read_chunk(u);
+      if (gi >= 0) {
         for (int u = n_done; u < n_items; ++u)
-          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + i) * K + k] = NAN;
+          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + gi) * K + k] = ok ? 0.0 : NAN;
       }
     }
   }
@@ -767,6 +804,121 @@ k_tc_label_moments(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N
 }
 
 // ---------------------------------------------------------------------------
+// Grain order of the gradient pass.  Grains sorted by the Morton code of
+// their label centroid (from the fixed-point label sums: feature 0 is 1,
+// features 1..DIM are x_1..x_DIM) make a 128-grain block of the parameter
+// image a compact region of the domain, so that most (tile, block) pairs
+// carry only negligible probabilities.  Ties, and grains without pixels
+// (last), go by index: the order is deterministic.  perm[r] is the grain
+// of image row r (-1 beyond N), rank its inverse.  One CTA, N <= kOrderMax.
+// ---------------------------------------------------------------------------
+constexpr int kOrderMax = 2048;
+
+__device__ __forceinline__ uint32_t spread_bits(uint32_t v, int dim) {
+  // bit b of v moves to bit dim * b
+  uint32_t r = 0;
+  for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (dim * b);
+  return r;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(1024)
+k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int Npad, int* __restrict__ perm,
+                 int* __restrict__ rank) {
+  __shared__ unsigned long long key[kOrderMax];
+  int M = 1;
+  while (M < N) M <<= 1;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    unsigned long long kv = ~0ull;
+    if (i < N) {
+      const long long cnt = (long long)lmom[(int64_t)i * K];
+      uint32_t code = 0xffffffffu;
+      if (cnt > 0) {
+        code = 0;
+        for (int a = 0; a < DIM; ++a) {
+          const double c = (double)(long long)lmom[(int64_t)i * K + 1 + a] / (double)cnt;  // in [-1, 1]
+          int v = (int)((c + 1.0) * 512.0);
+          v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
+          code |= spread_bits((uint32_t)v, DIM) << a;
+        }
+      }
+      kv = ((unsigned long long)code << 32) | (uint32_t)i;
+    }
+    key[i] = kv;
+  }
+  __syncthreads();
+  // bitonic sort, ascending
+  for (int size = 2; size <= M; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const unsigned long long a = key[i], b = key[j];
+          if ((a > b) == ((i & size) == 0)) {
+            key[i] = b;
+            key[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int r = threadIdx.x; r < Npad; r += blockDim.x) {
+    const int gi = r < N ? (int)(uint32_t)key[r] : -1;
+    perm[r] = gi;
+    if (gi >= 0) rank[gi] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per 128-grain block, the tiles whose need bit pass 1 set, in increasing
+// order (an ordered compaction, one CTA per block).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_tc_kept_lists(const uint32_t* __restrict__ need, int64_t n_words, int64_t n_tiles, int* __restrict__ lists,
+                int* __restrict__ counts) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  const int gb = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t* row = need + (int64_t)gb * n_words;
+  int* out = lists + (int64_t)gb * n_tiles;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int64_t w0 = 0; w0 < n_words; w0 += 1024) {
+    const int64_t w = w0 + threadIdx.x;
+    uint32_t bits = w < n_words ? row[w] : 0u;
+    const int c = __popc(bits);
+    int x = c;  // inclusive scan in the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int v = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      wsum[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    int pos = base + (wid > 0 ? wsum[wid - 1] : 0) + x - c;
+    while (bits) {
+      const int b = __ffs((int)bits) - 1;
+      out[pos++] = (int)(w * 32 + b);
+      bits &= bits - 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) counts[gb] = base;
+}
+
+// ---------------------------------------------------------------------------
 // Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
 // arrives at; the wait gives up after limit_ns and records PD_ETIMEOUT.
 // ---------------------------------------------------------------------------
@@ -804,12 +956,12 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   constexpr size_t kCap = 220 * 1024;
   // pass 1 keeps the image of ng grains resident: image, 2 operand stages,
   // 2 x centre logits, 2 x (max, sum), 2 x start, 2 x label logit, 2 x pixel
-  // index, and the float parameters when they fit too.  More grains than
+  // index, 2 x block maxima, and the float parameters when they fit too.  More grains than
   // one SM holds are split into groups of ng, one launch each, whose
   // (max, sum) per pixel are merged afterwards.
   auto p1_bytes = [&](size_t ng, bool th_res) {
     return ng * row_bytes + 2 * kTcPixTile * row_bytes + 2 * ng * 4 + 2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 +
-           2 * kTcPixTile * 8 + (th_res ? (size_t)K * ng * 4 : 0);
+           2 * kTcPixTile * 8 + 2 * ng * 4 + (th_res ? (size_t)K * ng * 4 : 0);
   };
   int n_grp = 1, Ng = Npad;
   while (p1_bytes((size_t)Ng, false) > kCap && Ng > kTcGrainTile) {
@@ -839,10 +991,20 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
   const int gridm = (int)((P + 255) / 256);  // merge blocks of a grain-split pass 1
   const int gblocks = (N + 127) / 128;  // pass-2 grain blocks
-  // pass 2: chunks of kP2ChunkTiles tiles (one gradient partial each),
-  // shared out in contiguous runs over one wave of CTAs per grain block
-  const int64_t n_chunks = (n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles;
-  const int cpg = (int)std::min<int64_t>(n_chunks, std::max(1, sms / gblocks));
+  // pass 2: one wave of CTAs per grain block, each with a contiguous share
+  // of the block's tiles and one gradient partial per kP2ChunkTiles of them
+  const int cpg = (int)std::min<int64_t>((n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles, std::max(1, sms / gblocks));
+  const int slots = (int)(((n_tiles + cpg - 1) / cpg + kP2ChunkTiles - 1) / kP2ChunkTiles);
+  const int64_t n_slots = (int64_t)cpg * slots;
+  // With a single pass 1 (which sees all grains of a pixel) the gradient
+  // pass visits only the (tile, block) pairs with a probability that
+  // survives in its fp16 operand, and the grains are reordered so that
+  // blocks are compact regions.
+  // (PD_TC_NO_SKIP=1 in the environment visits every pair in index order,
+  // for tests that compare the two)
+  const char* no_skip = getenv("PD_TC_NO_SKIP");
+  const bool skip = c.grad && n_grp == 1 && !(no_skip && no_skip[0] && no_skip[0] != '0');
+  const bool order = skip && Npad <= kOrderMax;
 
   Scratch sc(st);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
@@ -852,18 +1014,42 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
-  double* part = c.grad ? sc.get<double>((size_t)n_chunks * N * K) : nullptr;
+  double* part = c.grad ? sc.get<double>((size_t)n_slots * N * K) : nullptr;
   unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
+  // one bit per (128-grain block, tile): the block has a probability that
+  // the gradient pass cannot neglect on the tile; then the tiles per block
+  const int64_t n_words = (n_tiles + 31) / 32;
+  uint32_t* need = skip ? sc.get<uint32_t>((size_t)(Npad / 128) * n_words) : nullptr;
+  int* kept = skip ? sc.get<int>((size_t)(Npad / 128) * n_tiles) : nullptr;
+  int* nkept = skip ? sc.get<int>((size_t)(Npad / 128)) : nullptr;
+  int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
+  int* rank = order ? sc.get<int>((size_t)N) : nullptr;
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
+  if (need && cudaMemsetAsync(need, 0, sizeof(uint32_t) * (size_t)(Npad / 128) * n_words, st) != cudaSuccess)
+    return PD_ECUDA;
 
+  // |eta| <= 1, so a grain's label sum is bounded by P: the largest
+  // power-of-two scale that keeps P * scale below 2^62
+  int bits = 0;
+  while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
+  const float fx = ldexpf(1.f, 62 - bits);
+  if (c.grad) {
+    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+    const int64_t nthr = n_tiles * kTcPixTile;
+    PD_TIMED(st, "tc_label_moments",
+             (k_tc_label_moments<DIM, D><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
+                                                                                       lmom)));
+  }
+  if (order)
+    PD_TIMED(st, "tc_grain_order", k_tc_grain_order<DIM><<<1, 1024, 0, st>>>(lmom, N, K, Npad, perm, rank));
   const double scale = Arith<float>::theta_scale(c.eps);
   {
     const int64_t n = (int64_t)Npad * KW;
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, Npad, K, KW, scale,
-                                                                                nullptr, img, th32t));
+                                                                                nullptr, perm, img, th32t));
   }
   PD_TIMED(st, "tc_centre_logits",
            (k_tc_centre_logits<DIM, D><<<dim3((unsigned)(Npad / 256),
@@ -876,28 +1062,26 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   for (int q = 0; q < n_grp; ++q) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
-             k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, offg,
-                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, status));
+             k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, offg,
+                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, rank, need,
+                                                      n_words, status));
   }
+  // a launch that fails (resources, configuration) is an error of this call
+  if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   if (n_grp > 1)
     PD_TIMED(st, "tc_merge_lse", k_tc_merge_lse<<<gridm, 256, 0, st>>>(ms, n_grp, P, lgb, lse, objp, status));
-  // |eta| <= 1, so a grain's label sum is bounded by P: the largest
-  // power-of-two scale that keeps P * scale below 2^62
-  int bits = 0;
-  while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
-  const float fx = ldexpf(1.f, 62 - bits);
   if (c.grad) {
-    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
-    const int64_t nthr = n_tiles * kTcPixTile;
-    PD_TIMED(st, "tc_label_moments",
-             (k_tc_label_moments<DIM, D><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
-                                                                                       lmom)));
+    if (skip)
+      PD_TIMED(st, "tc_kept_lists",
+               k_tc_kept_lists<<<(unsigned)(Npad / 128), 1024, 0, st>>>(need, n_words, n_tiles, kept, nkept));
     auto k2 = k_tc_pass2<DIM, D, KS, NB, NA>;
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
     dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, n_chunks, part, status));
+             k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, perm, slots,
+                                                       part, status));
+    if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   }
   if (c.obj)
     PD_TIMED(st, "reduce_obj",
@@ -906,7 +1090,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const int64_t NK = (int64_t)N * K;
     PD_TIMED(st, "reduce_parts",
              k_tc_reduce_grad<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
-                 part, (int)n_chunks, NK, lmom, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), nullptr, c.grad));
+                 part, (int)n_slots, NK, lmom, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), nullptr, c.grad));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }

@@ -30,6 +30,12 @@ constexpr int kTcThreads = 11 * 32;               // at most 3 warps per SM sub-
 constexpr int kTcCols = 512;                      // TMEM columns per CTA (one CTA per SM)
 constexpr int kTcGrainTile = 256;                 // pass-1 grains per MMA group (N of the MMA)
 constexpr int kTcPixTile = 128;                   // pixels per tile (both passes)
+// objective pass 1: 8 epilogue warps, 4 producer warps (one pixel per
+// thread, one producer on each SM sub-partition), one MMA warp
+constexpr int kP1Producers = 128;
+constexpr int kP1PixPerThread = kTcPixTile / kP1Producers;
+constexpr int kP1MmaWarp = (kTcConsumers + kP1Producers) / 32;
+constexpr int kP1Threads = (kP1MmaWarp + 1) * 32;
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -245,19 +251,21 @@ __device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float*
 }
 
 // ---------------------------------------------------------------------------
-// Parameter images: rows = grains (padded to Npad with zero rows), K-major
-// no-swizzle, one slice of KW columns per term; plus float copies (grain
-// rows, and transposed K x Npad) used for the centre logits and the
-// label logit of the objective.
+// Parameter images: rows = grains (in the order perm gives, when given;
+// padded to Npad with zero rows), K-major no-swizzle, one slice of KW
+// columns per term; plus float copies (grain rows, and transposed
+// K x Npad) used for the centre logits and the label logit of the
+// objective.
 // ---------------------------------------------------------------------------
 template <int KS>
 __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Npad, int K, int KW, double scale,
-                                 const double* __restrict__ dscale, uint8_t* __restrict__ img,
-                                 float* __restrict__ th32t) {
+                                 const double* __restrict__ dscale, const int* __restrict__ perm,
+                                 uint8_t* __restrict__ img, float* __restrict__ th32t) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (row, k) pairs
   if (q >= (int64_t)Npad * KW) return;
   const int r = (int)(q / KW), k = (int)(q % KW);
-  const double t = (r < N && k < K) ? theta[(int64_t)r * K + k] * (dscale ? scale * *dscale : scale) : 0.0;
+  const int src = perm ? perm[r] : (r < N ? r : -1);  // row r holds grain src (-1: zero padding)
+  const double t = (src >= 0 && k < K) ? theta[(int64_t)src * K + k] * (dscale ? scale * *dscale : scale) : 0.0;
   const uint16_t h = __bfloat16_as_ushort(__double2bfloat16(t));
   const double r1 = t - (double)__bfloat162float(__ushort_as_bfloat16(h));
   const uint16_t m = __bfloat16_as_ushort(__double2bfloat16(r1));

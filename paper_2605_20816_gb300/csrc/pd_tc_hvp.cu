@@ -641,9 +641,9 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.theta, N, Npad, K, KW, Arith<float>::theta_scale(c.eps),
-                                                          nullptr, img, th32t));
+                                                          nullptr, nullptr, img, th32t));
     PD_TIMED(st, "tc_v_image",
-             k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.v, N, Npad, K, KW, 1.0, vsc + 1, vimg, v32t));
+             k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.v, N, Npad, K, KW, 1.0, vsc + 1, nullptr, vimg, v32t));
   }
   const dim3 gridc((unsigned)((Npad + 255) / 256),
                    (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles, 4096));

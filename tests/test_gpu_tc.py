@@ -78,6 +78,47 @@ def test_tc_bitwise_reproducible():
         np.testing.assert_array_equal(a[1], b[1])
 
 
+STRUCTURED = [
+    ((256, 192), 300, 4, 1e-3),
+    ((250, 130), 700, 3, 2e-3),       # ragged tiles on both axes, 6 blocks
+    ((40, 36, 30), 200, 2, 2e-3),
+]
+
+
+@pytest.mark.parametrize("shape,N,d,eps", STRUCTURED)
+def test_tc_skip_structured(shape, N, d, eps, monkeypatch):
+    # a sharp diagram: most (tile, 128-grain block) pairs of the gradient
+    # pass carry only probabilities below 2^-26 and are left out after the
+    # grains are reordered by label centroid.  Against the oracle, and
+    # against the same evaluation visiting every pair in index order (the
+    # two differ only by the fp32 accumulation order of the partials).
+    g, lab, N, th = poly_problem(shape, N, d, seed=synth.SEED_BASE + 5, noise=0.02)
+    phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
+    phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    monkeypatch.setenv("PD_TC_NO_SKIP", "1")
+    phi_a, grad_a = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    monkeypatch.delenv("PD_TC_NO_SKIP")
+    # the label part (1/(eps P)) sum_{x in G_i} eta(x), which the probability
+    # part cancels down to the gradient: the scale of its rounding
+    E = O.features(g, d)
+    L = np.zeros((N, E.shape[1]))
+    np.add.at(L, lab, E)
+    L /= eps * g.P
+    dgrad = np.linalg.norm(grad - grad_a) / np.linalg.norm(L)
+    print("skip %s N=%d: phi %.2e grad %.2e vs oracle; vs all pairs: phi %.2e grad %.2e of the label part"
+          % (shape, N, abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o), abs(phi - phi_a) / abs(phi_a), dgrad))
+    # Phi of a sharp fit is near zero: its error is measured on the scale of
+    # the log-sum-exp, O(1)
+    assert abs(phi - phi_o) <= 1e-5 * max(1.0, abs(phi_o)), (phi, phi_o)
+    assert rel(grad, grad_o) <= 2e-3, rel(grad, grad_o)
+    assert abs(phi - phi_a) <= 1e-6 * max(1.0, abs(phi_a))
+    assert dgrad <= 2e-5, dgrad
+    # deterministic
+    phi_b, grad_b = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    assert phi_b == phi
+    np.testing.assert_array_equal(grad_b, grad)
+
+
 def test_tc_unsupported_shapes():
     grid = pd.Grid((16, 16))
     lab = torch.zeros(256, dtype=torch.int32, device="cuda")
