@@ -57,7 +57,15 @@ namespace {
 // ---------------------------------------------------------------------------
 // Pass 1: log2 S(x) per pixel and objective partials.
 // ---------------------------------------------------------------------------
-constexpr int kP1Bufs = 2;  // logit tiles in flight in TMEM (2 x 256 columns)
+// Pass 1 takes the grains of a tile in blocks of 128 (one MMA of N = 128
+// per block and product) through a ring of four 128-column TMEM buffers;
+// the two epilogue warpgroups take alternate blocks.  A block whose logits
+// are all more than 130 below the logit of the label grain of the tile's
+// centre pixel, everywhere in the tile (a bound from the centre logits,
+// see k_tc_centre_logits), would only add exponentials that underflow to
+// zero: it is not visited.
+constexpr int kP1Bufs = 4;
+constexpr float kP1Far = 130.f;
 
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kP1Threads, 1)
@@ -65,13 +73,16 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
            const float* __restrict__ offg, float* __restrict__ lse_out, double* __restrict__ obj_part,
            float2* __restrict__ ms_out, float* __restrict__ lg_out, const int* __restrict__ rank,
+           const float* __restrict__ mb, const float* __restrict__ amax, int nblk,
            uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
   constexpr uint32_t kRowBytes = KT * 2;
   constexpr uint32_t kTileBytes = kTcPixTile * kRowBytes;
-  constexpr uint32_t IDESC = idesc_bf16(128, kTcGrainTile);
+  constexpr uint32_t IDESC = idesc_bf16(128, 128);
+  using TS = TileShape<DIM>;
+  constexpr int kRef = TS::X / 2 + TS::X * (TS::Y / 2) + TS::X * TS::Y * (TS::Z / 2);  // the centre pixel
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;                                            // Ng x KT (this launch's grains)
@@ -88,10 +99,25 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ double sred[kP1Threads / 32];
+  __shared__ int sRef[2];  // image row of the centre pixel's label grain (-1: none)
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int n_gt = Ng / kTcGrainTile;
+  const int nq = Ng / 128;  // grain blocks of this launch
   const int64_t n_tiles = tm.n_tiles;
+  // the blocks visited on tile t (stage s holds its producer data): all,
+  // less those whose largest bound off_i + A_i lies kP1Far below the
+  // reference logit's lower bound off_r - A_r
+  auto tile_mask = [&](int64_t t, int s) -> uint64_t {
+    uint64_t msk = nq >= 64 ? ~0ull : ((1ull << nq) - 1ull);
+    const int r = mb ? sRef[s] : -1;
+    if (r >= 0) {
+      const float lim = offg[t * Npad + r] - amax[r] - kP1Far;
+      const float* mt = mb + t * nblk + g0 / 128;
+      for (int q = 0; q < nq; ++q)
+        if (mt[q] < lim) msk &= ~(1ull << q);
+    }
+    return msk;
+  };
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
@@ -104,7 +130,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     }
     for (int b = 0; b < kP1Bufs; ++b) {
       mbar_init(&bar_d_full[b], 1);
-      mbar_init(&bar_d_empty[b], kTcConsumers);
+      mbar_init(&bar_d_empty[b], 128);  // one warpgroup reads a buffer
     }
     mbar_init(&bar_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -135,14 +161,15 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           bulk_g2s(rdst + off, rsrc + off, row_t - off < 32768u ? row_t - off : 32768u, &bar_theta);
       }
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
-      int64_t c = 0;  // grain-tile counter over the whole loop
+      int64_t c = 0;  // block counter over the whole loop
       int it = 0;
       for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
         const int s = it & 1;
         ok = mbar_wait(&bar_a_full[s], (it >> 1) & 1, &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
-        for (int gt = 0; gt < n_gt; ++gt, ++c) {
+        for (uint64_t msk = tile_mask(t, s); msk; msk &= msk - 1, ++c) {
+          const int q = __ffsll((long long)msk) - 1;
           const int b = (int)(c % kP1Bufs);
           if (c >= kP1Bufs) {
             ok = mbar_wait(&bar_d_empty[b], (uint32_t)(((c / kP1Bufs) - 1) & 1), &abort_flag, status);
@@ -150,8 +177,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
             tc_fence_after();
           }
           const uint32_t aaddr = smem_addr(sA + s * kTileBytes);
-          const uint32_t baddr = smem_addr(sB + (size_t)gt * kTcGrainTile * kRowBytes);
-          mma_terms<KS, KW>(tmem + b * kTcGrainTile, aaddr, KT * 16, false, baddr, KT * 16, IDESC);
+          const uint32_t baddr = smem_addr(sB + (size_t)q * 128 * kRowBytes);
+          mma_terms<KS, KW>(tmem + b * 128, aaddr, KT * 16, false, baddr, KT * 16, IDESC);
           mma_commit(&bar_d_full[b]);
         }
         if (!ok) break;
@@ -251,6 +278,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         sLG[s * 128 + p] = start;
         sLGv[s * 128 + p] = lg;
         sJ[s * 128 + p] = (long long)jc[u];
+        if (p == kRef) sRef[s] = jc[u] >= 0 && (unsigned)Gc[u] < (unsigned)N ? Gc[u] : -1;
       }
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
@@ -304,33 +332,32 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       m = mn;
       return cm;
     };
-    // the two 32-column halves of the thread's logits: the second is loaded
-    // while the first is used, and the first half of the next grain tile
-    // (when the tensor cores have it ready) while the second is used
+    // a block's 128 columns in four 32-column chunks, each loaded while the
+    // one before is used; warpgroup `half` takes the visited blocks of odd
+    // or even position
     uint32_t RA[32], RB[32];
-    bool pre = false;
     int it = 0;
     int64_t c = 0;
     bool ok = true;
+    uint64_t msk0 = 0;
     for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
       const int s = it & 1;
       // the stage's operands and per-row values come from the producers
       ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
       if (!ok) break;
       float m = sLG[s * 128 + row], ssum = 0.f;
-      const bool more_tiles = t + gridDim.x < n_tiles;
-      for (int gt = 0; gt < n_gt; ++gt, ++c) {
+      msk0 = tile_mask(t, s);
+      int kb = 0;
+      for (uint64_t msk = msk0; msk; msk &= msk - 1, ++c, ++kb) {
+        if ((kb & 1) != half) continue;
+        const int q = __ffsll((long long)msk) - 1;
         const int b = (int)(c % kP1Bufs);
-        const uint32_t col = (uint32_t)(b * kTcGrainTile + half * 128);
-        if (!pre) {
-          ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
-          if (!ok) break;
-          tc_fence_after();
-          tmem_ld32(tmem + lane_base + col, RA);
-        }
-        // the thread's 128 columns in four 32-column chunks, each loaded
-        // while the one before is used
-        const int cbase = gt * kTcGrainTile + half * 128;
+        const uint32_t col = (uint32_t)(b * 128);
+        ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
+        if (!ok) break;
+        tc_fence_after();
+        tmem_ld32(tmem + lane_base + col, RA);
+        const int cbase = q * 128;
         const float* off = sOff + s * Ng + cbase;
         const int nrem = N - g0 - cbase;  // valid grains from this chunk on
         tmem_wait_ld();
@@ -344,23 +371,14 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         bm = fmaxf(bm, chunk(RA, off + 64, nrem - 64, m, ssum));
         tmem_wait_ld();
         tc_fence_before();
-        mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM tile
-        pre = false;
-        if (gt + 1 < n_gt || more_tiles) {
-          const int bn = (int)((c + 1) % kP1Bufs);
-          if (__all_sync(0xffffffffu, mbar_peek(&bar_d_full[bn], (uint32_t)(((c + 1) / kP1Bufs) & 1)))) {
-            tc_fence_after();
-            tmem_ld32(tmem + lane_base + (uint32_t)(bn * kTcGrainTile + half * 128), RA);
-            pre = true;
-          }
-        }
+        mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM buffer
         bm = fmaxf(bm, chunk(RB, off + 96, nrem - 96, m, ssum));
-        // the largest logit of this pixel in the thread's 128-grain block
-        sBm[(s * n_gt + gt) * 256 + half * 128 + row] = bm;
+        // the largest logit of this pixel in the block
+        sBm[s * Ng + q * 128 + row] = bm;
       }
       if (!ok) break;
-      // combine the two column halves of each pixel (bounded mbarrier
-      // hand-off between the warpgroups; slot s is reused every 2 tiles)
+      // combine the two warpgroups' parts of each pixel (bounded mbarrier
+      // hand-off; slot s is reused every 2 tiles)
       if (half == 1) {
         if (it >= 2 && !mbar_wait_warp(&bar_part_free[s], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, status)) {
           ok = false;
@@ -392,8 +410,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           // a 128-grain block is needed by the gradient pass on this tile
           // unless every probability in it is below 2^-26: the fp16
           // gradient operand would round all of them to zero
-          for (int q = 0; q < 2 * n_gt; ++q) {
-            const bool nd = j >= 0 && !(sBm[s * Ng + q * 128 + row] < lse - 26.f);
+          for (int q = 0; q < nq; ++q) {
+            const bool nd = ((msk0 >> q) & 1) && j >= 0 && !(sBm[s * Ng + q * 128 + row] < lse - 26.f);
             const uint32_t bal = __ballot_sync(0xffffffffu, nd);
             if (lane == 0 && bal)
               atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
@@ -1003,7 +1021,11 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   // (PD_TC_NO_SKIP=1 in the environment visits every pair in index order,
   // for tests that compare the two)
   const char* no_skip = getenv("PD_TC_NO_SKIP");
-  const bool skip = c.grad && n_grp == 1 && !(no_skip && no_skip[0] && no_skip[0] != '0');
+  const bool skip_on = !(no_skip && no_skip[0] && no_skip[0] != '0');
+  const bool skip = c.grad && n_grp == 1 && skip_on;
+  // pass 1 leaves out the blocks that the centre-logit bounds show to be
+  // far below the tile's reference logit (structured grids)
+  const bool bounds = skip_on && !c.g.coords;
   const bool order = skip && Npad <= kOrderMax;
 
   Scratch sc(st);
@@ -1024,6 +1046,22 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   int* nkept = skip ? sc.get<int>((size_t)(Npad / 128)) : nullptr;
   int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
   int* rank = order ? sc.get<int>((size_t)N) : nullptr;
+  float* amax = bounds ? sc.get<float>((size_t)Npad) : nullptr;
+  float* mbb = bounds ? sc.get<float>((size_t)n_tiles * (Npad / 128)) : nullptr;
+  TileBound tb{};
+  if (bounds) {
+    using TS = TileShape<DIM>;
+    const double h[3] = {(double)TS::X / (double)c.g.n0, (double)TS::Y / (double)c.g.n1,
+                         DIM == 3 ? (double)TS::Z / (double)c.g.n2 : 0.0};
+    for (int k = 0; k < K; ++k) {
+      double dk = 0.0;
+      for (int a = 0; a < DIM; ++a) {
+        const int e = basis_exp(DIM, D, k, a);
+        dk += 0.5 * e * (e + 1) * h[a];
+      }
+      tb.d[k] = (float)(dk * (1.0 + 1e-6));  // rounded up
+    }
+  }
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
@@ -1055,7 +1093,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
            (k_tc_centre_logits<DIM, D><<<dim3((unsigned)(Npad / 256),
                                               (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles,
                                                                           4096)),
-                                         256, 0, st>>>(c.g, tm, th32t, N, Npad, offg)));
+                                         256, 0, st>>>(c.g, tm, th32t, N, Npad, offg, tb, amax, mbb)));
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
@@ -1063,8 +1101,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
              k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, offg,
-                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, rank, need,
-                                                      n_words, status));
+                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, rank, mbb,
+                                                      amax, Npad / 128, need, n_words, status));
   }
   // a launch that fails (resources, configuration) is an error of this call
   if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;

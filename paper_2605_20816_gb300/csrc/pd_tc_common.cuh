@@ -396,35 +396,75 @@ __device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp
 // block takes 256 grains (parameters in registers) and kCentreTiles tiles
 // (centre features in shared memory); the same fma order as a per-grain
 // fp32 dot product.
+//
+// With bounds (structured grids): the features of a tile's pixels differ
+// from those at its centre pixel by |eta_k(x) - eta_k(c)| <= D_k, where
+// D_k = sum_a alpha_a (alpha_a + 1) / 2 * h_a, since |P_m| <= 1 and
+// |P_m'| <= m (m + 1) / 2 on [-1, 1] and |x_a - c_a| <= h_a in the tile.
+// So every logit of grain i in tile t lies within A_i = sum_k |theta'_ik| D_k
+// of the centre logit, and the kernel writes A_i and, per tile and
+// 128-grain block, the largest off_i + A_i (+inf for a tile that crosses
+// the grid edge, whose centre may lie outside [-1, 1]).
 // ---------------------------------------------------------------------------
 constexpr int kCentreTiles = 32;
 
+struct TileBound {
+  float d[32];  // D_k
+};
+
 template <int DIM, int D>
 __global__ void __launch_bounds__(256)
-k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, int Npad, float* __restrict__ off) {
+k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, int Npad, float* __restrict__ off,
+                   TileBound tb, float* __restrict__ amax, float* __restrict__ mb) {
   constexpr int K = basis_K(DIM, D);
   __shared__ float sec[kCentreTiles][K];
+  __shared__ float smx[kCentreTiles][8];
+  __shared__ int srag[kCentreTiles];
   const int i = blockIdx.x * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nblk = Npad / 128;
   const bool live = i < Npad;  // (every thread takes part in the barriers)
   float th[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) th[k] = i < N ? th32t[(int64_t)k * Npad + i] : 0.f;
+  float A = 0.f;
+  if (mb) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) A = fmaf(fabsf(th[k]), tb.d[k], A);
+    if (blockIdx.y == 0 && live) amax[i] = A;
+  }
   for (int64_t t0 = (int64_t)blockIdx.y * kCentreTiles; t0 < tm.n_tiles; t0 += (int64_t)gridDim.y * kCentreTiles) {
     const int nt = (int)min((int64_t)kCentreTiles, tm.n_tiles - t0);
-    __syncthreads();  // the previous group's features are used up
+    __syncthreads();  // the previous group's features and maxima are used up
     if (threadIdx.x < nt) {
       float x[DIM], c[DIM], ec[K];
       tile_pixel<DIM>(g, tm, t0 + threadIdx.x, 0, x, c);
       legendre_features<DIM, D>(c, ec);
 #pragma unroll
       for (int k = 0; k < K; ++k) sec[threadIdx.x][k] = ec[k];
+      // the tile's last pixel lies outside the grid: a ragged tile
+      srag[threadIdx.x] = tile_pixel<DIM>(g, tm, t0 + threadIdx.x, kTcPixTile - 1, x, c) < 0;
     }
     __syncthreads();
-    for (int q = 0; live && q < nt; ++q) {
+    for (int q = 0; q < nt; ++q) {
       float acc = th[0] * sec[q][0];
 #pragma unroll
       for (int k = 1; k < K; ++k) acc = fmaf(th[k], sec[q][k], acc);
-      off[(t0 + q) * Npad + i] = acc;
+      if (live) off[(t0 + q) * Npad + i] = acc;
+      if (mb) {
+        float v = live && i < N ? acc + A : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) smx[q][wid] = v;
+      }
+    }
+    if (mb) {
+      __syncthreads();
+      if (threadIdx.x < 2 * nt) {
+        const int q = threadIdx.x >> 1, h = threadIdx.x & 1, blk = blockIdx.x * 2 + h;
+        const float v = fmaxf(fmaxf(smx[q][4 * h], smx[q][4 * h + 1]), fmaxf(smx[q][4 * h + 2], smx[q][4 * h + 3]));
+        if (blk < nblk) mb[(t0 + q) * nblk + blk] = srag[q] ? INFINITY : v;
+      }
     }
   }
 }
