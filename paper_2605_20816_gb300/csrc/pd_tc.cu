@@ -72,8 +72,7 @@ __global__ void __launch_bounds__(kP1Threads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng,
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
            const float* __restrict__ offg, float* __restrict__ lse_out, double* __restrict__ obj_part,
-           float2* __restrict__ ms_out, float* __restrict__ lg_out, const int* __restrict__ rank,
-           const float* __restrict__ mb, const float* __restrict__ amax, int nblk,
+           float2* __restrict__ ms_out, float* __restrict__ lg_out, const unsigned long long* __restrict__ masks,
            uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
@@ -81,8 +80,6 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   constexpr uint32_t kRowBytes = KT * 2;
   constexpr uint32_t kTileBytes = kTcPixTile * kRowBytes;
   constexpr uint32_t IDESC = idesc_bf16(128, 128);
-  using TS = TileShape<DIM>;
-  constexpr int kRef = TS::X / 2 + TS::X * (TS::Y / 2) + TS::X * TS::Y * (TS::Z / 2);  // the centre pixel
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;                                            // Ng x KT (this launch's grains)
@@ -99,25 +96,14 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ double sred[kP1Threads / 32];
-  __shared__ int sRef[2];  // image row of the centre pixel's label grain (-1: none)
+  __shared__ unsigned long long sMask[2];  // blocks visited on the stage's tile (bit q: image block q)
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nq = Ng / 128;  // grain blocks of this launch
   const int64_t n_tiles = tm.n_tiles;
-  // the blocks visited on tile t (stage s holds its producer data): all,
-  // less those whose largest bound off_i + A_i lies kP1Far below the
-  // reference logit's lower bound off_r - A_r
-  auto tile_mask = [&](int64_t t, int s) -> uint64_t {
-    uint64_t msk = nq >= 64 ? ~0ull : ((1ull << nq) - 1ull);
-    const int r = mb ? sRef[s] : -1;
-    if (r >= 0) {
-      const float lim = offg[t * Npad + r] - amax[r] - kP1Far;
-      const float* mt = mb + t * nblk + g0 / 128;
-      for (int q = 0; q < nq; ++q)
-        if (mt[q] < lim) msk &= ~(1ull << q);
-    }
-    return msk;
-  };
+  // the blocks of this launch visited on the tile of stage s
+  const uint64_t all_q = nq >= 64 ? ~0ull : ((1ull << nq) - 1ull);
+  auto tile_mask = [&](int s) -> uint64_t { return masks ? (sMask[s] >> (g0 / 128)) & all_q : all_q; };
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
@@ -168,7 +154,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         ok = mbar_wait(&bar_a_full[s], (it >> 1) & 1, &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
-        for (uint64_t msk = tile_mask(t, s); msk; msk &= msk - 1, ++c) {
+        for (uint64_t msk = tile_mask(s); msk; msk &= msk - 1, ++c) {
           const int q = __ffsll((long long)msk) - 1;
           const int b = (int)(c % kP1Bufs);
           if (c >= kP1Bufs) {
@@ -216,14 +202,14 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     int64_t jn[kP1PixPerThread];
     float xn[kP1PixPerThread][DIM], cn[DIM];
     int Gn[kP1PixPerThread];
+    unsigned long long maskn = 0;
     auto fetch = [&](int64_t t) {
 #pragma unroll
       for (int u = 0; u < kP1PixPerThread; ++u) {
         jn[u] = tile_pixel<DIM>(g, tm, t, p0 + kP1Producers * u, xn[u], cn);
         Gn[u] = jn[u] >= 0 ? labels[jn[u]] : -1;
-        // the label's row in the (reordered) parameter image
-        if (rank && (unsigned)Gn[u] < (unsigned)N) Gn[u] = rank[Gn[u]];
       }
+      if (masks && p0 == 0) maskn = masks[t];
     };
     if (ok && blockIdx.x < n_tiles) fetch(blockIdx.x);
     int it = 0;
@@ -241,13 +227,15 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) cc[a] = cn[a];
+      const unsigned long long maskc = maskn;
       if (t + gridDim.x < n_tiles) fetch(t + gridDim.x);
       if (use >= 1 && (!mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status) ||
                        !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)))
         break;
       if (p0 == 0) {
         // the tile's centre logits of this launch's grains, by one bulk copy
-        // that the stage's barrier also waits for
+        // that the stage's barrier also waits for, and the blocks to visit
+        sMask[s] = maskc;
         fence_proxy_async();
         mbar_expect_tx(&bar_a_full[s], (uint32_t)Ng * 4);
         bulk_g2s(sOff + s * Ng, offg + t * Npad + g0, (uint32_t)Ng * 4, &bar_a_full[s]);
@@ -278,7 +266,6 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         sLG[s * 128 + p] = start;
         sLGv[s * 128 + p] = lg;
         sJ[s * 128 + p] = (long long)jc[u];
-        if (p == kRef) sRef[s] = jc[u] >= 0 && (unsigned)Gc[u] < (unsigned)N ? Gc[u] : -1;
       }
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
@@ -346,7 +333,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
       if (!ok) break;
       float m = sLG[s * 128 + row], ssum = 0.f;
-      msk0 = tile_mask(t, s);
+      msk0 = tile_mask(s);
       int kb = 0;
       for (uint64_t msk = msk0; msk; msk &= msk - 1, ++c, ++kb) {
         if ((kb & 1) != half) continue;
@@ -888,6 +875,36 @@ k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int 
 }
 
 // ---------------------------------------------------------------------------
+// The 128-grain blocks pass 1 visits on each tile (bit q: image block q).
+// Reference: the label grain r of the tile's centre pixel, whose logit is
+// at least off_r - A_r everywhere in the tile, so that m(x) >= off_r - A_r;
+// block q, all of whose logits are at most mb[t][q], is left out when
+// mb[t][q] < off_r - A_r - kP1Far.  One thread per tile.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_tc_tile_masks(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const int* __restrict__ rank,
+                const float* __restrict__ offg, int Npad, const float* __restrict__ amax,
+                const float* __restrict__ mb, unsigned long long* __restrict__ masks) {
+  using TS = TileShape<DIM>;
+  constexpr int kRef = TS::X / 2 + TS::X * (TS::Y / 2) + TS::X * TS::Y * (TS::Z / 2);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tm.n_tiles) return;
+  const int nblk = Npad / 128;
+  unsigned long long msk = nblk >= 64 ? ~0ull : ((1ull << nblk) - 1ull);
+  float x[DIM], c[DIM];
+  const int64_t j = tile_pixel<DIM>(g, tm, t, kRef, x, c);
+  const int G = j >= 0 ? labels[j] : -1;
+  if ((unsigned)G < (unsigned)N) {
+    const int r = rank ? rank[G] : G;
+    const float lim = offg[t * Npad + r] - amax[r] - kP1Far;
+    for (int q = 0; q < nblk && q < 64; ++q)
+      if (mb[t * nblk + q] < lim) msk &= ~(1ull << q);
+  }
+  masks[t] = msk;
+}
+
+// ---------------------------------------------------------------------------
 // Per 128-grain block, the tiles whose need bit pass 1 set, in increasing
 // order (an ordered compaction, one CTA per block).
 // ---------------------------------------------------------------------------
@@ -1025,7 +1042,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const bool skip = c.grad && n_grp == 1 && skip_on;
   // pass 1 leaves out the blocks that the centre-logit bounds show to be
   // far below the tile's reference logit (structured grids)
-  const bool bounds = skip_on && !c.g.coords;
+  const bool bounds = skip_on && !c.g.coords && Npad / 128 <= 64;
   const bool order = skip && Npad <= kOrderMax;
 
   Scratch sc(st);
@@ -1048,6 +1065,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   int* rank = order ? sc.get<int>((size_t)N) : nullptr;
   float* amax = bounds ? sc.get<float>((size_t)Npad) : nullptr;
   float* mbb = bounds ? sc.get<float>((size_t)n_tiles * (Npad / 128)) : nullptr;
+  unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
   TileBound tb{};
   if (bounds) {
     using TS = TileShape<DIM>;
@@ -1093,7 +1111,11 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
            (k_tc_centre_logits<DIM, D><<<dim3((unsigned)(Npad / 256),
                                               (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles,
                                                                           4096)),
-                                         256, 0, st>>>(c.g, tm, th32t, N, Npad, offg, tb, amax, mbb)));
+                                         256, 0, st>>>(c.g, tm, th32t, perm, N, Npad, offg, tb, amax, mbb)));
+  if (bounds)
+    PD_TIMED(st, "tc_tile_masks",
+             k_tc_tile_masks<DIM><<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, rank, offg,
+                                                                                   Npad, amax, mbb, masks));
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
@@ -1101,8 +1123,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
              k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, offg,
-                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, rank, mbb,
-                                                      amax, Npad / 128, need, n_words, status));
+                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, masks, need,
+                                                      n_words, status));
   }
   // a launch that fails (resources, configuration) is an error of this call
   if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;

@@ -253,9 +253,9 @@ __device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float*
 // ---------------------------------------------------------------------------
 // Parameter images: rows = grains (in the order perm gives, when given;
 // padded to Npad with zero rows), K-major no-swizzle, one slice of KW
-// columns per term; plus float copies (grain rows, and transposed
-// K x Npad) used for the centre logits and the label logit of the
-// objective.
+// columns per term; plus a transposed float copy (K x Npad, in the
+// caller's grain order) used for the centre logits and the label logit of
+// the objective.
 // ---------------------------------------------------------------------------
 template <int KS>
 __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Npad, int K, int KW, double scale,
@@ -274,7 +274,8 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
   const uint16_t parts[3] = {h, m, l};
   const int KT = KW * n_terms(KS);
   for (int t = 0; t < n_terms(KS); ++t) *reinterpret_cast<uint16_t*>(img + kmaj(r, t * KW + k, KT)) = parts[t];
-  if (k < K) th32t[(int64_t)k * Npad + r] = (float)t;  // transposed, zero rows beyond N
+  // transposed float copy in the caller's grain order, zero rows beyond N
+  if (k < K) th32t[(int64_t)k * Npad + (src >= 0 ? src : r)] = (float)t;
 }
 
 // ---------------------------------------------------------------------------
@@ -414,8 +415,8 @@ struct TileBound {
 
 template <int DIM, int D>
 __global__ void __launch_bounds__(256)
-k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, int Npad, float* __restrict__ off,
-                   TileBound tb, float* __restrict__ amax, float* __restrict__ mb) {
+k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, const int* __restrict__ perm, int N,
+                   int Npad, float* __restrict__ off, TileBound tb, float* __restrict__ amax, float* __restrict__ mb) {
   constexpr int K = basis_K(DIM, D);
   __shared__ float sec[kCentreTiles][K];
   __shared__ float smx[kCentreTiles][8];
@@ -424,9 +425,11 @@ k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, i
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = Npad / 128;
   const bool live = i < Npad;  // (every thread takes part in the barriers)
+  // the grain of image row i (the float copy is in the caller's order)
+  const int src = perm ? (live ? perm[i] : -1) : (i < N ? i : -1);
   float th[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) th[k] = i < N ? th32t[(int64_t)k * Npad + i] : 0.f;
+  for (int k = 0; k < K; ++k) th[k] = src >= 0 ? th32t[(int64_t)k * Npad + src] : 0.f;
   float A = 0.f;
   if (mb) {
 #pragma unroll
@@ -452,7 +455,7 @@ k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, int N, i
       for (int k = 1; k < K; ++k) acc = fmaf(th[k], sec[q][k], acc);
       if (live) off[(t0 + q) * Npad + i] = acc;
       if (mb) {
-        float v = live && i < N ? acc + A : -INFINITY;
+        float v = src >= 0 ? acc + A : -INFINITY;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) smx[q][wid] = v;

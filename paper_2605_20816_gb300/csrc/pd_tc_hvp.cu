@@ -647,8 +647,8 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   }
   const dim3 gridc((unsigned)((Npad + 255) / 256),
                    (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles, 4096));
-  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, N, Npad, offg, TileBound{}, nullptr, nullptr)));
-  PD_TIMED(st, "tc_centre_u", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, v32t, N, Npad, uoffg, TileBound{}, nullptr, nullptr)));
+  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, nullptr, N, Npad, offg, TileBound{}, nullptr, nullptr)));
+  PD_TIMED(st, "tc_centre_u", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, v32t, nullptr, N, Npad, uoffg, TileBound{}, nullptr, nullptr)));
 
   auto k1 = k_tc_hvp_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
