@@ -436,7 +436,8 @@ template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2ThreadsG, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
            const float* __restrict__ lse, const int* __restrict__ kept, const int* __restrict__ n_kept_gb,
-           const int* __restrict__ perm, int slots, double* __restrict__ part, int* __restrict__ status) {
+           const int* __restrict__ perm, int slots, double* __restrict__ part, int* __restrict__ used,
+           int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
   constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
@@ -467,9 +468,9 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
   const int* klist = kept ? kept + (int64_t)gb * tm.n_tiles + k_lo : nullptr;
   auto tile_of = [&](int t) -> int64_t { return klist ? (int64_t)klist[t] : k_lo + t; };
   const int64_t c_begin = (int64_t)blockIdx.x * slots;
-  const int n_items = slots;                                          // chunk slots of this CTA
-  const int n_used = (n_kept + kP2ChunkTiles - 1) / kP2ChunkTiles;  // slots with a partial
+  const int n_used = (n_kept + kP2ChunkTiles - 1) / kP2ChunkTiles;  // chunk slots with a partial (<= slots)
   if (tid == 0) {
+    used[gb * gridDim.x + blockIdx.x] = n_used;  // the reduction reads these slots only
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < NB; ++s) {
@@ -712,12 +713,11 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     tmem_wait_ld();  // a prefetched load may be outstanding after an abort
     if (half == 0) {
       // the chunks not yet written: the last one (and, for a one-tile last
-      // chunk, the one before); after an abort the rest become NaN.  Chunk
-      // slots beyond the kept tiles' chunks hold zero.
+      // chunk, the one before); after an abort the rest become NaN
       for (int u = n_done; ok && u < n_used; ++u) ok = read_chunk(u);
-      if (gi >= 0) {
-        for (int u = n_done; u < n_items; ++u)
-          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + gi) * K + k] = ok ? 0.0 : NAN;
+      if (!ok && gi >= 0) {
+        for (int u = n_done; u < n_used; ++u)
+          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + gi) * K + k] = NAN;
       }
     }
   }
@@ -831,47 +831,31 @@ __global__ void __launch_bounds__(1024)
 k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int Npad, int* __restrict__ perm,
                  int* __restrict__ rank) {
   __shared__ unsigned long long key[kOrderMax];
-  int M = 1;
-  while (M < N) M <<= 1;
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    unsigned long long kv = ~0ull;
-    if (i < N) {
-      const long long cnt = (long long)lmom[(int64_t)i * K];
-      uint32_t code = 0xffffffffu;
-      if (cnt > 0) {
-        code = 0;
-        for (int a = 0; a < DIM; ++a) {
-          const double c = (double)(long long)lmom[(int64_t)i * K + 1 + a] / (double)cnt;  // in [-1, 1]
-          int v = (int)((c + 1.0) * 512.0);
-          v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
-          code |= spread_bits((uint32_t)v, DIM) << a;
-        }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const long long cnt = (long long)lmom[(int64_t)i * K];
+    uint32_t code = 0xffffffffu;
+    if (cnt > 0) {
+      code = 0;
+      for (int a = 0; a < DIM; ++a) {
+        const double c = (double)(long long)lmom[(int64_t)i * K + 1 + a] / (double)cnt;  // in [-1, 1]
+        int v = (int)((c + 1.0) * 512.0);
+        v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
+        code |= spread_bits((uint32_t)v, DIM) << a;
       }
-      kv = ((unsigned long long)code << 32) | (uint32_t)i;
     }
-    key[i] = kv;
+    key[i] = ((unsigned long long)code << 32) | (uint32_t)i;
   }
   __syncthreads();
-  // bitonic sort, ascending
-  for (int size = 2; size <= M; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const int j = i ^ stride;
-        if (j > i) {
-          const unsigned long long a = key[i], b = key[j];
-          if ((a > b) == ((i & size) == 0)) {
-            key[i] = b;
-            key[j] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  for (int r = threadIdx.x; r < Npad; r += blockDim.x) {
-    const int gi = r < N ? (int)(uint32_t)key[r] : -1;
-    perm[r] = gi;
-    if (gi >= 0) rank[gi] = r;
+  // the keys are distinct (index in the low half): a grain's rank is the
+  // number of smaller keys
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const unsigned long long ki = key[i];
+    int r = 0;
+    for (int j = 0; j < N; ++j) r += key[j] < ki;
+    perm[r] = i;
+    rank[i] = r;
   }
+  for (int r = N + threadIdx.x; r < Npad; r += blockDim.x) perm[r] = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -951,6 +935,50 @@ k_tc_kept_lists(const uint32_t* __restrict__ need, int64_t n_words, int64_t n_ti
     __syncthreads();
   }
   if (threadIdx.x == 0) counts[gb] = base;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient and objective of the evaluation: per grain the label part (64-bit
+// fixed point) plus the pass-2 partials of the chunk slots its block's CTAs
+// used, in a fixed order (CTA r, then slot u); block 0 also sums the
+// objective partials.  Rows are in the caller's grain order; the block of
+// grain gi is rank[gi] / 128 (gi / 128 without reordering).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_tc_reduce_eval(const double* __restrict__ part, int slots, int cpg, const int* __restrict__ used,
+                 const int* __restrict__ rank, int N, int K, const unsigned long long* __restrict__ base,
+                 double inv_fx, double scale, double* __restrict__ grad, const double* __restrict__ objp, int n_obj,
+                 double obj_scale, double* __restrict__ obj) {
+  __shared__ double ssum[8][32];
+  const int64_t NK = (int64_t)N * K;
+  if (obj && blockIdx.x == 0) {
+    if (threadIdx.y == 0) {
+      double v = 0.0;
+      for (int q = threadIdx.x; q < n_obj; q += 32) v += objp[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) *obj = v * obj_scale;
+    }
+  }
+  if (!grad) return;
+  const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  double s = 0.0;
+  if (q < NK) {
+    const int gi = (int)(q / K);
+    const int gb = (rank ? rank[gi] : gi) / 128;
+    for (int r = threadIdx.y; r < cpg; r += 8) {
+      const int nu = used[gb * cpg + r];
+      for (int u = 0; u < nu; ++u) s += part[((int64_t)r * slots + u) * NK + q];
+    }
+  }
+  ssum[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && q < NK) {
+    double t = (double)(long long)base[q] * inv_fx;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) t += ssum[y][threadIdx.x];
+    grad[q] = t * scale;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1054,6 +1082,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
   double* part = c.grad ? sc.get<double>((size_t)n_slots * N * K) : nullptr;
+  int* used = c.grad ? sc.get<int>((size_t)gblocks * cpg) : nullptr;  // chunk slots used per (block, CTA)
   unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   // one bit per (128-grain block, tile): the block has a probability that
   // the gradient pass cannot neglect on the tile; then the tiles per block
@@ -1140,17 +1169,16 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
              k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, perm, slots,
-                                                       part, status));
+                                                       part, used, status));
     if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   }
-  if (c.obj)
-    PD_TIMED(st, "reduce_obj",
-             k_reduce_obj<<<1, 1024, 0, st>>>(objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P, c.obj));
-  if (c.grad) {
+  if (c.obj || c.grad) {
     const int64_t NK = (int64_t)N * K;
-    PD_TIMED(st, "reduce_parts",
-             k_tc_reduce_grad<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
-                 part, (int)n_slots, NK, lmom, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), nullptr, c.grad));
+    const unsigned blocks = c.grad ? (unsigned)((NK + 31) / 32) : 1u;
+    PD_TIMED(st, "reduce_eval",
+             k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(
+                 part, slots, cpg, used, perm ? rank : nullptr, N, K, lmom, 1.0 / (double)fx, -1.0 / (c.eps * (double)P),
+                 c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P, c.obj));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }
