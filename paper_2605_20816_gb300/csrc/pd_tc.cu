@@ -321,7 +321,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     };
     // a block's 128 columns in four 32-column chunks, each loaded while the
     // one before is used; warpgroup `half` takes the visited blocks of odd
-    // or even position
+    // or even position (a prefetch of the next block's first chunk would
+    // keep 32 more registers live, above the 128 that 13 warps allow)
     uint32_t RA[32], RB[32];
     int it = 0;
     int64_t c = 0;

@@ -357,25 +357,31 @@ __device__ __forceinline__ float dot_f(const float* __restrict__ a, const float*
   return acc;
 }
 
-__device__ __forceinline__ float tree_max32(const float* v) {
-  float a[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) a[q] = fmaxf(v[q], v[q + 16]);
-#pragma unroll
-  for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-    for (int q = 0; q < w; ++q) a[q] = fmaxf(a[q], a[q + w]);
-  return a[0];
+// three-input maximum (a non-NaN operand wins over NaN, as in fmaxf)
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
+__device__ __forceinline__ float tree_max32(const float* v) {
+  float a[11];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) a[q] = fmax3f(v[3 * q], v[3 * q + 1], v[3 * q + 2]);
+  a[10] = fmaxf(v[30], v[31]);
+  const float b0 = fmax3f(a[0], a[1], a[2]), b1 = fmax3f(a[3], a[4], a[5]), b2 = fmax3f(a[6], a[7], a[8]);
+  return fmax3f(b0, b1, fmax3f(b2, a[9], a[10]));
+}
+// pairwise sums in packed fp32 adds (fixed order)
 __device__ __forceinline__ float tree_sum32(const float* v) {
-  float a[16];
+  float2 a[8];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) a[q] = v[q] + v[q + 16];
+  for (int q = 0; q < 8; ++q)
+    a[q] = __fadd2_rn(make_float2(v[4 * q], v[4 * q + 1]), make_float2(v[4 * q + 2], v[4 * q + 3]));
 #pragma unroll
-  for (int w = 8; w >= 1; w >>= 1)
+  for (int w = 4; w >= 1; w >>= 1)
 #pragma unroll
-    for (int q = 0; q < w; ++q) a[q] = a[q] + a[q + w];
-  return a[0];
+    for (int q = 0; q < w; ++q) a[q] = __fadd2_rn(a[q], a[q + w]);
+  return a[0].x + a[0].y;
 }
 
 // ---------------------------------------------------------------------------
