@@ -27,8 +27,8 @@
 //       writes it as the A operand (grains x pixels, K-major);
 //   D2 += C (128 grains x 128 pixels) . eta(tile) (128 pixels x K): the
 //       probability part of the gradient contraction, accumulated in TMEM
-//       over a chunk of tiles, then written as one double partial per
-//       grain and chunk.  The label part sum_{x in G_i} eta(x) comes from
+//       over a chunk of tiles; the chunks add up in double to one partial
+//       per grain and CTA.  The label part sum_{x in G_i} eta(x) comes from
 //       a separate pass over the pixels (k_tc_label_moments).
 //   A (tile, block) pair whose bit is clear would only add zeros: every
 //   c = -p of it is below 2^-26 and rounds to zero in the fp16 operand, so
@@ -437,8 +437,7 @@ template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2ThreadsG, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
            const float* __restrict__ lse, const int* __restrict__ kept, const int* __restrict__ n_kept_gb,
-           const int* __restrict__ perm, int slots, double* __restrict__ part, int* __restrict__ used,
-           int* __restrict__ status) {
+           const int* __restrict__ perm, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
   constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
@@ -468,10 +467,8 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
   const int n_kept = (int)(n_list * (blockIdx.x + 1) / gridDim.x - k_lo);
   const int* klist = kept ? kept + (int64_t)gb * tm.n_tiles + k_lo : nullptr;
   auto tile_of = [&](int t) -> int64_t { return klist ? (int64_t)klist[t] : k_lo + t; };
-  const int64_t c_begin = (int64_t)blockIdx.x * slots;
-  const int n_used = (n_kept + kP2ChunkTiles - 1) / kP2ChunkTiles;  // chunk slots with a partial (<= slots)
+  const int n_used = (n_kept + kP2ChunkTiles - 1) / kP2ChunkTiles;  // chunks
   if (tid == 0) {
-    used[gb * gridDim.x + blockIdx.x] = n_used;  // the reduction reads these slots only
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
     for (int s = 0; s < NB; ++s) {
@@ -613,8 +610,10 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     const int i = gb * 128 + gr;            // this thread's row of the parameter image
     const int gi = perm ? perm[i] : (i < N ? i : -1);  // its grain (-1: padding)
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    int n_done = 0;  // chunks whose partial this thread has written (first warpgroup)
-    // the D2 row of chunk u of this CTA: one double partial per grain
+    int n_done = 0;  // chunks this thread has added up (first warpgroup)
+    // the CTA's partial of this grain (a row of part): the D2 rows of its
+    // chunks added in order, in double
+    double* prow = gi >= 0 ? part + ((int64_t)blockIdx.x * N + gi) * K : nullptr;
     auto read_chunk = [&](int u) -> bool {
       const int db = u & 1;
       if (!mbar_wait_warp(&bar_d2_full[db], (uint32_t)((u >> 1) & 1), &abort_flag, status)) return false;
@@ -630,11 +629,12 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(&bar_d2_free[db]);
-      if (gi >= 0) {
-        double* row = part + ((c_begin + u) * N + gi) * K;
+      if (prow) {
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-          row[k] = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
+        for (int k = 0; k < K; ++k) {
+          const double v = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
+          prow[k] = u == 0 ? v : prow[k] + v;
+        }
       }
       n_done = u + 1;
       return true;
@@ -713,12 +713,11 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     }
     tmem_wait_ld();  // a prefetched load may be outstanding after an abort
     if (half == 0) {
-      // the chunks not yet written: the last one (and, for a one-tile last
-      // chunk, the one before); after an abort the rest become NaN
+      // the chunks not yet read: the last one (and, for a one-tile last
+      // chunk, the one before); the CTA's partial is NaN after an abort
       for (int u = n_done; ok && u < n_used; ++u) ok = read_chunk(u);
-      if (!ok && gi >= 0) {
-        for (int u = n_done; u < n_used; ++u)
-          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + gi) * K + k] = NAN;
+      if (prow && (!ok || n_used == 0)) {
+        for (int k = 0; k < K; ++k) prow[k] = ok ? 0.0 : NAN;
       }
     }
   }
@@ -816,7 +815,8 @@ k_tc_label_moments(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N
 // image a compact region of the domain, so that most (tile, block) pairs
 // carry only negligible probabilities.  Ties, and grains without pixels
 // (last), go by index: the order is deterministic.  perm[r] is the grain
-// of image row r (-1 beyond N), rank its inverse.  One CTA, N <= kOrderMax.
+// of image row r (-1 beyond N), rank its inverse.  N <= kOrderMax; one
+// thread per grain.
 // ---------------------------------------------------------------------------
 constexpr int kOrderMax = 2048;
 
@@ -828,7 +828,7 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t v, int dim) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int Npad, int* __restrict__ perm,
                  int* __restrict__ rank) {
   __shared__ unsigned long long key[kOrderMax];
@@ -848,15 +848,17 @@ k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int 
   }
   __syncthreads();
   // the keys are distinct (index in the low half): a grain's rank is the
-  // number of smaller keys
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  // number of smaller keys; every CTA holds all keys and ranks its 256
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
     const unsigned long long ki = key[i];
     int r = 0;
     for (int j = 0; j < N; ++j) r += key[j] < ki;
     perm[r] = i;
     rank[i] = r;
   }
-  for (int r = N + threadIdx.x; r < Npad; r += blockDim.x) perm[r] = -1;
+  if (blockIdx.x == 0)
+    for (int r = N + threadIdx.x; r < Npad; r += blockDim.x) perm[r] = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -940,18 +942,14 @@ k_tc_kept_lists(const uint32_t* __restrict__ need, int64_t n_words, int64_t n_ti
 
 // ---------------------------------------------------------------------------
 // Gradient and objective of the evaluation: per grain the label part (64-bit
-// fixed point) plus the pass-2 partials of the chunk slots its block's CTAs
-// used, in a fixed order (CTA r, then slot u); block 0 also sums the
-// objective partials.  Rows are in the caller's grain order; the block of
-// grain gi is rank[gi] / 128 (gi / 128 without reordering).
+// fixed point) plus the pass-2 partials of its block's CTAs, in a fixed
+// order; block 0 also sums the objective partials.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_tc_reduce_eval(const double* __restrict__ part, int slots, int cpg, const int* __restrict__ used,
-                 const int* __restrict__ rank, int N, int K, const unsigned long long* __restrict__ base,
+k_tc_reduce_eval(const double* __restrict__ part, int cpg, int64_t NK, const unsigned long long* __restrict__ base,
                  double inv_fx, double scale, double* __restrict__ grad, const double* __restrict__ objp, int n_obj,
                  double obj_scale, double* __restrict__ obj) {
   __shared__ double ssum[8][32];
-  const int64_t NK = (int64_t)N * K;
   if (obj && blockIdx.x == 0) {
     if (threadIdx.y == 0) {
       double v = 0.0;
@@ -964,14 +962,8 @@ k_tc_reduce_eval(const double* __restrict__ part, int slots, int cpg, const int*
   if (!grad) return;
   const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
   double s = 0.0;
-  if (q < NK) {
-    const int gi = (int)(q / K);
-    const int gb = (rank ? rank[gi] : gi) / 128;
-    for (int r = threadIdx.y; r < cpg; r += 8) {
-      const int nu = used[gb * cpg + r];
-      for (int u = 0; u < nu; ++u) s += part[((int64_t)r * slots + u) * NK + q];
-    }
-  }
+  if (q < NK)
+    for (int r = threadIdx.y; r < cpg; r += 8) s += part[(int64_t)r * NK + q];
   ssum[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.y == 0 && q < NK) {
@@ -1056,10 +1048,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int gridm = (int)((P + 255) / 256);  // merge blocks of a grain-split pass 1
   const int gblocks = (N + 127) / 128;  // pass-2 grain blocks
   // pass 2: one wave of CTAs per grain block, each with a contiguous share
-  // of the block's tiles and one gradient partial per kP2ChunkTiles of them
+  // of the block's tiles and one gradient partial per grain
   const int cpg = (int)std::min<int64_t>((n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles, std::max(1, sms / gblocks));
-  const int slots = (int)(((n_tiles + cpg - 1) / cpg + kP2ChunkTiles - 1) / kP2ChunkTiles);
-  const int64_t n_slots = (int64_t)cpg * slots;
   // With a single pass 1 (which sees all grains of a pixel) the gradient
   // pass visits only the (tile, block) pairs with a probability that
   // survives in its fp16 operand, and the grains are reordered so that
@@ -1082,8 +1072,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
-  double* part = c.grad ? sc.get<double>((size_t)n_slots * N * K) : nullptr;
-  int* used = c.grad ? sc.get<int>((size_t)gblocks * cpg) : nullptr;  // chunk slots used per (block, CTA)
+  double* part = c.grad ? sc.get<double>((size_t)cpg * N * K) : nullptr;  // one partial per pass-2 CTA and grain
   unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   // one bit per (128-grain block, tile): the block has a probability that
   // the gradient pass cannot neglect on the tile; then the tiles per block
@@ -1129,7 +1118,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
                                                                                        lmom)));
   }
   if (order)
-    PD_TIMED(st, "tc_grain_order", k_tc_grain_order<DIM><<<1, 1024, 0, st>>>(lmom, N, K, Npad, perm, rank));
+    PD_TIMED(st, "tc_grain_order",
+             k_tc_grain_order<DIM><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lmom, N, K, Npad, perm, rank));
   const double scale = Arith<float>::theta_scale(c.eps);
   {
     const int64_t n = (int64_t)Npad * KW;
@@ -1169,17 +1159,17 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
       return PD_ECUDA;
     dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, perm, slots,
-                                                       part, used, status));
+             k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, perm, part,
+                                                       status));
     if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   }
   if (c.obj || c.grad) {
     const int64_t NK = (int64_t)N * K;
     const unsigned blocks = c.grad ? (unsigned)((NK + 31) / 32) : 1u;
     PD_TIMED(st, "reduce_eval",
-             k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(
-                 part, slots, cpg, used, perm ? rank : nullptr, N, K, lmom, 1.0 / (double)fx, -1.0 / (c.eps * (double)P),
-                 c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P, c.obj));
+             k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(part, cpg, NK, lmom, 1.0 / (double)fx,
+                                                              -1.0 / (c.eps * (double)P), c.grad, objp,
+                                                              n_grp > 1 ? gridm : grid1, 1.0 / (double)P, c.obj));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }

@@ -487,7 +487,7 @@ k_tc_centre_logits(Geom g, TileMap tm, const float* __restrict__ th32t, const in
 // contractions, so neither waits behind the other.  The consumers pick the
 // next tile's logits up early when they are already there.  The gradient
 // accumulates in TMEM over chunks of kP2ChunkTiles tiles (two buffers,
-// alternating), and each chunk becomes one double partial per grain.
+// alternating), and the chunks add up in double to one partial per grain.
 //
 // Shared-memory operand layouts (all K-major, no swizzle):
 //   sB   pixel rows x KT feature differences; the 8-row groups lie
