@@ -58,18 +58,20 @@ namespace {
 // Pass 1: log2 S(x) per pixel and objective partials.
 // ---------------------------------------------------------------------------
 // Pass 1 takes the grains of a tile in blocks of 128 (one MMA of N = 128
-// per block and product) through a ring of four 128-column TMEM buffers;
-// the two epilogue warpgroups take alternate blocks.  A block whose logits
+// per block and product); the two epilogue warpgroups take alternate
+// tiles, each all blocks of its tile (so that a pixel's log-sum-exp needs
+// no exchange), through its own two 128-column TMEM buffers.  A block whose logits
 // are all more than 130 below the logit of the label grain of the tile's
 // centre pixel, everywhere in the tile (a bound from the centre logits,
 // see k_tc_centre_logits), would only add exponentials that underflow to
 // zero: it is not visited.
 constexpr int kP1Bufs = 4;
+constexpr int kP1Stages = 3;  // pixel-operand stages at most (two tiles in the epilogue, one being written)
 constexpr float kP1Far = 130.f;
 
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kP1Threads, 1)
-k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng,
+k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng, int n_stages,
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
            const float* __restrict__ offg, float* __restrict__ lse_out, double* __restrict__ obj_part,
            float2* __restrict__ ms_out, float* __restrict__ lg_out, const unsigned long long* __restrict__ masks,
@@ -81,22 +83,22 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   constexpr uint32_t kTileBytes = kTcPixTile * kRowBytes;
   constexpr uint32_t IDESC = idesc_bf16(128, 128);
 
+  const int S = n_stages;  // 2 or 3
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;                                            // Ng x KT (this launch's grains)
-  uint8_t* sA = smem + (size_t)Ng * kRowBytes;                   // 2 stages x 128 x KT
-  float* sOff = reinterpret_cast<float*>(sA + 2 * kTileBytes);   // 2 stages x Ng centre logits (bulk copied)
-  float2* sPart = reinterpret_cast<float2*>(sOff + 2 * Ng);     // 2 stages x 128 (max, sum) of half 1
-  float* sLG = reinterpret_cast<float*>(sPart + 2 * 128);        // 2 stages x 128 starting max
-  float* sLGv = sLG + 2 * 128;                                   // 2 stages x 128 label logits
-  long long* sJ = reinterpret_cast<long long*>(sLGv + 2 * 128);  // 2 stages x 128 pixel indices
-  float* sBm = reinterpret_cast<float*>(sJ + 2 * 128);           // 2 stages x Ng/128 x 128 block maxima
-  float* sTh = sBm + 2 * Ng;                                     // K x Ng scaled parameters (when resident)
-  __shared__ __align__(8) uint64_t bar_theta, bar_a_full[2], bar_a_empty[2], bar_off_free[2], bar_d_full[kP1Bufs],
-      bar_d_empty[kP1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
+  uint8_t* sA = smem + (size_t)Ng * kRowBytes;                   // S stages x 128 x KT
+  float* sOff = reinterpret_cast<float*>(sA + S * kTileBytes);   // S stages x Ng centre logits (bulk copied)
+  float* sLG = sOff + S * Ng;                                    // S stages x 128 starting max
+  float* sLGv = sLG + S * 128;                                   // S stages x 128 label logits
+  long long* sJ = reinterpret_cast<long long*>(sLGv + S * 128);  // S stages x 128 pixel indices
+  float* sBm = reinterpret_cast<float*>(sJ + S * 128);           // S stages x Ng/128 x 128 block maxima
+  float* sTh = sBm + S * Ng;                                     // K x Ng scaled parameters (when resident)
+  __shared__ __align__(8) uint64_t bar_theta, bar_a_full[kP1Stages], bar_a_empty[kP1Stages], bar_off_free[kP1Stages],
+      bar_d_full[kP1Bufs], bar_d_empty[kP1Bufs], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ double sred[kP1Threads / 32];
-  __shared__ unsigned long long sMask[2];  // blocks visited on the stage's tile (bit q: image block q)
+  __shared__ unsigned long long sMask[kP1Stages];  // blocks visited on the stage's tile (bit q: image block q)
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nq = Ng / 128;  // grain blocks of this launch
@@ -107,12 +109,10 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_theta, 1);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&bar_a_full[s], kP1Producers);
       mbar_init(&bar_a_empty[s], 1);
-      mbar_init(&bar_off_free[s], kTcConsumers);
-      mbar_init(&bar_part_full[s], 128);
-      mbar_init(&bar_part_free[s], 128);
+      mbar_init(&bar_off_free[s], 128);  // the warpgroup of the stage's tile
     }
     for (int b = 0; b < kP1Bufs; ++b) {
       mbar_init(&bar_d_full[b], 1);
@@ -147,28 +147,67 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           bulk_g2s(rdst + off, rsrc + off, row_t - off < 32768u ? row_t - off : 32768u, &bar_theta);
       }
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
-      int64_t c = 0;  // block counter over the whole loop
-      int it = 0;
-      for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
-        const int s = it & 1;
-        ok = mbar_wait(&bar_a_full[s], (it >> 1) & 1, &abort_flag, status);
-        if (!ok) break;
-        tc_fence_after();
-        for (uint64_t msk = tile_mask(s); msk; msk &= msk - 1, ++c) {
-          const int q = __ffsll((long long)msk) - 1;
-          const int b = (int)(c % kP1Bufs);
-          if (c >= kP1Bufs) {
-            ok = mbar_wait(&bar_d_empty[b], (uint32_t)(((c / kP1Bufs) - 1) & 1), &abort_flag, status);
-            if (!ok) break;
-            tc_fence_after();
+      // Two cursors, one per epilogue warpgroup: cursor h holds a tile of
+      // position parity h and issues its blocks into the warpgroup's two
+      // TMEM buffers (h * 2, h * 2 + 1).  Tiles are taken in order, each
+      // once its operands are in; the cursors alternate as their buffers
+      // free, so that neither warpgroup waits behind the other's tile.
+      // Every wait below is a non-blocking test inside one bounded loop.
+      int it_next = 0;            // position of the next tile to take
+      int it_of[2] = {0, 0};      // position of each cursor's tile
+      uint64_t rem[2] = {0, 0};   // its blocks not yet issued
+      bool act[2] = {false, false};
+      int64_t cw[2] = {0, 0};     // blocks issued into each warpgroup's ring
+      const int n_mine = (int)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // tiles of this CTA
+      uint64_t t_last = global_ns();
+      while (ok) {
+        bool done = true, prog = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!act[h]) {
+            if (it_next < n_mine && (it_next & 1) == h) {
+              done = false;
+              const int s = it_next % S;
+              if (mbar_peek(&bar_a_full[s], (uint32_t)((it_next / S) & 1))) {
+                tc_fence_after();
+                it_of[h] = it_next++;
+                rem[h] = tile_mask(s);
+                act[h] = true;
+                prog = true;
+              }
+            }
+            continue;
           }
+          done = false;
+          const int s = it_of[h] % S;
+          if (rem[h] == 0) {
+            mma_commit(&bar_a_empty[s]);  // the tile's operands are no longer read
+            act[h] = false;
+            prog = true;
+            continue;
+          }
+          const int b = h * 2 + (int)(cw[h] & 1);
+          if (cw[h] >= 2 && !mbar_peek(&bar_d_empty[b], (uint32_t)(((cw[h] >> 1) - 1) & 1))) continue;
+          tc_fence_after();
+          const int q = __ffsll((long long)rem[h]) - 1;
+          rem[h] &= rem[h] - 1;
           const uint32_t aaddr = smem_addr(sA + s * kTileBytes);
           const uint32_t baddr = smem_addr(sB + (size_t)q * 128 * kRowBytes);
           mma_terms<KS, KW>(tmem + b * 128, aaddr, KT * 16, false, baddr, KT * 16, IDESC);
           mma_commit(&bar_d_full[b]);
+          ++cw[h];
+          prog = true;
         }
-        if (!ok) break;
-        mma_commit(&bar_a_empty[s]);
+        if (done) break;
+        if (prog) {
+          t_last = global_ns();
+        } else if (abort_flag) {
+          ok = false;
+        } else if (global_ns() - t_last > kWaitLimitNs) {
+          abort_flag = 1;
+          atomicCAS(status, 0, PD_ETIMEOUT);
+          ok = false;
+        }
       }
       // every MMA issued above has completed before TMEM is released
       mma_commit(&bar_drain);
@@ -214,7 +253,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     if (ok && blockIdx.x < n_tiles) fetch(blockIdx.x);
     int it = 0;
     for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
-      const int s = it & 1, use = it >> 1;
+      const int s = it % S, use = it / S;
       int64_t jc[kP1PixPerThread];
       float xc[kP1PixPerThread][DIM], cc[DIM];
       int Gc[kP1PixPerThread];
@@ -320,28 +359,25 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       return cm;
     };
     // a block's 128 columns in four 32-column chunks, each loaded while the
-    // one before is used; warpgroup `half` takes the visited blocks of odd
-    // or even position (a prefetch of the next block's first chunk would
-    // keep 32 more registers live, above the 128 that 13 warps allow)
+    // one before is used; warpgroup `half` takes the tiles of even or odd
+    // position and, in order, all their visited blocks
     uint32_t RA[32], RB[32];
     int it = 0;
-    int64_t c = 0;
+    int64_t cw = 0;  // blocks this warpgroup has read
     bool ok = true;
-    uint64_t msk0 = 0;
     for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
-      const int s = it & 1;
+      if ((it & 1) != half) continue;
+      const int s = it % S;
       // the stage's operands and per-row values come from the producers
-      ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
+      ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it / S) & 1), &abort_flag, status);
       if (!ok) break;
       float m = sLG[s * 128 + row], ssum = 0.f;
-      msk0 = tile_mask(s);
-      int kb = 0;
-      for (uint64_t msk = msk0; msk; msk &= msk - 1, ++c, ++kb) {
-        if ((kb & 1) != half) continue;
+      const uint64_t msk0 = tile_mask(s);
+      for (uint64_t msk = msk0; msk; msk &= msk - 1, ++cw) {
         const int q = __ffsll((long long)msk) - 1;
-        const int b = (int)(c % kP1Bufs);
+        const int b = half * 2 + (int)(cw & 1);  // this warpgroup's two buffers
         const uint32_t col = (uint32_t)(b * 128);
-        ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kP1Bufs) & 1), &abort_flag, status);
+        ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((cw >> 1) & 1), &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
         tmem_ld32(tmem + lane_base + col, RA);
@@ -365,45 +401,26 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         sBm[s * Ng + q * 128 + row] = bm;
       }
       if (!ok) break;
-      // combine the two warpgroups' parts of each pixel (bounded mbarrier
-      // hand-off; slot s is reused every 2 tiles)
-      if (half == 1) {
-        if (it >= 2 && !mbar_wait_warp(&bar_part_free[s], (uint32_t)(((it >> 1) - 1) & 1), &abort_flag, status)) {
-          ok = false;
-          break;
+      const int64_t j = sJ[s * 128 + row];
+      float lse = NAN;
+      if (j >= 0) {
+        if (ms_out) {
+          ms_out[j] = make_float2(m, ssum);  // this launch's grains only: merged later
+        } else {
+          lse = m + Arith<float>::lg(ssum);
+          lse_out[j] = lse;
+          racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
         }
-        sPart[s * 128 + row] = make_float2(m, ssum);
-        mbar_arrive(&bar_part_full[s]);
-      } else {
-        if (!mbar_wait_warp(&bar_part_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status)) {
-          ok = false;
-          break;
-        }
-        const float2 o = sPart[s * 128 + row];
-        mbar_arrive(&bar_part_free[s]);
-        const int64_t j = sJ[s * 128 + row];
-        float lse = NAN;
-        if (j >= 0) {
-          const float mm = fmaxf(m, o.x);
-          const float sum = ssum * Arith<float>::ex(m - mm) + o.y * Arith<float>::ex(o.x - mm);
-          if (ms_out) {
-            ms_out[j] = make_float2(mm, sum);  // this launch's grains only: merged later
-          } else {
-            lse = mm + Arith<float>::lg(sum);
-            lse_out[j] = lse;
-            racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
-          }
-        }
-        if (need_bits) {
-          // a 128-grain block is needed by the gradient pass on this tile
-          // unless every probability in it is below 2^-26: the fp16
-          // gradient operand would round all of them to zero
-          for (int q = 0; q < nq; ++q) {
-            const bool nd = ((msk0 >> q) & 1) && j >= 0 && !(sBm[s * Ng + q * 128 + row] < lse - 26.f);
-            const uint32_t bal = __ballot_sync(0xffffffffu, nd);
-            if (lane == 0 && bal)
-              atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
-          }
+      }
+      if (need_bits) {
+        // a 128-grain block is needed by the gradient pass on this tile
+        // unless every probability in it is below 2^-26: the fp16
+        // gradient operand would round all of them to zero
+        for (int q = 0; q < nq; ++q) {
+          const bool nd = ((msk0 >> q) & 1) && j >= 0 && !(sBm[s * Ng + q * 128 + row] < lse - 26.f);
+          const uint32_t bal = __ballot_sync(0xffffffffu, nd);
+          if (lane == 0 && bal)
+            atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
         }
       }
       mbar_arrive(&bar_off_free[s]);
@@ -1010,14 +1027,14 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int Npad = (N + kTcGrainTile - 1) / kTcGrainTile * kTcGrainTile;  // parameter image rows
   const size_t row_bytes = (size_t)KT * 2;
   constexpr size_t kCap = 220 * 1024;
-  // pass 1 keeps the image of ng grains resident: image, 2 operand stages,
-  // 2 x centre logits, 2 x (max, sum), 2 x start, 2 x label logit, 2 x pixel
-  // index, 2 x block maxima, and the float parameters when they fit too.  More grains than
-  // one SM holds are split into groups of ng, one launch each, whose
-  // (max, sum) per pixel are merged afterwards.
-  auto p1_bytes = [&](size_t ng, bool th_res) {
-    return ng * row_bytes + 2 * kTcPixTile * row_bytes + 2 * ng * 4 + 2 * kTcPixTile * 8 + 4 * kTcPixTile * 4 +
-           2 * kTcPixTile * 8 + 2 * ng * 4 + (th_res ? (size_t)K * ng * 4 : 0);
+  // pass 1 keeps the image of ng grains resident: the image, and per
+  // operand stage the pixel rows, centre logits, start and label logits,
+  // pixel indices and block maxima; and the float parameters when they
+  // fit too.  More grains than one SM holds are split into groups of ng,
+  // one launch each, whose (max, sum) per pixel are merged afterwards.
+  auto p1_bytes = [&](size_t ng, bool th_res, size_t S = 2) {
+    return ng * row_bytes + S * (kTcPixTile * row_bytes + ng * 4 + 2 * kTcPixTile * 4 + kTcPixTile * 8 + ng * 4) +
+           (th_res ? (size_t)K * ng * 4 : 0);
   };
   int n_grp = 1, Ng = Npad;
   while (p1_bytes((size_t)Ng, false) > kCap && Ng > kTcGrainTile) {
@@ -1026,7 +1043,9 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   }
   n_grp = (Npad + Ng - 1) / Ng;
   const int th_resident = p1_bytes((size_t)Ng, true) <= kCap ? 1 : 0;
-  const size_t smem1 = p1_bytes((size_t)Ng, th_resident != 0);
+  // a third operand stage where it fits beside the same grains
+  const int p1_stages = p1_bytes((size_t)Ng, th_resident != 0, kP1Stages) <= kCap ? kP1Stages : 2;
+  const size_t smem1 = p1_bytes((size_t)Ng, th_resident != 0, (size_t)p1_stages);
   // pass-2 stages: four pixel-operand and two gradient-operand stages when
   // they fit, else fewer
   using L2 = Pass2Layout<DIM, D, KS>;
@@ -1142,7 +1161,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   for (int q = 0; q < n_grp; ++q) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
-             k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, img, th32t, th_resident, offg,
+             k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, p1_stages, img, th32t,
+                                                      th_resident, offg,
                                                       lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, masks, need,
                                                       n_words, status));
   }
