@@ -406,6 +406,9 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       if (j >= 0) {
         if (ms_out) {
           ms_out[j] = make_float2(m, ssum);  // this launch's grains only: merged later
+          // a lower bound of the pixel's log2 S for the need bits: this
+          // group's part, and the label logit (one term of the full sum)
+          lse = fmaxf(m + Arith<float>::lg(ssum), sLG[s * 128 + row]);
         } else {
           lse = m + Arith<float>::lg(ssum);
           lse_out[j] = lse;
@@ -1069,15 +1072,15 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   // pass 2: one wave of CTAs per grain block, each with a contiguous share
   // of the block's tiles and one gradient partial per grain
   const int cpg = (int)std::min<int64_t>((n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles, std::max(1, sms / gblocks));
-  // With a single pass 1 (which sees all grains of a pixel) the gradient
-  // pass visits only the (tile, block) pairs with a probability that
-  // survives in its fp16 operand, and the grains are reordered so that
-  // blocks are compact regions.
+  // The gradient pass visits only the (tile, block) pairs with a
+  // probability that survives in its fp16 operand (judged against a lower
+  // bound of log2 S when pass 1 runs in grain groups), and the grains are
+  // reordered so that blocks are compact regions.
   // (PD_TC_NO_SKIP=1 in the environment visits every pair in index order,
   // for tests that compare the two)
   const char* no_skip = getenv("PD_TC_NO_SKIP");
   const bool skip_on = !(no_skip && no_skip[0] && no_skip[0] != '0');
-  const bool skip = c.grad && n_grp == 1 && skip_on;
+  const bool skip = c.grad && skip_on;
   // pass 1 leaves out the blocks that the centre-logit bounds show to be
   // far below the tile's reference logit (structured grids)
   const bool bounds = skip_on && !c.g.coords && Npad / 128 <= 64;
