@@ -784,104 +784,6 @@ k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float*
 }
 
 // ---------------------------------------------------------------------------
-// Label part of eq. (grad): sum_{x in G_i} eta(x) per grain, at the points
-// of the tile walk of the two passes.  A warp sums the features of each
-// group of equal labels in fp32 (a fixed butterfly order), and lane k adds
-// the group's feature-k sum to the grain's 64-bit fixed-point accumulator,
-// so that the result does not depend on the order of the atomics.
-// ---------------------------------------------------------------------------
-template <int DIM, int D>
-__global__ void __launch_bounds__(256)
-k_tc_label_moments(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, float fx_scale,
-                   unsigned long long* __restrict__ acc) {
-  constexpr int K = basis_K(DIM, D);
-  static_assert(K <= 32, "one lane per feature");
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t t = q / kTcPixTile;
-  int G = -1;
-  float x[DIM], c[DIM], eta[K];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) x[a] = 0.f;
-  if (t < tm.n_tiles) {
-    const int64_t j = tile_pixel<DIM>(g, tm, t, (int)(q % kTcPixTile), x, c);
-    if (j >= 0) {
-      G = labels[j];
-      if ((unsigned)G >= (unsigned)N) G = -1;
-    }
-  }
-  legendre_features<DIM, D>(x, eta);
-  const int lane = threadIdx.x & 31;
-  unsigned todo = __ballot_sync(0xffffffffu, G >= 0);
-  while (todo) {
-    const int L = __shfl_sync(0xffffffffu, G, __ffs(todo) - 1);
-    const bool mine = G == L;
-    float pick = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float v = mine ? eta[k] : 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == k) pick = v;
-    }
-    if (lane < K) atomicAdd(&acc[(int64_t)L * K + lane], (unsigned long long)__float2ll_rn(pick * fx_scale));
-    todo &= ~__ballot_sync(0xffffffffu, mine);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Grain order of the gradient pass.  Grains sorted by the Morton code of
-// their label centroid (from the fixed-point label sums: feature 0 is 1,
-// features 1..DIM are x_1..x_DIM) make a 128-grain block of the parameter
-// image a compact region of the domain, so that most (tile, block) pairs
-// carry only negligible probabilities.  Ties, and grains without pixels
-// (last), go by index: the order is deterministic.  perm[r] is the grain
-// of image row r (-1 beyond N), rank its inverse.  N <= kOrderMax; one
-// thread per grain.
-// ---------------------------------------------------------------------------
-constexpr int kOrderMax = 2048;
-
-__device__ __forceinline__ uint32_t spread_bits(uint32_t v, int dim) {
-  // bit b of v moves to bit dim * b
-  uint32_t r = 0;
-  for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (dim * b);
-  return r;
-}
-
-template <int DIM>
-__global__ void __launch_bounds__(256)
-k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int Npad, int* __restrict__ perm,
-                 int* __restrict__ rank) {
-  __shared__ unsigned long long key[kOrderMax];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const long long cnt = (long long)lmom[(int64_t)i * K];
-    uint32_t code = 0xffffffffu;
-    if (cnt > 0) {
-      code = 0;
-      for (int a = 0; a < DIM; ++a) {
-        const double c = (double)(long long)lmom[(int64_t)i * K + 1 + a] / (double)cnt;  // in [-1, 1]
-        int v = (int)((c + 1.0) * 512.0);
-        v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
-        code |= spread_bits((uint32_t)v, DIM) << a;
-      }
-    }
-    key[i] = ((unsigned long long)code << 32) | (uint32_t)i;
-  }
-  __syncthreads();
-  // the keys are distinct (index in the low half): a grain's rank is the
-  // number of smaller keys; every CTA holds all keys and ranks its 256
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    const unsigned long long ki = key[i];
-    int r = 0;
-    for (int j = 0; j < N; ++j) r += key[j] < ki;
-    perm[r] = i;
-    rank[i] = r;
-  }
-  if (blockIdx.x == 0)
-    for (int r = N + threadIdx.x; r < Npad; r += blockDim.x) perm[r] = -1;
-}
-
-// ---------------------------------------------------------------------------
 // The 128-grain blocks pass 1 visits on each tile (bit q: image block q).
 // Reference: the label grain r of the tile's centre pixel, whose logit is
 // at least off_r - A_r everywhere in the tile, so that m(x) >= off_r - A_r;
@@ -909,55 +811,6 @@ k_tc_tile_masks(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, c
       if (mb[t * nblk + q] < lim) msk &= ~(1ull << q);
   }
   masks[t] = msk;
-}
-
-// ---------------------------------------------------------------------------
-// Per 128-grain block, the tiles whose need bit pass 1 set, in increasing
-// order (an ordered compaction, one CTA per block).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
-k_tc_kept_lists(const uint32_t* __restrict__ need, int64_t n_words, int64_t n_tiles, int* __restrict__ lists,
-                int* __restrict__ counts) {
-  __shared__ int wsum[32];
-  __shared__ int base;
-  const int gb = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t* row = need + (int64_t)gb * n_words;
-  int* out = lists + (int64_t)gb * n_tiles;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  for (int64_t w0 = 0; w0 < n_words; w0 += 1024) {
-    const int64_t w = w0 + threadIdx.x;
-    uint32_t bits = w < n_words ? row[w] : 0u;
-    const int c = __popc(bits);
-    int x = c;  // inclusive scan in the warp
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      int v = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-      }
-      wsum[lane] = v;  // inclusive over warps
-    }
-    __syncthreads();
-    int pos = base + (wid > 0 ? wsum[wid - 1] : 0) + x - c;
-    while (bits) {
-      const int b = __ffs((int)bits) - 1;
-      out[pos++] = (int)(w * 32 + b);
-      bits &= bits - 1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) base += wsum[31];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) counts[gb] = base;
 }
 
 // ---------------------------------------------------------------------------

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_t* __restrict__ img,
                const uint8_t* __restrict__ vimg, const float* __restrict__ offg, const float* __restrict__ uoffg,
                float* __restrict__ lse_out, float* __restrict__ ubar_out, float4* __restrict__ ms_out,
-               int* __restrict__ status) {
+               uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
@@ -72,6 +72,7 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
   float* sUoff = sOff + 2 * Ng;                                  // 2 stages x Ng centre parts of u
   float4* sPart = reinterpret_cast<float4*>(sUoff + 2 * Ng);    // 2 stages x 128 (max, S, T) of half 1
   long long* sJ = reinterpret_cast<long long*>(sPart + 2 * 128);  // 2 stages x 128 pixel indices
+  float* sBm = reinterpret_cast<float*>(sJ + 2 * 128);           // 2 stages x Ng/128 blocks x 2 halves x 128
   __shared__ __align__(8) uint64_t bar_img, bar_a_full[2], bar_a_empty[2], bar_off_free[2], bar_d_full[kH1Bufs],
       bar_d_empty[kH1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
@@ -180,13 +181,13 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
     // one 32-grain chunk: logits r + off, u = w + uoff; the online
     // log-sum-exp (m, S) and T = sum 2^(l - m) u share the rescaling
     auto chunk = [&](const uint32_t(&r)[32], const uint32_t(&w)[32], const float* off, const float* uoff, int nv,
-                     float& m, float& S, float& T) {
-      if (nv <= 0) return;
+                     float& m, float& S, float& T) -> float {
+      if (nv <= 0) return -INFINITY;
       float v[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) v[q] = q < nv ? __uint_as_float(r[q]) + off[q] : -INFINITY;
       const float cm = tree_max32(v);
-      if (__all_sync(0xffffffffu, cm < m - 127.f)) return;
+      if (__all_sync(0xffffffffu, cm < m - 127.f)) return cm;
       const float mn = fmaxf(m, cm);
       const float sc = Arith<float>::ex(m - mn);
       float es = 0.f, eu = 0.f;
@@ -199,6 +200,7 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
       S = fmaf(S, sc, es);
       T = fmaf(T, sc, eu);
       m = mn;
+      return cm;
     };
     uint32_t R[32], U[32];
     int it = 0;
@@ -216,6 +218,7 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
         tc_fence_after();
         const int cbase = gt * kH1Tile + half * 64;
         const int nrem = N - g0 - cbase;
+        float bm = -INFINITY;
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
           const uint32_t col = (uint32_t)(b * 256 + half * 64 + 32 * h2);
@@ -226,8 +229,11 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
             tc_fence_before();
             mbar_arrive(&bar_d_empty[b]);  // both halves of the buffer are in registers
           }
-          chunk(R, U, sOff + s * Ng + cbase + 32 * h2, sUoff + s * Ng + cbase + 32 * h2, nrem - 32 * h2, m, S, T);
+          bm = fmaxf(bm, chunk(R, U, sOff + s * Ng + cbase + 32 * h2, sUoff + s * Ng + cbase + 32 * h2,
+                               nrem - 32 * h2, m, S, T));
         }
+        // the largest logit of this pixel in the thread's half of the block
+        sBm[((s * n_gt + gt) * 2 + half) * 128 + row] = bm;
       }
       if (!ok) break;
       // combine the two column halves of each pixel
@@ -246,15 +252,31 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
         const float4 o = sPart[s * 128 + row];
         mbar_arrive(&bar_part_free[s]);
         const int64_t j = sJ[s * 128 + row];
+        float lse = NAN;
         if (j >= 0) {
           const float mm = fmaxf(m, o.x);
           const float a = Arith<float>::ex(m - mm), bb = Arith<float>::ex(o.x - mm);
           const float Sm = S * a + o.y * bb, Tm = T * a + o.z * bb;
+          // log2 S of the pixel, or of this group's part (a lower bound)
+          lse = mm + Arith<float>::lg(Sm);
           if (ms_out) {
             ms_out[j] = make_float4(mm, Sm, Tm, 0.f);
           } else {
-            lse_out[j] = mm + Arith<float>::lg(Sm);
+            lse_out[j] = lse;
             ubar_out[j] = Tm / Sm;
+          }
+        }
+        if (need_bits) {
+          // a 128-grain block is needed by the HVP pass 2 on this tile
+          // unless every probability in it is below 2^-32: with |u - ubar|
+          // <= 2K <= 64, every c = p (u - ubar) of it is below 2^-26 and
+          // rounds to zero in fp16
+          for (int q = 0; q < n_gt; ++q) {
+            const float bmq = fmaxf(sBm[((s * n_gt + q) * 2) * 128 + row], sBm[((s * n_gt + q) * 2 + 1) * 128 + row]);
+            const bool nd = j >= 0 && !(bmq < lse - 32.f);
+            const uint32_t bal = __ballot_sync(0xffffffffu, nd);
+            if (lane == 0 && bal)
+              atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
           }
         }
       }
@@ -310,8 +332,8 @@ template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2Threads, 1)
 k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const uint8_t* __restrict__ vimg,
                const float* __restrict__ offg, const float* __restrict__ uoffg, const float* __restrict__ lse,
-               const float* __restrict__ ubar, int64_t n_chunks, double* __restrict__ part,
-               int* __restrict__ status) {
+               const float* __restrict__ ubar, const int* __restrict__ kept, const int* __restrict__ n_kept_gb,
+               const int* __restrict__ perm, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
   constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
@@ -336,11 +358,14 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int gb = blockIdx.y;
-  const int64_t c_begin = (int64_t)blockIdx.x * n_chunks / gridDim.x;
-  const int64_t c_end = (int64_t)(blockIdx.x + 1) * n_chunks / gridDim.x;
-  const int64_t t_begin = c_begin * kP2ChunkTiles;
-  const int n_pt = (int)(min(c_end * kP2ChunkTiles, tm.n_tiles) - t_begin);
-  const int n_items = (int)(c_end - c_begin);
+  // this CTA's share of the tiles on which the grain block has a
+  // non-negligible probability (all tiles without the lists), in order
+  const int64_t n_list = kept ? (int64_t)n_kept_gb[gb] : tm.n_tiles;
+  const int64_t k_lo = n_list * blockIdx.x / gridDim.x;
+  const int n_pt = (int)(n_list * (blockIdx.x + 1) / gridDim.x - k_lo);
+  const int* klist = kept ? kept + (int64_t)gb * tm.n_tiles + k_lo : nullptr;
+  auto tile_of = [&](int t) -> int64_t { return klist ? (int64_t)klist[t] : k_lo + t; };
+  const int n_items = (n_pt + kP2ChunkTiles - 1) / kP2ChunkTiles;  // chunks
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_img, 1);
@@ -423,7 +448,7 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
     auto fetch = [&](int t) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int64_t j = tile_pixel<DIM>(g, tm, t_begin + t, q2 + u, xn[u], cn);
+        const int64_t j = tile_pixel<DIM>(g, tm, tile_of(t), q2 + u, xn[u], cn);
         lsn[u] = j >= 0 ? lse[j] : INFINITY;
         ubn[u] = j >= 0 ? ubar[j] : 0.f;
       }
@@ -444,8 +469,9 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
       if (q2 == 0) {
         fence_proxy_async();
         mbar_expect_tx(&bar_b_full[s], 2 * 128 * 4);
-        bulk_g2s(sOffP + s * 128, offg + (t_begin + t) * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
-        bulk_g2s(sUoffP + s * 128, uoffg + (t_begin + t) * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
+        const int64_t tc = tile_of(t);
+        bulk_g2s(sOffP + s * 128, offg + tc * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
+        bulk_g2s(sUoffP + s * 128, uoffg + tc * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
       }
       float ec[K], e0[K], e1[K];
       legendre_features<DIM, D>(cc, ec);
@@ -482,9 +508,13 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
   } else {
     const int quad = warp & 3, half = warp >> 2, lane = tid & 31;
     const int gr = quad * 32 + lane;
-    const int i = gb * 128 + gr;
+    const int i = gb * 128 + gr;  // row of the parameter image
+    const int gi = perm ? perm[i] : (i < N ? i : -1);  // its grain (-1: padding)
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     int n_done = 0;
+    // the CTA's partial of this grain (a row of part): the chunks added in
+    // order, in double
+    double* prow = gi >= 0 ? part + ((int64_t)blockIdx.x * N + gi) * K : nullptr;
     auto read_chunk = [&](int u) -> bool {
       const int db = u & 1;
       if (!mbar_wait_warp(&bar_d2_full[db], (uint32_t)((u >> 1) & 1), &abort_flag, status)) return false;
@@ -500,11 +530,12 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(&bar_d2_free[db]);
-      if (i < N) {
-        double* row = part + ((c_begin + u) * N + i) * K;
+      if (prow) {
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-          row[k] = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
+        for (int k = 0; k < K; ++k) {
+          const double v = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
+          prow[k] = u == 0 ? v : prow[k] + v;
+        }
       }
       n_done = u + 1;
       return true;
@@ -563,9 +594,8 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
     tmem_wait_ld();
     if (half == 0) {
       for (int u = n_done; ok && u < n_items; ++u) ok = read_chunk(u);
-      if (!ok && i < N) {
-        for (int u = n_done; u < n_items; ++u)
-          for (int k = 0; k < K; ++k) part[((c_begin + u) * N + i) * K + k] = NAN;
+      if (prow && (!ok || n_items == 0)) {
+        for (int k = 0; k < K; ++k) prow[k] = ok ? 0.0 : NAN;
       }
     }
   }
@@ -593,7 +623,8 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   // pass 1 keeps both images of ng grains resident; more grains run in
   // groups whose (max, S, T) are merged
   auto p1_bytes = [&](size_t ng) {
-    return 2 * ng * row_bytes + 2 * kTcPixTile * row_bytes + 4 * ng * 4 + 2 * kTcPixTile * 16 + 2 * kTcPixTile * 8;
+    return 2 * ng * row_bytes + 2 * kTcPixTile * row_bytes + 4 * ng * 4 + 2 * kTcPixTile * 16 + 2 * kTcPixTile * 8 +
+           4 * ng * 4;
   };
   int n_grp = 1, Ng = Npad;
   while (p1_bytes((size_t)Ng) > kCap && Ng > kH1Tile) {
@@ -616,8 +647,14 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t n_tiles = tm.n_tiles;
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
   const int gblocks = (N + 127) / 128;
-  const int64_t n_chunks = (n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles;
-  const int cpg = (int)std::min<int64_t>(n_chunks, std::max(1, sms / gblocks));
+  const int cpg = (int)std::min<int64_t>((n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles, std::max(1, sms / gblocks));
+  // as for the gradient: pass 2 visits the (tile, block) pairs whose c can
+  // survive in fp16, with the grains in the Morton order of their label
+  // centroids (PD_TC_NO_SKIP=1: every pair, index order)
+  const char* no_skip = getenv("PD_TC_NO_SKIP");
+  const bool skip = !(no_skip && no_skip[0] && no_skip[0] != '0');
+  const bool order = skip && Npad <= kOrderMax;
+  const int64_t n_words = (n_tiles + 31) / 32;
 
   Scratch sc(st);
   double* vsc = sc.get<double>(2);
@@ -630,10 +667,30 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   float* lse = sc.get<float>((size_t)P);
   float* ubar = sc.get<float>((size_t)P);
   float4* ms = n_grp > 1 ? sc.get<float4>((size_t)n_grp * P) : nullptr;
-  double* part = sc.get<double>((size_t)n_chunks * N * K);
+  double* part = sc.get<double>((size_t)cpg * N * K);  // one partial per pass-2 CTA and grain
+  uint32_t* need = skip ? sc.get<uint32_t>((size_t)gblocks * n_words) : nullptr;
+  int* kept = skip ? sc.get<int>((size_t)gblocks * n_tiles) : nullptr;
+  int* nkept = skip ? sc.get<int>((size_t)gblocks) : nullptr;
+  unsigned long long* lmom = order ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
+  int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
+  int* rank = order ? sc.get<int>((size_t)N) : nullptr;
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
+  if (need && cudaMemsetAsync(need, 0, sizeof(uint32_t) * (size_t)gblocks * n_words, st) != cudaSuccess)
+    return PD_ECUDA;
+  if (order) {
+    int bits = 0;
+    while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
+    const float fx = ldexpf(1.f, 62 - bits);
+    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+    const int64_t nthr = n_tiles * kTcPixTile;
+    PD_TIMED(st, "tc_label_moments",
+             (k_tc_label_moments<DIM, D><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
+                                                                                       lmom)));
+    PD_TIMED(st, "tc_grain_order",
+             k_tc_grain_order<DIM><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lmom, N, K, Npad, perm, rank));
+  }
 
   PD_TIMED(st, "tc_hvp_vscale", k_tc_vscale<<<1, 1024, 0, st>>>(c.v, (int64_t)N * K, vsc));
   {
@@ -641,14 +698,14 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.theta, N, Npad, K, KW, Arith<float>::theta_scale(c.eps),
-                                                          nullptr, nullptr, img, th32t));
+                                                          nullptr, perm, img, th32t));
     PD_TIMED(st, "tc_v_image",
-             k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.v, N, Npad, K, KW, 1.0, vsc + 1, nullptr, vimg, v32t));
+             k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.v, N, Npad, K, KW, 1.0, vsc + 1, perm, vimg, v32t));
   }
   const dim3 gridc((unsigned)((Npad + 255) / 256),
                    (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles, 4096));
-  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, nullptr, N, Npad, offg, TileBound{}, nullptr, nullptr)));
-  PD_TIMED(st, "tc_centre_u", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, v32t, nullptr, N, Npad, uoffg, TileBound{}, nullptr, nullptr)));
+  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, perm, N, Npad, offg, TileBound{}, nullptr, nullptr)));
+  PD_TIMED(st, "tc_centre_u", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, v32t, perm, N, Npad, uoffg, TileBound{}, nullptr, nullptr)));
 
   auto k1 = k_tc_hvp_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
@@ -657,20 +714,23 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_hvp_pass1" : "tc_bf16x3_hvp_pass1",
              k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, N, Npad, g0, ng, img, vimg, offg, uoffg, lse, ubar,
-                                                      ms ? ms + (size_t)q * P : nullptr, status));
+                                                      ms ? ms + (size_t)q * P : nullptr, need, n_words, status));
   }
   if (n_grp > 1)
     PD_TIMED(st, "tc_hvp_merge", k_tc_hvp_merge<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(ms, n_grp, P, lse, ubar));
+  if (skip)
+    PD_TIMED(st, "tc_kept_lists",
+             k_tc_kept_lists<<<(unsigned)gblocks, 1024, 0, st>>>(need, n_words, n_tiles, kept, nkept));
   auto k2 = k_tc_hvp_pass2<DIM, D, KS, NB, NA>;
   if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
     return PD_ECUDA;
   PD_TIMED(st, KS == 1 ? "tc_bf16_hvp_pass2" : "tc_bf16x3_hvp_pass2",
            (k2<<<dim3(cpg, gblocks), kP2Threads, smem2_req, st>>>(c.g, tm, N, Npad, img, vimg, offg, uoffg, lse, ubar,
-                                                                 n_chunks, part, status)));
+                                                                 kept, nkept, perm, part, status)));
   const int64_t NK = (int64_t)N * K;
   PD_TIMED(st, "reduce_parts",
            k_tc_reduce_grad<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
-               part, (int)n_chunks, NK, nullptr, 0.0, -1.0 / (c.eps * c.eps * (double)P), vsc, c.hv));
+               part, cpg, NK, nullptr, 0.0, -1.0 / (c.eps * c.eps * (double)P), vsc, c.hv));
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }
 

@@ -117,6 +117,17 @@ def test_tc_skip_structured(shape, N, d, eps, monkeypatch):
     phi_b, grad_b = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
     assert phi_b == phi
     np.testing.assert_array_equal(grad_b, grad)
+    # the Hessian-vector product skips the pairs whose c = p (u - ubar)
+    # fp16 rounds to zero, in the same grain order
+    v = synth.random_theta(44, N, th.shape[1], 2.0)
+    hv_o = O.hvp(g, lab, N, d, eps, th, v)
+    hv = pd.pd_hvp(pd.Grid(shape), dev(lab), N, dev(th), dev(v), d, eps, prec=pd.PD_BF16X3).cpu().numpy()
+    monkeypatch.setenv("PD_TC_NO_SKIP", "1")
+    hv_a = pd.pd_hvp(pd.Grid(shape), dev(lab), N, dev(th), dev(v), d, eps, prec=pd.PD_BF16X3).cpu().numpy()
+    monkeypatch.delenv("PD_TC_NO_SKIP")
+    print("skip %s N=%d: hvp %.2e vs oracle, %.2e vs all pairs" % (shape, N, rel(hv, hv_o), rel(hv, hv_a)))
+    assert rel(hv, hv_o) <= 1e-3, rel(hv, hv_o)
+    assert rel(hv, hv_a) <= 2e-5, rel(hv, hv_a)
 
 
 def test_tc_unsupported_shapes():
