@@ -67,7 +67,6 @@ namespace {
 // zero: it is not visited.
 constexpr int kP1Bufs = 4;
 constexpr int kP1Stages = 3;  // pixel-operand stages at most (two tiles in the epilogue, one being written)
-constexpr float kP1Far = 130.f;
 
 template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kP1Threads, 1)
@@ -784,36 +783,6 @@ k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float*
 }
 
 // ---------------------------------------------------------------------------
-// The 128-grain blocks pass 1 visits on each tile (bit q: image block q).
-// Reference: the label grain r of the tile's centre pixel, whose logit is
-// at least off_r - A_r everywhere in the tile, so that m(x) >= off_r - A_r;
-// block q, all of whose logits are at most mb[t][q], is left out when
-// mb[t][q] < off_r - A_r - kP1Far.  One thread per tile.
-// ---------------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(256)
-k_tc_tile_masks(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const int* __restrict__ rank,
-                const float* __restrict__ offg, int Npad, const float* __restrict__ amax,
-                const float* __restrict__ mb, unsigned long long* __restrict__ masks) {
-  using TS = TileShape<DIM>;
-  constexpr int kRef = TS::X / 2 + TS::X * (TS::Y / 2) + TS::X * TS::Y * (TS::Z / 2);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tm.n_tiles) return;
-  const int nblk = Npad / 128;
-  unsigned long long msk = nblk >= 64 ? ~0ull : ((1ull << nblk) - 1ull);
-  float x[DIM], c[DIM];
-  const int64_t j = tile_pixel<DIM>(g, tm, t, kRef, x, c);
-  const int G = j >= 0 ? labels[j] : -1;
-  if ((unsigned)G < (unsigned)N) {
-    const int r = rank ? rank[G] : G;
-    const float lim = offg[t * Npad + r] - amax[r] - kP1Far;
-    for (int q = 0; q < nblk && q < 64; ++q)
-      if (mb[t * nblk + q] < lim) msk &= ~(1ull << q);
-  }
-  masks[t] = msk;
-}
-
-// ---------------------------------------------------------------------------
 // Gradient and objective of the evaluation: per grain the label part (64-bit
 // fixed point) plus the pass-2 partials of its block's CTAs, in a fixed
 // order; block 0 also sums the objective partials.
@@ -960,20 +929,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   float* amax = bounds ? sc.get<float>((size_t)Npad) : nullptr;
   float* mbb = bounds ? sc.get<float>((size_t)n_tiles * (Npad / 128)) : nullptr;
   unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
-  TileBound tb{};
-  if (bounds) {
-    using TS = TileShape<DIM>;
-    const double h[3] = {(double)TS::X / (double)c.g.n0, (double)TS::Y / (double)c.g.n1,
-                         DIM == 3 ? (double)TS::Z / (double)c.g.n2 : 0.0};
-    for (int k = 0; k < K; ++k) {
-      double dk = 0.0;
-      for (int a = 0; a < DIM; ++a) {
-        const int e = basis_exp(DIM, D, k, a);
-        dk += 0.5 * e * (e + 1) * h[a];
-      }
-      tb.d[k] = (float)(dk * (1.0 + 1e-6));  // rounded up
-    }
-  }
+  const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;

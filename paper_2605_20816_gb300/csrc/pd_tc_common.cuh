@@ -698,9 +698,63 @@ k_tc_kept_lists(const uint32_t* __restrict__ need, int64_t n_words, int64_t n_ti
   if (threadIdx.x == 0) counts[gb] = base;
 }
 
+// A block of grains is left out of a log-sum-exp pass when every logit of
+// it lies more than kP1Far (log2 units) below the pixel's maximum: its
+// exponentials underflow to zero in ex2.approx.ftz.
+constexpr float kP1Far = 130.f;
+
+// ---------------------------------------------------------------------------
+// The 128-grain blocks pass 1 visits on each tile (bit q: image block q).
+// Reference: the label grain r of the tile's centre pixel, whose logit is
+// at least off_r - A_r everywhere in the tile, so that m(x) >= off_r - A_r;
+// block q, all of whose logits are at most mb[t][q], is left out when
+// mb[t][q] < off_r - A_r - kP1Far.  One thread per tile.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_tc_tile_masks(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const int* __restrict__ rank,
+                const float* __restrict__ offg, int Npad, const float* __restrict__ amax,
+                const float* __restrict__ mb, unsigned long long* __restrict__ masks) {
+  using TS = TileShape<DIM>;
+  constexpr int kRef = TS::X / 2 + TS::X * (TS::Y / 2) + TS::X * TS::Y * (TS::Z / 2);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tm.n_tiles) return;
+  const int nblk = Npad / 128;
+  unsigned long long msk = nblk >= 64 ? ~0ull : ((1ull << nblk) - 1ull);
+  float x[DIM], c[DIM];
+  const int64_t j = tile_pixel<DIM>(g, tm, t, kRef, x, c);
+  const int G = j >= 0 ? labels[j] : -1;
+  if ((unsigned)G < (unsigned)N) {
+    const int r = rank ? rank[G] : G;
+    const float lim = offg[t * Npad + r] - amax[r] - kP1Far;
+    for (int q = 0; q < nblk && q < 64; ++q)
+      if (mb[t * nblk + q] < lim) msk &= ~(1ull << q);
+  }
+  masks[t] = msk;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// D_k of k_tc_centre_logits for a structured grid: the largest offset of
+// a tile's pixel from its centre pixel is TileShape_a / n_a along axis a.
+template <int DIM, int D>
+TileBound tile_bound(const Geom& g) {
+  using TS = TileShape<DIM>;
+  const double h[3] = {(double)TS::X / (double)g.n0, (double)TS::Y / (double)g.n1,
+                       DIM == 3 ? (double)TS::Z / (double)g.n2 : 0.0};
+  TileBound tb{};
+  for (int k = 0; k < basis_K(DIM, D); ++k) {
+    double dk = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+      const int e = basis_exp(DIM, D, k, a);
+      dk += 0.5 * e * (e + 1) * h[a];
+    }
+    tb.d[k] = (float)(dk * (1.0 + 1e-6));  // rounded up
+  }
+  return tb;
+}
+
 template <int DIM>
 TileMap make_tiles(const Geom& g) {
   TileMap tm{1, 1, 1, 0, 1, 1, 1, 1.f, 1.f, 1.f};

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_t* __restrict__ img,
                const uint8_t* __restrict__ vimg, const float* __restrict__ offg, const float* __restrict__ uoffg,
                float* __restrict__ lse_out, float* __restrict__ ubar_out, float4* __restrict__ ms_out,
-               uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
+               const unsigned long long* __restrict__ masks, uint32_t* __restrict__ need_bits, int64_t n_words,
+               int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KW = (K + 15) / 16 * 16;
   constexpr int KT = KW * n_terms(KS);
@@ -77,9 +78,14 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
       bar_d_empty[kH1Bufs], bar_part_full[2], bar_part_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  __shared__ unsigned long long sMask[2];  // blocks visited on the stage's tile (bit q: image block q)
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n_gt = Ng / kH1Tile;
+  // the blocks of this launch visited on the tile of stage s: all, less
+  // those whose exponentials the centre-logit bounds show to underflow
+  const uint64_t all_q = n_gt >= 64 ? ~0ull : ((1ull << n_gt) - 1ull);
+  auto tile_mask = [&](int s) -> uint64_t { return masks ? (sMask[s] >> (g0 / 128)) & all_q : all_q; };
   const int64_t n_tiles = tm.n_tiles;
   if (tid == 0) {
     abort_flag = 0;
@@ -121,7 +127,8 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
         ok = mbar_wait(&bar_a_full[s], (it >> 1) & 1, &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
-        for (int gt = 0; gt < n_gt; ++gt, ++c) {
+        for (uint64_t msk = tile_mask(s); msk; msk &= msk - 1, ++c) {
+          const int gt = __ffsll((long long)msk) - 1;
           const int b = (int)(c % kH1Bufs);
           if (c >= kH1Bufs) {
             ok = mbar_wait(&bar_d_empty[b], (uint32_t)(((c / kH1Bufs) - 1) & 1), &abort_flag, status);
@@ -147,12 +154,17 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
     const int p0 = tid - kTcConsumers;
     int it = 0;
     bool ok = true;
+    // the tile's block mask, fetched a tile ahead (thread p0 == 0)
+    unsigned long long maskn = masks && p0 == 0 && blockIdx.x < n_tiles ? masks[blockIdx.x] : 0ull;
     for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
       const int s = it & 1, use = it >> 1;
+      const unsigned long long maskc = maskn;
+      if (masks && p0 == 0 && t + gridDim.x < n_tiles) maskn = masks[t + gridDim.x];
       if (use >= 1 && (!mbar_wait_warp(&bar_a_empty[s], (uint32_t)((use - 1) & 1), &abort_flag, status) ||
                        !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)))
         break;
       if (p0 == 0) {
+        sMask[s] = maskc;
         fence_proxy_async();
         mbar_expect_tx(&bar_a_full[s], (uint32_t)Ng * 8);
         bulk_g2s(sOff + s * Ng, offg + t * Npad + g0, (uint32_t)Ng * 4, &bar_a_full[s]);
@@ -211,7 +223,9 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
       ok = mbar_wait_warp(&bar_a_full[s], (uint32_t)((it >> 1) & 1), &abort_flag, status);
       if (!ok) break;
       float m = -INFINITY, S = 0.f, T = 0.f;
-      for (int gt = 0; gt < n_gt; ++gt, ++c) {
+      const uint64_t msk0 = tile_mask(s);
+      for (uint64_t msk = msk0; msk; msk &= msk - 1, ++c) {
+        const int gt = __ffsll((long long)msk) - 1;
         const int b = (int)(c % kH1Bufs);
         ok = mbar_wait_warp(&bar_d_full[b], (uint32_t)((c / kH1Bufs) & 1), &abort_flag, status);
         if (!ok) break;
@@ -273,7 +287,7 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
           // rounds to zero in fp16
           for (int q = 0; q < n_gt; ++q) {
             const float bmq = fmaxf(sBm[((s * n_gt + q) * 2) * 128 + row], sBm[((s * n_gt + q) * 2 + 1) * 128 + row]);
-            const bool nd = j >= 0 && !(bmq < lse - 32.f);
+            const bool nd = ((msk0 >> q) & 1) && j >= 0 && !(bmq < lse - 32.f);
             const uint32_t bal = __ballot_sync(0xffffffffu, nd);
             if (lane == 0 && bal)
               atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
@@ -654,6 +668,9 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   const char* no_skip = getenv("PD_TC_NO_SKIP");
   const bool skip = !(no_skip && no_skip[0] && no_skip[0] != '0');
   const bool order = skip && Npad <= kOrderMax;
+  // pass 1 leaves out the blocks that the centre-logit bounds place far
+  // below the tile's reference logit (structured grids)
+  const bool bounds = skip && !c.g.coords && Npad / 128 <= 64;
   const int64_t n_words = (n_tiles + 31) / 32;
 
   Scratch sc(st);
@@ -674,6 +691,10 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   unsigned long long* lmom = order ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
   int* rank = order ? sc.get<int>((size_t)N) : nullptr;
+  float* amax = bounds ? sc.get<float>((size_t)Npad) : nullptr;
+  float* mbb = bounds ? sc.get<float>((size_t)n_tiles * gblocks) : nullptr;
+  unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
+  const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
@@ -704,8 +725,12 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   }
   const dim3 gridc((unsigned)((Npad + 255) / 256),
                    (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles, 4096));
-  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, perm, N, Npad, offg, TileBound{}, nullptr, nullptr)));
+  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, perm, N, Npad, offg, tb, amax, mbb)));
   PD_TIMED(st, "tc_centre_u", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, v32t, perm, N, Npad, uoffg, TileBound{}, nullptr, nullptr)));
+  if (bounds)
+    PD_TIMED(st, "tc_tile_masks",
+             k_tc_tile_masks<DIM><<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, rank, offg,
+                                                                                   Npad, amax, mbb, masks));
 
   auto k1 = k_tc_hvp_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
@@ -714,7 +739,7 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_hvp_pass1" : "tc_bf16x3_hvp_pass1",
              k1<<<grid1, kTcThreads, smem1_req, st>>>(c.g, tm, N, Npad, g0, ng, img, vimg, offg, uoffg, lse, ubar,
-                                                      ms ? ms + (size_t)q * P : nullptr, need, n_words, status));
+                                                      ms ? ms + (size_t)q * P : nullptr, masks, need, n_words, status));
   }
   if (n_grp > 1)
     PD_TIMED(st, "tc_hvp_merge", k_tc_hvp_merge<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(ms, n_grp, P, lse, ubar));
