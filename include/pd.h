@@ -216,7 +216,10 @@ typedef struct pd_fit_opts {
 
 typedef struct pd_fit_report {
   double phi;         /* final Phi (evaluated in FP64)                     */
-  double gnorm;       /* final ||grad Phi||_2 over the free blocks         */
+  double gnorm;       /* final ||grad Phi||_2 over the free blocks (from
+                         the last evaluation with a gradient: a target met in
+                         reduced precision is confirmed by the FP64 objective
+                         alone)                                              */
   double err;         /* final Err^G (Sec. 4)                              */
   int iters;          /* iterations of both phases                         */
   int iters_phase1;   /* iterations of the first phase                     */

@@ -377,12 +377,20 @@ int fit_run(Evaluator& ev, const Vec& th, int N, int K, const pd_fit_opts& o, Fi
   if (rc) return rc;
   int status = r1.status;
   // a target reached in reduced precision counts only once the FP64
-  // objective confirms it; otherwise the FP64 refinement continues
+  // objective confirms it (the objective alone: no gradient pass); otherwise
+  // the FP64 refinement continues from a full FP64 evaluation
   if (o.refine_iter > 0 && status == 3 && prec != PD_FP64) {
-    prec = PD_FP64;
-    rc = ev.eval(cur.x, prec, &cur.f, &cur.g);
+    double f64 = 0.0;
+    rc = ev.eval(cur.x, PD_FP64, &f64, nullptr);
     if (rc) return rc;
-    if (!(-cur.f >= target)) status = 0;
+    prec = PD_FP64;
+    if (-f64 >= target) {
+      cur.f = f64;  // the gradient stays that of the reduced-precision phase
+    } else {
+      status = 0;
+      rc = ev.eval(cur.x, prec, &cur.f, &cur.g);
+      if (rc) return rc;
+    }
   }
   if (o.refine_iter > 0 && status != 3) {
     if (prec != PD_FP64) {
