@@ -15,8 +15,9 @@
 //       threads from the in-register Legendre recurrence;
 //   B = all grains' scaled parameters -theta*log2(e)/eps (rows) x K, copied
 //       once per CTA from a prepared global image by a bulk (TMA) copy;
-//   D = A B^T, 128 pixels x 256 grains per MMA group, double-buffered in
-//       TMEM; the epilogue warps read their pixel row of logits and keep an
+//   D = A B^T, 128 pixels x 128 grains per MMA group, for the blocks of
+//       grains that the tile's mask keeps (k_tc_tile_masks); an epilogue
+//       warpgroup owns a tile, reads its pixel rows of logits and keeps an
 //       online log-sum-exp; out: log2 S(x) per pixel and per-CTA objective
 //       partials, and one bit per (tile, 128-grain block): whether any
 //       probability of the block on the tile reaches 2^-26.
@@ -60,8 +61,8 @@ namespace {
 // Pass 1 takes the grains of a tile in blocks of 128 (one MMA of N = 128
 // per block and product); the two epilogue warpgroups take alternate
 // tiles, each all blocks of its tile (so that a pixel's log-sum-exp needs
-// no exchange), through its own two 128-column TMEM buffers.  A block whose logits
-// are all more than 130 below the logit of the label grain of the tile's
+// no exchange), through its own two 128-column TMEM buffers.  A block
+// whose logits are all more than 130 below the logit of the label grain of the tile's
 // centre pixel, everywhere in the tile (a bound from the centre logits,
 // see k_tc_centre_logits), would only add exponentials that underflow to
 // zero: it is not visited.
