@@ -73,11 +73,19 @@ extern "C" {
                       on the tensor cores                                     */
 /* The tensor-core precisions serve the objective, the gradient and the
  * Hessian-vector product for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid
- * sides <= 2^23; other combinations return PD_ENOTSUP.  The log-sum-exp pass keeps the grains'
- * parameters resident in one SM's shared memory (about 104 bytes a grain
- * at K <= 16 in PD_BF16X3, up to 1792 grains); more grains are processed
- * in groups whose partial sums are merged, with a scratch buffer of
- * 8 bytes per pixel and group.                                          */
+ * sides <= 2^23; other combinations return PD_ENOTSUP.  The log-sum-exp
+ * pass keeps the grains' parameters resident in one SM's shared memory
+ * (about 120 bytes a grain at K <= 16 in PD_BF16X3, up to about 1500
+ * grains); more grains are processed in groups whose partial sums are
+ * merged, with a scratch buffer of 8 bytes per pixel and group.  Besides
+ * log S per pixel, the scratch holds one float per (128-pixel tile,
+ * grain) of centre logits (4 N / 128 bytes per pixel).  Internally the
+ * grains are reordered by the Morton code of their label centroids and
+ * the passes leave out the (tile, grain block) pairs whose contributions
+ * round to zero (underflowing exponentials; probabilities below 2^-26,
+ * 2^-32 for the HVP, which the fp16 gradient operand rounds to zero);
+ * results are in the caller's grain order.  Setting PD_TC_NO_SKIP=1 in
+ * the environment visits every pair in the caller's order.             */
 
 /* ---- supported sizes --------------------------------------------------- */
 #define PD_MAX_DEGREE_2D 7
