@@ -75,7 +75,7 @@ extern "C" {
  * Hessian-vector product for K <= 32 (2-D d <= 6, 3-D d <= 3) and grid
  * sides <= 2^23; other combinations return PD_ENOTSUP.  The log-sum-exp
  * pass keeps the grains' parameters resident in one SM's shared memory
- * (about 120 bytes a grain at K <= 16 in PD_BF16X3, up to about 1500
+ * (about 112 bytes a grain at K <= 16 in PD_BF16X3, up to 1536
  * grains); more grains are processed in groups whose partial sums are
  * merged, with a scratch buffer of 8 bytes per pixel and group.  Besides
  * log S per pixel, the scratch holds one float per (128-pixel tile,
