@@ -145,9 +145,10 @@ def test_tc_unsupported_shapes():
 
 @pytest.mark.parametrize("N,d", [(1792, 4), (1793, 4), (2300, 4), (1000, 6)])
 def test_tc_grain_groups(N, d):
-    # K = 15 in bf16x3: 1792 grains is the largest parameter image one SM
-    # holds; beyond it (and at K = 28 from about 700 grains) pass 1 runs in
-    # groups of grains whose log-sum-exp parts are merged
+    # K = 15 in bf16x3: 1536 grains is the largest parameter image one SM
+    # holds beside the pass's stages; beyond it (and at K = 28 from a few
+    # hundred grains) pass 1 runs in groups of grains whose log-sum-exp
+    # parts are merged
     shape, eps = (64, 48), 2e-2
     g = O.Grid(shape)
     K = O.K(2, d)
