@@ -453,10 +453,64 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   }
 }
 
+// The gradient pass's CTAs per grain block, in proportion to the blocks'
+// kept-tile counts: one to every block with kept tiles, the rest by the
+// floor of the proportional share, the leftover one each to the first
+// blocks with kept tiles.  p2_share gives CTA r its block, its index among
+// the block's CTAs and their number; every caller computes the same split.
+struct P2Share {
+  int gb, idx, n;
+};
+// Walks the blocks in order with their first CTA and CTA count; stops when
+// stop(b, first, count) returns true.  O(nb).
+template <typename F>
+__device__ __forceinline__ void p2_walk(const int* counts, int64_t n_tiles, int nb, int n_cta, F stop) {
+  long long U = 0;
+  int base = 0;
+  for (int b = 0; b < nb; ++b) {
+    const long long c = counts ? counts[b] : n_tiles;
+    U += c;
+    base += c > 0;
+  }
+  if (U == 0) return;
+  const long long R = n_cta - base;
+  long long floors = 0;
+  for (int b = 0; b < nb; ++b) {
+    const long long c = counts ? counts[b] : n_tiles;
+    if (c > 0) floors += R * c / U;
+  }
+  long long left = R - floors;
+  int pre = 0;
+  for (int b = 0; b < nb; ++b) {
+    const long long c = counts ? counts[b] : n_tiles;
+    int a = 0;
+    if (c > 0) {
+      a = 1 + (int)(R * c / U);
+      if (left > 0) {
+        ++a;
+        --left;
+      }
+    }
+    if (stop(b, pre, a)) return;
+    pre += a;
+  }
+}
+__device__ __forceinline__ P2Share p2_share(const int* counts, int64_t n_tiles, int nb, int n_cta, int r) {
+  P2Share sh{0, 0, 0};
+  p2_walk(counts, n_tiles, nb, n_cta, [&](int b, int first, int a) {
+    if (r < first + a) {
+      sh = P2Share{b, r - first, a};
+      return true;
+    }
+    return false;
+  });
+  return sh;
+}
+
 template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2ThreadsG, 1)
 k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
-           const float* __restrict__ lse, const int* __restrict__ kept, const int* __restrict__ n_kept_gb,
+           const float* __restrict__ lse, const int* __restrict__ kept, const int* __restrict__ n_kept_gb, int nb,
            const int* __restrict__ perm, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
   constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
@@ -478,13 +532,14 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int gb = blockIdx.y;  // grain block
-  // this CTA's share of the tiles on which the grain block has a
+  // this CTA's grain block and share of the tiles on which the block has a
   // non-negligible probability (all tiles without the lists), in tile
-  // order; chunks of kP2ChunkTiles of them give one gradient partial each
-  const int64_t n_list = kept ? (int64_t)n_kept_gb[gb] : tm.n_tiles;
-  const int64_t k_lo = n_list * blockIdx.x / gridDim.x;
-  const int n_kept = (int)(n_list * (blockIdx.x + 1) / gridDim.x - k_lo);
+  // order; chunks of kP2ChunkTiles of them add up to one gradient partial
+  const P2Share sh = p2_share(kept ? n_kept_gb : nullptr, tm.n_tiles, nb, gridDim.x, blockIdx.x);
+  const int gb = sh.gb;  // grain block
+  const int64_t n_list = sh.n > 0 ? (kept ? (int64_t)n_kept_gb[gb] : tm.n_tiles) : 0;
+  const int64_t k_lo = sh.n > 0 ? n_list * sh.idx / sh.n : 0;
+  const int n_kept = sh.n > 0 ? (int)(n_list * (sh.idx + 1) / sh.n - k_lo) : 0;
   const int* klist = kept ? kept + (int64_t)gb * tm.n_tiles + k_lo : nullptr;
   auto tile_of = [&](int t) -> int64_t { return klist ? (int64_t)klist[t] : k_lo + t; };
   const int n_used = (n_kept + kP2ChunkTiles - 1) / kP2ChunkTiles;  // chunks
@@ -786,12 +841,14 @@ k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float*
 // ---------------------------------------------------------------------------
 // Gradient and objective of the evaluation: per grain the label part (64-bit
 // fixed point) plus the pass-2 partials of its block's CTAs, in a fixed
-// order; block 0 also sums the objective partials.
+// order; block 0 also sums the objective partials.  (The other CTAs' rows
+// of the grain are never written.)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_tc_reduce_eval(const double* __restrict__ part, int cpg, int64_t NK, const unsigned long long* __restrict__ base,
-                 double inv_fx, double scale, double* __restrict__ grad, const double* __restrict__ objp, int n_obj,
-                 double obj_scale, double* __restrict__ obj) {
+k_tc_reduce_eval(const double* __restrict__ part, int n_cta, const int* __restrict__ n_kept_gb, int nb,
+                 const int* __restrict__ rank, int64_t n_tiles, int K, int64_t NK,
+                 const unsigned long long* __restrict__ base, double inv_fx, double scale, double* __restrict__ grad,
+                 const double* __restrict__ objp, int n_obj, double obj_scale, double* __restrict__ obj) {
   __shared__ double ssum[8][32];
   if (obj && blockIdx.x == 0) {
     if (threadIdx.y == 0) {
@@ -805,8 +862,20 @@ k_tc_reduce_eval(const double* __restrict__ part, int cpg, int64_t NK, const uns
   if (!grad) return;
   const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
   double s = 0.0;
-  if (q < NK)
-    for (int r = threadIdx.y; r < cpg; r += 8) s += part[(int64_t)r * NK + q];
+  if (q < NK) {
+    // the CTAs of this grain's block, [r0, r0 + n), as the gradient pass
+    // gave them out
+    const int gi = (int)(q / K);
+    const int gb = (rank ? rank[gi] : gi) / 128;
+    int r0 = 0, n = 0;
+    p2_walk(n_kept_gb, n_tiles, nb, n_cta, [&](int b, int first, int a) {
+      if (b != gb) return false;
+      r0 = first;
+      n = a;
+      return true;
+    });
+    for (int r = r0 + threadIdx.y; r < r0 + n; r += 8) s += part[(int64_t)r * NK + q];
+  }
   ssum[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.y == 0 && q < NK) {
@@ -892,9 +961,11 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
   const int gridm = (int)((P + 255) / 256);  // merge blocks of a grain-split pass 1
   const int gblocks = (N + 127) / 128;  // pass-2 grain blocks
-  // pass 2: one wave of CTAs per grain block, each with a contiguous share
-  // of the block's tiles and one gradient partial per grain
-  const int cpg = (int)std::min<int64_t>((n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles, std::max(1, sms / gblocks));
+  // pass 2: one wave of CTAs, at least one per grain block, the blocks
+  // sharing the SMs in proportion to their kept tiles (p2_share); a CTA
+  // takes a contiguous share of its block's tiles and writes one gradient
+  // partial per grain of the block
+  const int n_cta2 = std::max(sms, gblocks);
   // The gradient pass visits only the (tile, block) pairs with a
   // probability that survives in its fp16 operand (judged against a lower
   // bound of log2 S when pass 1 runs in grain groups), and the grains are
@@ -917,7 +988,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
-  double* part = c.grad ? sc.get<double>((size_t)cpg * N * K) : nullptr;  // one partial per pass-2 CTA and grain
+  double* part = c.grad ? sc.get<double>((size_t)n_cta2 * N * K) : nullptr;  // one partial per pass-2 CTA and grain
   unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
   // one bit per (128-grain block, tile): the block has a probability that
   // the gradient pass cannot neglect on the tile; then the tiles per block
@@ -990,19 +1061,19 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     auto k2 = k_tc_pass2<DIM, D, KS, NB, NA>;
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
-    dim3 grid2(cpg, gblocks);
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<grid2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, perm, part,
-                                                       status));
+             k2<<<n_cta2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, gblocks, perm,
+                                                        part, status));
     if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   }
   if (c.obj || c.grad) {
     const int64_t NK = (int64_t)N * K;
     const unsigned blocks = c.grad ? (unsigned)((NK + 31) / 32) : 1u;
     PD_TIMED(st, "reduce_eval",
-             k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(part, cpg, NK, lmom, 1.0 / (double)fx,
-                                                              -1.0 / (c.eps * (double)P), c.grad, objp,
-                                                              n_grp > 1 ? gridm : grid1, 1.0 / (double)P, c.obj));
+             k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(
+                 part, n_cta2, kept ? nkept : nullptr, gblocks, perm ? rank : nullptr, n_tiles, K, NK, lmom,
+                 1.0 / (double)fx, -1.0 / (c.eps * (double)P), c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P,
+                 c.obj));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
 }
