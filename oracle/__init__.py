@@ -19,8 +19,9 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
   assign .................... brute-force numpy argmin, constructed ties
   mono_to_legendre .......... numpy poly2leg
   theta_from_apd ............ direct power-distance argmin, round trips
-  heuristic_theta ........... parity unpinned beyond round trips and the
-                              printed formulas (no value in the paper)
+  heuristic_theta ........... printed formulas against numpy; its diagram
+                              against numpy's (anisotropic) power diagram
+                              of those parameters (d = 1, 2, 4)
   lbfgs_fit, newton_cg_fit .. scipy L-BFGS-B optimum on non-separable data,
                               recovery certificate (Cor. 4.10)
 """

@@ -209,3 +209,34 @@ def test_nested_degrees(oracle):
     assert abs(phi_pad - r1.phi) < 1e-13
     th2, r2, _ = oracle.lbfgs_fit(g, lab, N, 2, eps, pad, 300, gtol=1e-10)
     assert r2.phi >= r1.phi - 1e-14
+
+
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_heuristic_theta_diagram(oracle, d):
+    # the heuristic's parameters (Sec. 5.5.2), computed here from their
+    # printed formulas in numpy, define a (d = 1: isotropic, d >= 2:
+    # anisotropic) power diagram; heuristic_theta must rasterise to exactly
+    # that diagram, whatever the degree its higher terms are padded to
+    shape, N = (36, 30), 7
+    y0, w0 = synth.power_params(11, N)
+    g = oracle.Grid(shape)
+    lab, _ = oracle.assign(g, N, 1, oracle.theta_from_apd(2, 1, y0, w0))
+    lab, N, _ = synth.compact(lab)
+    X = centres_2d(shape)
+    ys, ws, As = [], [], []
+    for i in range(N):
+        Xi = X[lab == i]
+        y = Xi.mean(0)
+        A = np.linalg.inv(np.cov(Xi.T, bias=True)) if d >= 2 else np.eye(2)
+        ys.append(y)
+        As.append(A)
+        ws.append(math.sqrt(np.linalg.det(A)) * len(Xi) / (g.P * math.pi))
+    ys, ws, As = np.array(ys), np.array(ws), np.array(As)
+    D = X[:, None, :] - ys[None]
+    cost = np.einsum("pna,nab,pnb->pn", D, As, D) - ws[None]
+    th = oracle.heuristic_theta(g, lab, N, d)
+    assert th.shape == (N, oracle.K(2, d))
+    got, gap = oracle.assign(g, N, d, th)
+    sure = gap > 1e-9
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(got[sure], np.argmin(cost, 1)[sure])
