@@ -381,17 +381,23 @@ int pd_microbench(int kind, double* ops_per_s, void* stream);
  * is a deployment variant of the objective/gradient call above.
  *
  * Arguments, results and precisions are those of pd_objective_grad, limited
- * to 2-D pixel sets (PD_ENOTSUP otherwise) and PD_FP64 / PD_FP32.  A problem
- * whose scratch (about P * 4 bytes in FP32, P * 8 in FP64, plus at least one
- * N*K*8-byte gradient partial) does not fit returns PD_ESCRATCH before
- * anything is enqueued.  Results equal pd_objective_grad's up to the order
- * of the fixed cross-chunk sum (fewer chunks when scratch is tight).
+ * to 2-D pixel sets (PD_ENOTSUP otherwise) and PD_FP64 / PD_FP32 (another
+ * valid precision: PD_ENOTSUP; an invalid one: PD_EINVAL).  A problem whose
+ * scratch does not fit returns PD_ESCRATCH before anything is enqueued: in
+ * FP32 about P * (4 + K/16) bytes (log S, and per 128-pixel tile its centre
+ * features and reference logit), in FP64 P * 8, plus the scaled parameters
+ * and at least one N*K*8-byte gradient partial.  Results equal
+ * pd_objective_grad's up to the order of the fixed cross-chunk sum (fewer
+ * chunks when scratch is tight).
  *
  * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (on different streams, or from several host threads)
- * race on it and must be serialised by the caller. */
+ * device (cudaGetSymbolAddress, with that device current) and keeps it;
+ * make that first call before any stream capture.  pd_release forgets the
+ * address of the current device: call it after a reset of the device
+ * (cudaDeviceReset), which reloads the library's module, before the next
+ * call.  All calls share the one array: calls that overlap on the GPU (on
+ * different streams, or from several host threads) race on it and must be
+ * serialised by the caller. */
 #define PD_NOALLOC_SCRATCH_BYTES (32u << 20)
 int pd_objective_grad_noalloc(const pd_grid* grid, const int32_t* labels,
                               int N, const double* theta,
@@ -407,8 +413,9 @@ int pd_objective_grad_noalloc(const pd_grid* grid, const int32_t* labels,
 int pd_selftest_wait_timeout(double seconds, int* status_out, void* stream);
 
 /* Release cached library state on the current device (memory pool
- * reservations are trimmed).  Safe to call at any time when no call of
- * this library is in flight. */
+ * reservations are trimmed, the cached device address of the allocation-
+ * free entry point's array is forgotten).  Safe to call at any time when no
+ * call of this library is in flight. */
 void pd_release(void);
 
 #ifdef __cplusplus

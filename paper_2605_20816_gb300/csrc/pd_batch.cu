@@ -4,7 +4,10 @@
 // ascent scheme built on it (pd_fit_batched).
 //
 // Work items: pass 1 = (map, 512-pixel block), pass 2 = (map, pixel chunk,
-// 128-grain tile).  A CTA takes items from a global counter until none are
+// 128-grain tile); in FP32 the pixels are the tiles of the single-map FP32
+// evaluation (pd_tiles.cuh): pass 1 = (map, block of four tiles), pass 2 =
+// (map, run of tiles, 128-grain tile), with each map's centre features and
+// reference logits formed first.  A CTA takes items from a global counter until none are
 // left, heaviest maps first (items are listed in decreasing N), and runs
 // for each item exactly the per-block code of the single-map kernels, so a
 // map's partial sums are those of a single-map call with the same chunking
@@ -30,15 +33,19 @@ namespace {
 
 struct BatchMapDev {
   Geom g;
+  TileMap tm;        // FP32: the map's tiles
   const int32_t* labels;
   const double* theta;
-  void* thS;
+  void* thS;         // scaled parameters (FP32: the hi parts)
+  float* thL;        // FP32: the lo parts
+  float2* ec;        // FP32: centre features [tiles][K]
+  float2* ref;       // FP32: reference logits [tiles]
   void* lse;
   double* objp;
   double* part;
   double* obj_out;
   double* grad_out;
-  int64_t ppc;
+  int64_t ppc;       // pixels (FP64) or tiles (FP32) per pass-2 chunk
   int N, nch, blocks1, pad;
 };
 
@@ -52,8 +59,50 @@ __global__ void k_batch_scale(const BatchMapDev* __restrict__ maps, int K, int K
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)mp.N * KP;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(q / KP), k = (int)(q % KP);
-    out[q] = k < K ? (T)(mp.theta[(int64_t)i * K + k] * scale) : (T)0;
+    const double v = k < K ? mp.theta[(int64_t)i * K + k] * scale : 0.0;
+    out[q] = (T)v;
+    if (mp.thL) mp.thL[q] = (float)(v - (double)(T)v);
   }
+}
+
+// FP32: centre features of every map's tiles (they depend on the pixel set
+// only: formed once when the plan is built).
+template <int D>
+__global__ void __launch_bounds__(256) k_batch_features(const BatchMapDev* __restrict__ maps) {
+  const BatchMapDev& mp = maps[blockIdx.y];
+  constexpr int K = basis_K(2, D);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < mp.tm.n_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double c[2], P[2][D + 1];
+    tile_centre<2>(mp.g, mp.tm, t, c);
+    for (int a = 0; a < 2; ++a) {
+      P[a][0] = 1.0;
+      P[a][1] = c[a];
+      for (int m = 1; m < D; ++m) P[a][m + 1] = ((2.0 * m + 1.0) * c[a] * P[a][m] - (double)m * P[a][m - 1]) * (1.0 / (m + 1.0));
+    }
+    double eta[K];
+    basis_all<2, D>(P, eta, std::make_integer_sequence<int, K>{});
+    for (int k = 0; k < K; ++k) {
+      const float h = (float)eta[k];
+      mp.ec[t * K + k] = make_float2(h, (float)(eta[k] - (double)h));
+    }
+  }
+}
+
+// FP32: reference logits of every map's tiles (blockIdx.y = map; blocks walk
+// the map's groups of kRefTiles tiles).
+template <int D>
+__global__ void __launch_bounds__(kRefThreads)
+k_batch_refs(const BatchMapDev* __restrict__ maps, const int* __restrict__ active) {
+  constexpr int K = basis_K(2, D);
+  __shared__ float2 sec[kRefTiles][K];
+  __shared__ __align__(16) float sech[kRefTiles][padded_K<float>(K)];
+  __shared__ uint32_t smax[kRefTiles];
+  const int m = blockIdx.y;
+  if (!active[m]) return;
+  const BatchMapDev& mp = maps[m];
+  for (int64_t t0 = (int64_t)blockIdx.x * kRefTiles; t0 < mp.tm.n_tiles; t0 += (int64_t)gridDim.x * kRefTiles)
+    tile_centres_block<K>(static_cast<const float*>(mp.thS), mp.N, mp.tm.n_tiles, mp.ec, mp.ref, t0, sec, sech, smax);
 }
 
 __device__ __forceinline__ int next_item(int* counter) {
@@ -74,8 +123,12 @@ k_batch_pass1(const BatchMapDev* __restrict__ maps, const int2* __restrict__ ite
     const int2 w = items[it];
     if (!active[w.x]) continue;
     const BatchMapDev& mp = maps[w.x];
-    pass1_block<T, 2, D, 2, false>(mp.g, mp.labels, mp.N, static_cast<const T*>(mp.thS), nullptr,
-                                   static_cast<T*>(mp.lse), nullptr, mp.objp + w.y, w.y);
+    if constexpr (std::is_same<T, float>::value)
+      pass1_tiles_block<2, D, false>(mp.g, mp.tm, mp.labels, mp.N, static_cast<const float*>(mp.thS), mp.thL,
+                                     nullptr, mp.ec, mp.ref, static_cast<float*>(mp.lse), nullptr, mp.objp + w.y, w.y);
+    else
+      pass1_block<T, 2, D, 2, false>(mp.g, mp.labels, mp.N, static_cast<const T*>(mp.thS), nullptr,
+                                     static_cast<T*>(mp.lse), nullptr, mp.objp + w.y, w.y);
   }
 }
 
@@ -91,9 +144,14 @@ k_batch_pass2(const BatchMapDev* __restrict__ maps, const int2* __restrict__ ite
     const BatchMapDev& mp = maps[w.x];
     if (!mp.grad_out) continue;
     const int gtiles = (mp.N + kGradThreads - 1) / kGradThreads;
-    pass2_block<T, 2, D, false>(mp.g, mp.labels, mp.N, static_cast<const T*>(mp.thS), nullptr,
-                                static_cast<const T*>(mp.lse), nullptr, mp.ppc, mp.part, w.y / gtiles,
-                                w.y % gtiles);
+    if constexpr (std::is_same<T, float>::value)
+      pass2_tiles_block<2, D, false>(mp.g, mp.tm, mp.labels, mp.N, static_cast<const float*>(mp.thS), mp.thL,
+                                     nullptr, mp.ec, mp.ref, static_cast<const float*>(mp.lse), nullptr, mp.ppc,
+                                     mp.part, w.y / gtiles, w.y % gtiles);
+    else
+      pass2_block<T, 2, D, false>(mp.g, mp.labels, mp.N, static_cast<const T*>(mp.thS), nullptr,
+                                  static_cast<const T*>(mp.lse), nullptr, mp.ppc, mp.part, w.y / gtiles,
+                                  w.y % gtiles);
   }
 }
 
@@ -184,6 +242,12 @@ void launch_batch(pd_batch* b, cudaStream_t st) {
   cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), st);
   k_batch_scale<T><<<dim3((maxNKP + 255) / 256, b->n_maps), 256, 0, st>>>(b->d_maps, b->K, b->KP, scale,
                                                                           b->d_active);
+  if (std::is_same<T, float>::value) {
+    int64_t max_tiles = 1;
+    for (const auto& m : b->hmaps) max_tiles = std::max<int64_t>(max_tiles, m.tm.n_tiles);
+    const unsigned gx = std::min<unsigned>(tile_centre_blocks(max_tiles), 1024u);
+    k_batch_refs<D><<<dim3(gx, b->n_maps), kRefThreads, 0, st>>>(b->d_maps, b->d_active);
+  }
   k_batch_pass1<T, D><<<b->grid1, kLseThreads, 0, st>>>(b->d_maps, b->d_items1, b->n_items1, b->d_counters,
                                                          b->d_active);
   k_batch_pass2<T, D><<<b->grid2, kGradThreads, 0, st>>>(b->d_maps, b->d_items2, b->n_items2, b->d_counters + 1,
@@ -256,6 +320,7 @@ int build_plan(pd_batch* b, const Tune& tu) {
     return o;
   };
   std::vector<size_t> o_th(b->n_maps), o_lse(b->n_maps), o_objp(b->n_maps), o_part(b->n_maps);
+  std::vector<size_t> o_thl(b->n_maps, 0), o_ec(b->n_maps, 0), o_ref(b->n_maps, 0);
   b->hmaps.assign(b->n_maps, BatchMapDev{});
   std::vector<int2> items1, items2;
   for (int m = 0; m < b->n_maps; ++m) {
@@ -268,13 +333,24 @@ int build_plan(pd_batch* b, const Tune& tu) {
     h.grad_out = mp.grad_out;
     h.N = mp.N;
     const int64_t P = h.g.P;
-    h.blocks1 = (int)((P + kLseThreads * 2 - 1) / (kLseThreads * 2));
     const int gtiles = (mp.N + kGradThreads - 1) / kGradThreads;
-    const int64_t tiles = (P + kPixTile - 1) / kPixTile;
-    int64_t want = ((int64_t)sms * tu.chunk_factor + gtiles - 1) / gtiles;
-    want = std::max<int64_t>(1, std::min<int64_t>(want, tiles));
-    h.ppc = ((tiles + want - 1) / want) * kPixTile;
-    h.nch = (int)((P + h.ppc - 1) / h.ppc);
+    const bool f32 = b->prec == PD_FP32;
+    if (f32) {
+      h.tm = make_tiles<2>(h.g);
+      h.blocks1 = (int)((h.tm.n_tiles + kT1Tiles - 1) / kT1Tiles);
+      h.ppc = tiles_per_chunk(h.tm.n_tiles, gtiles, sms, tu.chunk_factor);
+      h.nch = (int)((h.tm.n_tiles + h.ppc - 1) / h.ppc);
+      o_thl[m] = take(4 * (size_t)mp.N * b->KP);
+      o_ec[m] = take(sizeof(float2) * (size_t)h.tm.n_tiles * b->K);
+      o_ref[m] = take(sizeof(float2) * (size_t)h.tm.n_tiles);
+    } else {
+      h.blocks1 = (int)((P + kLseThreads * 2 - 1) / (kLseThreads * 2));
+      const int64_t tiles = (P + kPixTile - 1) / kPixTile;
+      int64_t want = ((int64_t)sms * tu.chunk_factor + gtiles - 1) / gtiles;
+      want = std::max<int64_t>(1, std::min<int64_t>(want, tiles));
+      h.ppc = ((tiles + want - 1) / want) * kPixTile;
+      h.nch = (int)((P + h.ppc - 1) / h.ppc);
+    }
     o_th[m] = take(esz * (size_t)mp.N * b->KP);
     o_lse[m] = take(esz * (size_t)P);
     o_objp[m] = take(8 * (size_t)h.blocks1);
@@ -297,6 +373,11 @@ int build_plan(pd_batch* b, const Tune& tu) {
     BatchMapDev& h = b->hmaps[m];
     h.thS = base + o_th[m];
     h.lse = base + o_lse[m];
+    if (b->prec == PD_FP32) {
+      h.thL = reinterpret_cast<float*>(base + o_thl[m]);
+      h.ec = reinterpret_cast<float2*>(base + o_ec[m]);
+      h.ref = reinterpret_cast<float2*>(base + o_ref[m]);
+    }
     h.objp = reinterpret_cast<double*>(base + o_objp[m]);
     h.part = b->maps[m].grad_out ? reinterpret_cast<double*>(base + o_part[m]) : nullptr;
   }
@@ -315,6 +396,23 @@ int build_plan(pd_batch* b, const Tune& tu) {
       (!items2.empty() &&
        cudaMemcpy(b->d_items2, items2.data(), sizeof(int2) * items2.size(), cudaMemcpyHostToDevice) != cudaSuccess))
     return PD_ECUDA;
+  if (b->prec == PD_FP32) {
+    // the maps' centre features, once per plan
+    int64_t max_tiles = 1;
+    for (const auto& m : b->hmaps) max_tiles = std::max<int64_t>(max_tiles, m.tm.n_tiles);
+    const unsigned gx = (unsigned)std::min<int64_t>((max_tiles + 255) / 256, 1024);
+    switch (b->d) {
+      case 1: k_batch_features<1><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      case 2: k_batch_features<2><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      case 3: k_batch_features<3><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      case 4: k_batch_features<4><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      case 5: k_batch_features<5><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      case 6: k_batch_features<6><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      case 7: k_batch_features<7><<<dim3(gx, b->n_maps), 256>>>(b->d_maps); break;
+      default: break;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return PD_ECUDA;
+  }
   b->grid1 = std::max(1, std::min(b->n_items1, sms * std::max(1, b->occ1 / tu.occ_div)));
   b->grid2 = std::max(1, std::min(std::max(b->n_items2, 1), sms * std::max(1, b->occ2 / tu.occ_div)));
   b->tune = tu;

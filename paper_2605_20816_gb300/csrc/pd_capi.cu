@@ -373,6 +373,7 @@ int pd_heuristic_init(const pd_grid* grid, const int32_t* labels, int N, int d, 
 void pd_release(void) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
+  noalloc_forget_device();
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
     cudaDeviceSynchronize();

@@ -92,6 +92,9 @@ int eval_tc(const EvalCall& c, cudaStream_t st);
 int eval_tc_hvp(const EvalCall& c, cudaStream_t st);  // pd_tc_hvp.cu
 int selftest_wait_timeout(double seconds, int* status_out, cudaStream_t st);
 
+// pd_noalloc.cu
+void noalloc_forget_device();
+
 // pd_capi.cu
 int validate_grid(const pd_grid* grid, Geom* g);
 int theta_from_apd_host(int dim, int d, int N, const double* y, const double* w, const double* A,

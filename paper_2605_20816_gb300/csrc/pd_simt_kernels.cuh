@@ -21,6 +21,7 @@
 
 #include "pd_common.cuh"
 #include "pd_internal.h"
+#include "pd_tiles.cuh"
 
 namespace pd {
 // Everything here has internal linkage: each translation unit that includes
@@ -346,6 +347,329 @@ static __global__ void k_reduce_obj(const double* __restrict__ part, int n, doub
 }
 
 // ---------------------------------------------------------------------------
+// FP32 evaluation on tiles (pd_tiles.cuh).  The logits of a pixel are kept
+// relative to its tile's reference logit: l_i(x) - C(t) = o_i(t) +
+// theta'_i . (eta(x) - eta(c)), with o_i(t) = theta'_i . eta(c) - C(t)
+// formed in float-float inside the kernels (once per grain and tile) and
+// rounded once; log2 S(x) is kept relative to the same C(t).  Pass 2 forms
+// c = delta_{iG(x)} - p_i(x) from the same offsets and log2 S.
+//   pass 1: a block = kT1Tiles tiles (two pixels a thread), grains in
+//           shared-memory chunks with their offsets on the block's tiles;
+//   pass 2: a block = 128 grains over a run of tiles; per tile the pixels'
+//           features, feature differences, log2 S and labels in shared
+//           memory and each thread's offset on the tile.
+// ---------------------------------------------------------------------------
+constexpr int kT1Tiles = 4;  // tiles per pass-1 block: 512 pixels, two a thread
+static_assert(kGradThreads == kTilePix, "pass 2: one producer thread per tile row");
+
+// log2 of a float sum S >= 1 (the largest term of a log-sum-exp is 1): the
+// accurate library logarithm, so that log2 S of pixels whose sum is 1 plus
+// tiny terms carries no approximation bias.
+__device__ __forceinline__ float lse_log2(float s) { return log2f(s); }
+
+template <int DIM, int D, bool HVP>
+__device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& tm, const int32_t* __restrict__ labels,
+                                                  int N, const float* __restrict__ thH, const float* __restrict__ thL,
+                                                  const float* __restrict__ vS, const float2* __restrict__ ecg,
+                                                  const float2* __restrict__ refg, float* __restrict__ lse_out,
+                                                  float* __restrict__ ubar_out, double* __restrict__ obj_slot,
+                                                  int64_t blk) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<float>(K);
+  constexpr int GT = HVP ? 64 : 128;  // grains per shared chunk
+  __shared__ __align__(16) float sth[GT * KP];
+  __shared__ __align__(16) float stl[GT * KP];
+  __shared__ __align__(16) float sv[HVP ? GT * KP : 1];
+  __shared__ float soff[kT1Tiles][GT];
+  __shared__ float2 sec[kT1Tiles][K];
+  __shared__ float2 sref[kT1Tiles];
+  __shared__ double sred[kLseThreads / 32];
+
+  const int64_t t0 = blk * kT1Tiles;
+  const int r = threadIdx.x & (kTilePix - 1), hq = threadIdx.x / kTilePix;  // row; local tiles hq, hq + 2
+  for (int e = threadIdx.x; e < kT1Tiles * K; e += kLseThreads) {
+    const int64_t t = t0 + e / K;
+    sec[e / K][e % K] = t < tm.n_tiles ? ecg[t * K + e % K] : make_float2(0.f, 0.f);
+  }
+  if (threadIdx.x < kT1Tiles) {
+    const int64_t t = t0 + threadIdx.x;
+    sref[threadIdx.x] = t < tm.n_tiles ? refg[t] : make_float2(0.f, 0.f);
+  }
+  float de[2][K], eta[HVP ? 2 : 1][K];
+  int64_t jq[2];
+  float m[2], s[2], tu[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t t = t0 + hq + 2 * q;
+    float x[DIM], c[DIM], dx[DIM];
+    if (t < tm.n_tiles) {
+      jq[q] = tile_pixel_dx<DIM>(g, tm, t, r, x, c, dx);
+    } else {
+      jq[q] = -1;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) x[a] = c[a] = dx[a] = 0.f;
+    }
+    legendre_delta<DIM, D>(x, c, dx, de[q], HVP ? eta[q] : nullptr);
+    m[q] = -INFINITY;
+    s[q] = 0.f;
+    tu[q] = 0.f;
+  }
+
+  for (int g0 = 0; g0 < N; g0 += GT) {
+    const int gn = min(GT, N - g0);
+    __syncthreads();
+    {
+      const int nv = gn * KP / 4;
+      const uint4* src = reinterpret_cast<const uint4*>(thH + (int64_t)g0 * KP);
+      const uint4* srcl = reinterpret_cast<const uint4*>(thL + (int64_t)g0 * KP);
+      uint4* dst = reinterpret_cast<uint4*>(sth);
+      uint4* dstl = reinterpret_cast<uint4*>(stl);
+      for (int e = threadIdx.x; e < nv; e += kLseThreads) {
+        dst[e] = src[e];
+        dstl[e] = srcl[e];
+      }
+      if (HVP) {
+        const uint4* srcv = reinterpret_cast<const uint4*>(vS + (int64_t)g0 * KP);
+        uint4* dstv = reinterpret_cast<uint4*>(sv);
+        for (int e = threadIdx.x; e < nv; e += kLseThreads) dstv[e] = srcv[e];
+      }
+    }
+    __syncthreads();
+    // the chunk's offsets on the block's tiles, one (grain, tile) pair a thread
+    for (int e = threadIdx.x; e < gn * kT1Tiles; e += kLseThreads) {
+      const int gi = e % gn, q = e / gn;
+      soff[q][gi] = centre_offset<K>(sth + gi * KP, stl + gi * KP, sec[q], sref[q]);
+    }
+    __syncthreads();
+    int i = 0;
+    for (; i + kChunk <= gn; i += kChunk) {
+      float l[2][kChunk];
+      float u[2][HVP ? kChunk : 1];
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          l[q][c] = soff[hq + 2 * q][i + c] + dot_k<K>(sth + (i + c) * KP, de[q]);
+          if (HVP) u[q][c] = dot_k<K>(sv + (i + c) * KP, eta[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float cm = l[q][0];
+#pragma unroll
+        for (int c = 1; c < kChunk; ++c) cm = fmaxf(cm, l[q][c]);
+        const float mn = fmaxf(m[q], cm);
+        const float rr = Arith<float>::ex(m[q] - mn);
+        float add = 0.f, addu = 0.f;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+          const float e = Arith<float>::ex(l[q][c] - mn);
+          add += e;
+          if (HVP) addu = fmaf(e, u[q][c], addu);
+        }
+        s[q] = fmaf(s[q], rr, add);
+        if (HVP) tu[q] = fmaf(tu[q], rr, addu);
+        m[q] = mn;
+      }
+    }
+    for (; i < gn; ++i) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float l = soff[hq + 2 * q][i] + dot_k<K>(sth + i * KP, de[q]);
+        const float mn = fmaxf(m[q], l);
+        const float rr = Arith<float>::ex(m[q] - mn);
+        const float e = Arith<float>::ex(l - mn);
+        s[q] = fmaf(s[q], rr, e);
+        if (HVP) tu[q] = fmaf(tu[q], rr, e * dot_k<K>(sv + i * KP, eta[q]));
+        m[q] = mn;
+      }
+    }
+  }
+
+  double racc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t j = jq[q];
+    if (j < 0) continue;
+    const float lse = m[q] + lse_log2(s[q]);
+    if (lse_out) lse_out[j] = lse;
+    if (HVP) ubar_out[j] = tu[q] / s[q];
+    if (!HVP && obj_slot) {
+      const int G = labels[j];
+      if ((unsigned)G < (unsigned)N) {
+        float h[K], l[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          h[k] = thH[(int64_t)G * KP + k];
+          l[k] = thL[(int64_t)G * KP + k];
+        }
+        const int lt = hq + 2 * q;
+        const float lG = centre_offset<K>(h, l, sec[lt], sref[lt]) + dot_k<K>(h, de[q]);
+        racc += (double)(lG - lse) * Arith<float>::to_nat;
+      } else {
+        racc = NAN;  // a label outside 0..N-1 poisons the objective
+      }
+    }
+  }
+  if (!HVP && obj_slot) {
+    const double bs = block_sum_fixed(racc, sred);
+    if (threadIdx.x == 0) *obj_slot = bs;
+  }
+}
+
+template <int DIM, int D, bool HVP>
+__global__ void __launch_bounds__(kLseThreads)
+k_pass1_tiles(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const float* __restrict__ thH,
+              const float* __restrict__ thL, const float* __restrict__ vS, const float2* __restrict__ ecg,
+              const float2* __restrict__ refg, float* __restrict__ lse_out, float* __restrict__ ubar_out,
+              double* __restrict__ obj_part) {
+  pass1_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse_out, ubar_out,
+                                 obj_part ? obj_part + blockIdx.x : nullptr, blockIdx.x);
+}
+
+// Pass 2 on tiles: grain tile `gtile` over the tiles [chunk * tpc, ...).
+//   GRAD: c = delta_{iG(x)} - p_i(x);  HVP: c = p_i(x) (u_i(x) - ubar(x)).
+// Only the feature differences eta(x) - eta(c) are staged: the sum
+// sum_x c eta(x) of a tile is sum_x c (eta(x) - eta(c)) + (sum_x c) eta(c),
+// which reuses the operand the logit was formed from (and u = v.eta(c) +
+// v.(eta(x) - eta(c)) for the HVP).  Rows lie kP2Stride floats apart, an
+// odd number of 16-byte units, so that the producers' 16-byte stores of a
+// warp hit distinct banks.  The float sums of kP2Flush tiles go into one
+// double per grain and feature.
+template <int KP>
+__host__ __device__ constexpr int p2_stride() { return (KP / 4) % 2 == 0 ? KP + 4 : KP; }
+constexpr int kP2Flush = 8;
+
+template <int DIM, int D, bool HVP>
+__device__ __forceinline__ void pass2_tiles_block(const Geom& g, const TileMap& tm, const int32_t* __restrict__ labels,
+                                                  int N, const float* __restrict__ thH, const float* __restrict__ thL,
+                                                  const float* __restrict__ vS, const float2* __restrict__ ecg,
+                                                  const float2* __restrict__ refg, const float* __restrict__ lse,
+                                                  const float* __restrict__ ubar, int64_t tpc,
+                                                  double* __restrict__ part, int64_t chunk, int gtile) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<float>(K);
+  constexpr int RS = p2_stride<KP>();
+  __shared__ __align__(16) float sde[kTilePix * RS];
+  __shared__ float slse[kTilePix];
+  __shared__ float subar[HVP ? kTilePix : 1];
+  __shared__ int slab[kTilePix];
+  __shared__ float2 sec[K];
+  __shared__ float2 sref;
+  __shared__ double sacc[K * kGradThreads];
+
+  const int i = gtile * kGradThreads + threadIdx.x;
+  const bool vi = i < N;
+  float th[K], vv[HVP ? K : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    th[k] = vi ? thH[(int64_t)i * KP + k] : 0.f;
+    if (HVP) vv[k] = vi ? vS[(int64_t)i * KP + k] : 0.f;
+    sacc[k * kGradThreads + threadIdx.x] = 0.0;
+  }
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  const int64_t tb = chunk * tpc;
+  const int64_t te = min(tb + tpc, tm.n_tiles);
+  for (int64_t t = tb; t < te; ++t) {
+    __syncthreads();
+    {
+      // row threadIdx.x of the tile (rows outside the set: log2 S = +inf
+      // and no label, so that c = 0)
+      float x[DIM], c[DIM], dx[DIM], dd[KP];
+      const int64_t j = tile_pixel_dx<DIM>(g, tm, t, threadIdx.x, x, c, dx);
+      legendre_delta<DIM, D>(x, c, dx, dd, nullptr);
+#pragma unroll
+      for (int k = K; k < KP; ++k) dd[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < KP; k += 4)
+        *reinterpret_cast<float4*>(sde + threadIdx.x * RS + k) = make_float4(dd[k], dd[k + 1], dd[k + 2], dd[k + 3]);
+      slse[threadIdx.x] = j >= 0 ? lse[j] : INFINITY;
+      if (HVP) subar[threadIdx.x] = j >= 0 ? ubar[j] : 0.f;
+      else slab[threadIdx.x] = j >= 0 ? labels[j] : -1;
+      if (threadIdx.x < K) sec[threadIdx.x] = ecg[t * K + threadIdx.x];
+      if (threadIdx.x == 0) sref = refg[t];
+    }
+    __syncthreads();
+    // (the lo parts from L1 once per tile: registers are better spent on
+    // the pixel loop)
+    const float off = vi ? centre_offset<K>(th, thL + (int64_t)i * KP, sec, sref) : 0.f;
+    float uc = 0.f;  // v_i . eta(c)
+    if (HVP) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) uc = fmaf(vv[k], sec[k].x, uc);
+    }
+    float cs = 0.f;  // sum of c over the tile
+    auto coef = [&](int q, float l, const float* de) -> float {
+      const float p = Arith<float>::ex(l - slse[q]);
+      float cc;
+      if (HVP) {
+        const float u = uc + dot_k<K>(vv, de);
+        cc = p * (u - subar[q]);
+      } else {
+        cc = (slab[q] == i ? 1.f : 0.f) - p;
+      }
+      return vi ? cc : 0.f;
+    };
+    // PS pixels a step: two independent chains where registers allow
+    constexpr int PS = K <= 20 ? 2 : 1;
+    for (int q = 0; q < kTilePix; q += PS) {
+      float dq[PS][KP], cq[PS];
+#pragma unroll
+      for (int u = 0; u < PS; ++u) {
+#pragma unroll
+        for (int k = 0; k < KP; k += 4) {
+          const float4 a = *reinterpret_cast<const float4*>(sde + (q + u) * RS + k);
+          dq[u][k] = a.x;
+          dq[u][k + 1] = a.y;
+          dq[u][k + 2] = a.z;
+          dq[u][k + 3] = a.w;
+        }
+      }
+      bool nz = false;
+#pragma unroll
+      for (int u = 0; u < PS; ++u) {
+        cq[u] = coef(q + u, off + dot_k<K>(th, dq[u]), dq[u]);
+        nz |= cq[u] != 0.f;
+      }
+      if (__any_sync(0xffffffffu, nz)) {
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[k] = fmaf(cq[u], dq[u][k], acc[k]);
+          cs += cq[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = fmaf(cs, sec[k].x, acc[k]);
+    if ((t - tb) % kP2Flush == kP2Flush - 1 || t == te - 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        sacc[k * kGradThreads + threadIdx.x] += (double)acc[k];
+        acc[k] = 0.f;
+      }
+    }
+  }
+  if (vi) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[(chunk * N + i) * K + k] = sacc[k * kGradThreads + threadIdx.x];
+  }
+  __syncthreads();  // the shared tiles may be reused by the next work item
+}
+
+template <int DIM, int D, bool HVP>
+__global__ void __launch_bounds__(kGradThreads)
+k_pass2_tiles(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const float* __restrict__ thH,
+              const float* __restrict__ thL, const float* __restrict__ vS, const float2* __restrict__ ecg,
+              const float2* __restrict__ refg, const float* __restrict__ lse, const float* __restrict__ ubar,
+              int64_t tpc, double* __restrict__ part) {
+  pass2_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse, ubar, tpc, part, blockIdx.x,
+                                 blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
 // Arg-min assignment in double, smallest index on ties (eq. Li_def).
 // ---------------------------------------------------------------------------
 constexpr int kAssignThreads = 256;
@@ -487,8 +811,106 @@ inline int chunks_for(int64_t P, int grain_tiles, int sms) {
   return (int)want;
 }
 
+// Launches of one FP32 tile evaluation into caller-provided scratch:
+// parameters thH/thL/vS [N][KP], centre features ec [tiles][K], reference
+// logits ref [tiles], lse and ubar [P], objective partials objp [tiles /
+// kT1Tiles], gradient partials part [chunks][N][K].  Shared by the
+// allocating and the allocation-free entry points.
+template <int DIM, int D>
+int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* thL, float* vS, float2* ec,
+                      float2* ref, float* lse, float* ubar, double* objp, double* part, int64_t tpc,
+                      cudaStream_t st) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<float>(K);
+  const int N = c.N;
+  const int64_t P = c.g.P;
+  const bool hvp = c.v != nullptr;
+  const bool want_grad = c.grad != nullptr;
+  const int64_t n_tiles = tm.n_tiles;
+  const int64_t blocks1 = (n_tiles + kT1Tiles - 1) / kT1Tiles;
+  const int gtiles = (N + kGradThreads - 1) / kGradThreads;
+  const int nch = (int)((n_tiles + tpc - 1) / tpc);
+  const int64_t nth = (int64_t)N * KP;
+  PD_TIMED(st, "theta_ff",
+           k_theta_ff<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(c.theta, N, K, KP,
+                                                                      Arith<float>::theta_scale(c.eps), thH, thL));
+  if (hvp)
+    PD_TIMED(st, "scale_theta", k_copy_pad<float><<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(c.v, N, K, KP, vS));
+  PD_TIMED(st, "centre_features",
+           (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ec)));
+  PD_TIMED(st, "tile_refs",
+           (k_tile_refs<K><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(thH, N, n_tiles, ec, ref)));
+  const dim3 grid2(nch, gtiles);
+  if (hvp) {
+    PD_TIMED(st, "simt_hvp_pass1",
+             (k_pass1_tiles<DIM, D, true><<<(unsigned)blocks1, kLseThreads, 0, st>>>(
+                 c.g, tm, c.labels, N, thH, thL, vS, ec, ref, lse, ubar, nullptr)));
+    PD_TIMED(st, "simt_hvp_pass2",
+             (k_pass2_tiles<DIM, D, true><<<grid2, kGradThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, vS, ec, ref,
+                                                                         lse, ubar, tpc, part)));
+  } else {
+    PD_TIMED(st, "simt_lse_pass1",
+             (k_pass1_tiles<DIM, D, false><<<(unsigned)blocks1, kLseThreads, 0, st>>>(
+                 c.g, tm, c.labels, N, thH, thL, nullptr, ec, ref, lse, nullptr, objp)));
+    if (want_grad)
+      PD_TIMED(st, "simt_grad_pass2",
+               (k_pass2_tiles<DIM, D, false><<<grid2, kGradThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, nullptr,
+                                                                            ec, ref, lse, nullptr, tpc, part)));
+  }
+  if (c.obj && !hvp)
+    PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, (int)blocks1, 1.0 / (double)P, c.obj));
+  if (want_grad || hvp) {
+    const int64_t NK = (int64_t)N * K;
+    const double scale = hvp ? -1.0 / (c.eps * c.eps * (double)P) : -1.0 / (c.eps * (double)P);
+    PD_TIMED(st, "reduce_parts",
+             k_reduce_parts<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(part, nch, NK, scale,
+                                                                                       hvp ? c.hv : c.grad));
+  }
+  if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+  return PD_OK;
+}
+
+// Tiles per pass-2 chunk: about 6 CTAs per SM over the grain tiles.
+inline int64_t tiles_per_chunk(int64_t n_tiles, int grain_tiles, int sms, int factor = 6) {
+  int64_t want = ((int64_t)sms * factor + grain_tiles - 1) / grain_tiles;
+  want = std::max<int64_t>(1, std::min<int64_t>(want, n_tiles));
+  return (n_tiles + want - 1) / want;
+}
+
+// The FP32 evaluation on tiles (objective/gradient or HVP).
+template <int DIM, int D>
+int eval_simt_tiles(const EvalCall& c, cudaStream_t st) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<float>(K);
+  const int N = c.N;
+  const int64_t P = c.g.P;
+  const bool hvp = c.v != nullptr;
+  const bool want_grad = c.grad != nullptr;
+  const int sms = device_sm_count();
+  const TileMap tm = make_tiles<DIM>(c.g);
+  const int64_t n_tiles = tm.n_tiles;
+  const int64_t blocks1 = (n_tiles + kT1Tiles - 1) / kT1Tiles;
+  const int gtiles = (N + kGradThreads - 1) / kGradThreads;
+  const int64_t tpc = tiles_per_chunk(n_tiles, gtiles, sms);
+  const int nch = (int)((n_tiles + tpc - 1) / tpc);
+
+  Scratch sc(st);
+  float* thH = sc.get<float>((size_t)N * KP);
+  float* thL = sc.get<float>((size_t)N * KP);
+  float* vS = hvp ? sc.get<float>((size_t)N * KP) : nullptr;
+  float2* ec = sc.get<float2>((size_t)n_tiles * K);
+  float2* ref = sc.get<float2>((size_t)n_tiles);
+  float* lse = (want_grad || hvp) ? sc.get<float>((size_t)P) : nullptr;
+  float* ubar = hvp ? sc.get<float>((size_t)P) : nullptr;
+  double* objp = (!hvp && c.obj) ? sc.get<double>((size_t)blocks1) : nullptr;
+  double* part = (want_grad || hvp) ? sc.get<double>((size_t)nch * N * K) : nullptr;
+  if (!sc.ok()) return PD_ENOMEM;
+  return launch_simt_tiles<DIM, D>(c, tm, thH, thL, vS, ec, ref, lse, ubar, objp, part, tpc, st);
+}
+
 template <typename T, int DIM, int D>
 int eval_simt_dd(const EvalCall& c, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) return eval_simt_tiles<DIM, D>(c, st);
   constexpr int K = basis_K(DIM, D);
   constexpr int KP = padded_K<T>(K);
   const int N = c.N;

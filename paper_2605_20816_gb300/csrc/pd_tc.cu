@@ -73,7 +73,8 @@ template <int DIM, int D, int KS>
 __global__ void __launch_bounds__(kP1Threads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng, int n_stages,
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
-           const float* __restrict__ offg, float* __restrict__ lse_out, double* __restrict__ obj_part,
+           const float* __restrict__ offg, const int* __restrict__ rank, float* __restrict__ lse_out,
+           double* __restrict__ obj_part,
            float2* __restrict__ ms_out, float* __restrict__ lg_out, const unsigned long long* __restrict__ masks,
            uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
@@ -91,7 +92,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   float* sLG = sOff + S * Ng;                                    // S stages x 128 starting max
   float* sLGv = sLG + S * 128;                                   // S stages x 128 label logits
   long long* sJ = reinterpret_cast<long long*>(sLGv + S * 128);  // S stages x 128 pixel indices
-  float* sBm = reinterpret_cast<float*>(sJ + S * 128);           // S stages x Ng/128 x 128 block maxima
+  int* sLRow = reinterpret_cast<int*>(sJ + S * 128);             // S stages x 128 image rows of the labels
+  float* sBm = reinterpret_cast<float*>(sLRow + S * 128);        // S stages x Ng/128 x 128 block maxima
   float* sTh = sBm + S * Ng;                                     // K x Ng scaled parameters (when resident)
   __shared__ __align__(8) uint64_t bar_theta, bar_a_full[kP1Stages], bar_a_empty[kP1Stages], bar_off_free[kP1Stages],
       bar_d_full[kP1Bufs], bar_d_empty[kP1Bufs], bar_drain;
@@ -239,13 +241,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     };
     bool ok = !th_resident || mbar_wait_warp(&bar_theta, 0, &abort_flag, status);
     int64_t jn[kP1PixPerThread];
-    float xn[kP1PixPerThread][DIM], cn[DIM];
+    float xn[kP1PixPerThread][DIM], cn[DIM], dxn[kP1PixPerThread][DIM];
     int Gn[kP1PixPerThread];
     unsigned long long maskn = 0;
     auto fetch = [&](int64_t t) {
 #pragma unroll
       for (int u = 0; u < kP1PixPerThread; ++u) {
-        jn[u] = tile_pixel<DIM>(g, tm, t, p0 + kP1Producers * u, xn[u], cn);
+        jn[u] = tile_pixel_dx<DIM>(g, tm, t, p0 + kP1Producers * u, xn[u], cn, dxn[u]);
         Gn[u] = jn[u] >= 0 ? labels[jn[u]] : -1;
       }
       if (masks && p0 == 0) maskn = masks[t];
@@ -255,14 +257,17 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     for (int64_t t = blockIdx.x; ok && t < n_tiles; t += gridDim.x, ++it) {
       const int s = it % S, use = it / S;
       int64_t jc[kP1PixPerThread];
-      float xc[kP1PixPerThread][DIM], cc[DIM];
+      float xc[kP1PixPerThread][DIM], cc[DIM], dxc[kP1PixPerThread][DIM];
       int Gc[kP1PixPerThread];
 #pragma unroll
       for (int u = 0; u < kP1PixPerThread; ++u) {
         jc[u] = jn[u];
         Gc[u] = Gn[u];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) xc[u][a] = xn[u][a];
+        for (int a = 0; a < DIM; ++a) {
+          xc[u][a] = xn[u][a];
+          dxc[u][a] = dxn[u][a];
+        }
       }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) cc[a] = cn[a];
@@ -279,22 +284,21 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         mbar_expect_tx(&bar_a_full[s], (uint32_t)Ng * 4);
         bulk_g2s(sOff + s * Ng, offg + t * Npad + g0, (uint32_t)Ng * 4, &bar_a_full[s]);
       }
-      float ec[K];
-      legendre_features<DIM, D>(cc, ec);
 #pragma unroll
       for (int u = 0; u < kP1PixPerThread; ++u) {
         const int p = p0 + kP1Producers * u;
-        float eta[K];
-        legendre_features<DIM, D>(xc[u], eta);
         float de[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
+        legendre_delta<DIM, D>(xc[u], cc, dxc[u], de, nullptr);
         store_eta_row<K, KW, KS>(sA + s * kTileBytes, p, de);
         float start = -INFINITY, lg = 0.f;
+        int lrow = -1;
         if (jc[u] >= 0) {
           const int G = Gc[u];
           if ((unsigned)G < (unsigned)N) {
-            lg = dot_g(G, ec) + dot_g(G, de);
+            // the label logit relative to the tile's reference logit: its
+            // centre offset plus the remainder
+            lrow = rank ? rank[G] : G;
+            lg = offg[t * Npad + lrow] + dot_g(G, de);
             start = lg;
           } else {
             lg = NAN;
@@ -305,6 +309,7 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         sLG[s * 128 + p] = start;
         sLGv[s * 128 + p] = lg;
         sJ[s * 128 + p] = (long long)jc[u];
+        sLRow[s * 128 + p] = lrow;
       }
       fence_proxy_async();
       mbar_arrive(&bar_a_full[s]);
@@ -410,7 +415,8 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           // group's part, and the label logit (one term of the full sum)
           lse = fmaxf(m + Arith<float>::lg(ssum), sLG[s * 128 + row]);
         } else {
-          lse = m + Arith<float>::lg(ssum);
+          // the accurate logarithm: S is 1 plus small terms at most pixels
+          lse = m + log2f(ssum);
           lse_out[j] = lse;
           racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
         }
@@ -424,6 +430,15 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           const uint32_t bal = __ballot_sync(0xffffffffu, nd);
           if (lane == 0 && bal)
             atomicOr(&need_bits[(int64_t)(g0 / 128 + q) * n_words + (t >> 5)], 1u << (int)(t & 31));
+        }
+        // the gradient pass forms c = delta - p, so the block of every
+        // pixel's label is needed on its tile (set by the first launch)
+        if (g0 == 0) {
+          const int lrow = j >= 0 ? sLRow[s * 128 + row] : -1;
+          const int lq = lrow >= 0 ? lrow / 128 : -1;
+          const unsigned same = __match_any_sync(0xffffffffu, lq);
+          if (lq >= 0 && lane == __ffs(same) - 1)
+            atomicOr(&need_bits[(int64_t)lq * n_words + (t >> 5)], 1u << (int)(t & 31));
         }
       }
       mbar_arrive(&bar_off_free[s]);
@@ -509,32 +524,35 @@ __device__ __forceinline__ P2Share p2_share(const int* counts, int64_t n_tiles, 
 
 template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2ThreadsG, 1)
-k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img, const float* __restrict__ offg,
-           const float* __restrict__ lse, const int* __restrict__ kept, const int* __restrict__ n_kept_gb, int nb,
-           const int* __restrict__ perm, double* __restrict__ part, int* __restrict__ status) {
+k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, const uint8_t* __restrict__ img,
+           const float* __restrict__ offg, const float* __restrict__ lse, const int* __restrict__ kept,
+           const int* __restrict__ n_kept_gb, int nb, const int* __restrict__ perm, double* __restrict__ part,
+           int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
-  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
+  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2, CT = L::CT, LB = L::LB;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
   constexpr uint32_t IDESC2 = idesc_f16(128, N2);
-  constexpr int D2COL = kP2LogitBufs * kTcPixTile;  // TMEM: D1 ring [0, 384), D2 x 2 from 384
-  static_assert(D2COL + 2 * N2 <= kTcCols, "TMEM columns");
+  constexpr int D2COL = LB * kTcPixTile;  // TMEM: D1 ring [0, LB*128); D2 buffer db at D2COL + db*CT*N2
+  static_assert(D2COL + 2 * CT * N2 <= kTcCols, "TMEM columns");
+  constexpr float kLoScale = 4096.f;       // c_lo = fl16((c - c_hi) * 2^12)
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                             // theta block image
   uint8_t* sB = sA + L::kABytes;                  // NB stages of eta - eta(c) rows
   uint8_t* sB2 = sB + NB * L::kBBytes;            // NB stages of eta^T
-  uint8_t* sA2 = sB2 + NB * L::kB2Bytes;          // NA stages of c
+  uint8_t* sA2 = sB2 + NB * L::kB2Bytes;          // NA stages of c (CT terms)
   float* sLse = reinterpret_cast<float*>(sA2 + NA * L::kA2Bytes);  // [NB][128] log2 S of the pixels
   float* sOffP = sLse + NB * kTcPixTile;                           // [NB][128] centre logits of the block
-  __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[kP2LogitBufs],
-      bar_d1_empty[kP2LogitBufs], bar_a2_full[NA], bar_a2_empty[NA], bar_d2_full[2], bar_d2_free[2], bar_drain;
+  int* sLab = reinterpret_cast<int*>(sOffP + NB * 128);            // [NB][128] labels of the pixels
+  __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[LB], bar_d1_empty[LB],
+      bar_a2_full[NA], bar_a2_empty[NA], bar_d2_full[2], bar_d2_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5;
   // this CTA's grain block and share of the tiles on which the block has a
-  // non-negligible probability (all tiles without the lists), in tile
-  // order; chunks of kP2ChunkTiles of them add up to one gradient partial
+  // non-negligible probability or a label (all tiles without the lists), in
+  // tile order; chunks of kP2ChunkTiles of them add up to one gradient partial
   const P2Share sh = p2_share(kept ? n_kept_gb : nullptr, tm.n_tiles, nb, gridDim.x, blockIdx.x);
   const int gb = sh.gb;  // grain block
   const int64_t n_list = sh.n > 0 ? (kept ? (int64_t)n_kept_gb[gb] : tm.n_tiles) : 0;
@@ -550,7 +568,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       mbar_init(&bar_b_full[s], kP2Producers);
       mbar_init(&bar_b_empty[s], 2);  // both MMA issuers are done with the stage
     }
-    for (int b = 0; b < kP2LogitBufs; ++b) {
+    for (int b = 0; b < LB; ++b) {
       mbar_init(&bar_d1_full[b], 1);
       mbar_init(&bar_d1_empty[b], kTcConsumers);
     }
@@ -579,10 +597,9 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       bulk_g2s(sA, img + (size_t)gb * L::kABytes, L::kABytes, &bar_theta);
       bool ok = mbar_wait(&bar_theta, 0, &abort_flag, status);
       for (int t = 0; ok && t < n_kept; ++t) {
-        const int s = t % NB, b1 = t % kP2LogitBufs;
+        const int s = t % NB, b1 = t % LB;
         ok = mbar_wait(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status);
-        if (ok && t >= kP2LogitBufs)
-          ok = mbar_wait(&bar_d1_empty[b1], (uint32_t)(((t / kP2LogitBufs) - 1) & 1), &abort_flag, status);
+        if (ok && t >= LB) ok = mbar_wait(&bar_d1_empty[b1], (uint32_t)(((t / LB) - 1) & 1), &abort_flag, status);
         if (!ok) break;
         tc_fence_after();
         mma_terms<KS, KW>(tmem + b1 * kTcPixTile, smem_addr(sA), KT * 16, true, smem_addr(sB + s * L::kBBytes),
@@ -595,9 +612,10 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     }
     __syncwarp();
   } else if (warp == kP2GradWarpG) {
-    // gradient D2 += C . [eta_h | eta_l], fp16; one D2 accumulation per
-    // chunk, alternating between two TMEM buffers so that the consumers
-    // read one while the next fills
+    // gradient D2 += C . [eta_h | eta_l] (fp16), one product per term of c
+    // into its own columns; one D2 accumulation per chunk, alternating
+    // between two TMEM buffers so that the consumers read one while the
+    // next fills
     if (tid == kP2GradWarpG * 32) {
       bool ok = true;
       for (int t = 0; ok && t < n_kept; ++t) {
@@ -611,9 +629,12 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
         const uint32_t a2 = smem_addr(sA2 + a * L::kA2Bytes), b2 = smem_addr(sB2 + s * L::kB2Bytes);
 #pragma unroll 2
         for (int q = 0; q < kTcPixTile / 16; ++q) {
-          const uint64_t ad = smem_desc(a2 + q * 256, 128, kTcPixTile * 16);
           const uint64_t bd = smem_desc(b2 + q * 2 * L::kLbo2, L::kLbo2, L::kSbo2);
-          mma_bf16(tmem + D2COL + db * N2, ad, bd, IDESC2, (!first || q > 0) ? 1u : 0u);
+#pragma unroll
+          for (int ct = 0; ct < CT; ++ct) {
+            const uint64_t ad = smem_desc(a2 + ct * L::kA2Term + q * 256, 128, kTcPixTile * 16);
+            mma_bf16(tmem + D2COL + (db * CT + ct) * N2, ad, bd, IDESC2, (!first || q > 0) ? 1u : 0u);
+          }
         }
         mma_commit(&bar_a2_empty[a]);
         mma_commit(&bar_b_empty[s]);
@@ -624,26 +645,31 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     }
     __syncwarp();
   } else if (warp >= kP2ProdWarp0 && warp < kP2MmaWarp) {
-    // pixel operands of every tile: the logit operand row, the transposed
-    // gradient operand, log2 S of the pixel and (first thread) the block's
-    // centre logits.  A thread owns one pixel row; the next tile's
-    // coordinates and log2 S are fetched while the current tile is written.
+    // pixel operands of every tile: the logit operand row (eta - eta(c)),
+    // the transposed gradient operand (eta), log2 S and the label of the
+    // pixel and (first thread) the block's centre logits.  A thread owns one
+    // pixel row; the next tile's coordinates, log2 S and label are fetched
+    // while the current tile is written.
     const int p = tid - kTcConsumers;
-    float xn[DIM], cn[DIM], lsn = INFINITY;
+    float xn[DIM], cn[DIM], dxn[DIM], lsn = INFINITY;
+    int labn = -1;
     auto fetch = [&](int t) {
-      const int64_t j = tile_pixel<DIM>(g, tm, tile_of(t), p, xn, cn);
+      const int64_t j = tile_pixel_dx<DIM>(g, tm, tile_of(t), p, xn, cn, dxn);
       lsn = j >= 0 ? lse[j] : INFINITY;
+      labn = j >= 0 ? labels[j] : -1;
     };
     if (n_kept > 0) fetch(0);
     for (int t = 0; t < n_kept; ++t) {
       const int s = t % NB;
-      float xc[DIM], cc[DIM];
+      float xc[DIM], cc[DIM], dxc[DIM];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         xc[a] = xn[a];
         cc[a] = cn[a];
+        dxc[a] = dxn[a];
       }
       const float lsc = lsn;
+      const int labc = labn;
       const int64_t tc = tile_of(t);
       if (t + 1 < n_kept) fetch(t + 1);
       if (t >= NB && !mbar_wait_warp(&bar_b_empty[s], (uint32_t)(((t / NB) - 1) & 1), &abort_flag, status)) break;
@@ -654,15 +680,9 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
         mbar_expect_tx(&bar_b_full[s], 128 * 4);
         bulk_g2s(sOffP + s * 128, offg + tc * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
       }
-      float ec[K], e0[K];
-      legendre_features<DIM, D>(cc, ec);
-      legendre_features<DIM, D>(xc, e0);
-      {
-        float de[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = e0[k] - ec[k];
-        store_eta_row<K, KW, KS, L::kSboB>(sB + s * L::kBBytes, p, de);
-      }
+      float e0[K], de[K];
+      legendre_delta<DIM, D>(xc, cc, dxc, de, e0);
+      store_eta_row<K, KW, KS, L::kSboB>(sB + s * L::kBBytes, p, de);
       // eta^T in fp16 (hi, and lo for PD_BF16X3); neighbouring threads fill
       // the two halves of one 32-bit word (pixels outside the set have
       // c = 0, so their features need no masking)
@@ -676,6 +696,7 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
         if (ET == 2) *reinterpret_cast<__half*>(b2 + L::kB2Term + o) = __float2half_rn(a0 - __half2float(h));
       }
       sLse[s * kTcPixTile + p] = lsc;
+      sLab[s * kTcPixTile + p] = labc;
       fence_proxy_async();
       mbar_arrive(&bar_b_full[s]);
     }
@@ -693,45 +714,68 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
       const int db = u & 1;
       if (!mbar_wait_warp(&bar_d2_full[db], (uint32_t)((u >> 1) & 1), &abort_flag, status)) return false;
       tc_fence_after();
-      uint32_t r[N2 < 32 ? 32 : N2];
-      const uint32_t base = tmem + lane_base + (uint32_t)(D2COL + db * N2);
-      if (N2 == 16) {
-        tmem_ld16(base, r);
-      } else {
+      const uint32_t base = tmem + lane_base + (uint32_t)(D2COL + db * CT * N2);
+      // 16 features at a time: the eta_h and eta_l columns of each term of
+      // c, added in fp32 (the accumulators' own precision), c_lo scaled back
 #pragma unroll
-        for (int c0 = 0; c0 < N2; c0 += 32) tmem_ld32(base + c0, r + c0);
-      }
-      tmem_wait_ld();
-      tc_fence_before();
-      mbar_arrive(&bar_d2_free[db]);
-      if (prow) {
+      for (int kb = 0; kb < KW; kb += 16) {
+        float f[16];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const double v = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
-          prow[k] = u == 0 ? v : prow[k] + v;
+        for (int ct = 0; ct < CT; ++ct) {
+          uint32_t r[ET][16];
+#pragma unroll
+          for (int et = 0; et < ET; ++et) tmem_ld16(base + (uint32_t)(ct * N2 + et * KW + kb), r[et]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            const float v = ET == 2 ? __uint_as_float(r[0][kk]) + __uint_as_float(r[ET - 1][kk]) : __uint_as_float(r[0][kk]);
+            f[kk] = ct == 0 ? v : fmaf(v, 1.f / kLoScale, f[kk]);
+          }
+        }
+        if (prow) {
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            const int k = kb + kk;
+            if (k < K) prow[k] = u == 0 ? (double)f[kk] : prow[k] + (double)f[kk];
+          }
         }
       }
+      tc_fence_before();
+      mbar_arrive(&bar_d2_free[db]);
       n_done = u + 1;
       return true;
     };
-    // c = -p for 32 pixels (columns q0 .. q0+31 of this thread's half),
-    // written as fp16 pairs, one 16-byte core-matrix row per 8 pixels
-    auto emit = [&](const uint32_t(&r)[32], const float* ls, float off, uint8_t* a2, int q0) {
+    // c = delta - p for 32 pixels (columns q0 .. q0+31 of this thread's
+    // half), written as fp16 pairs, one 16-byte core-matrix row per 8
+    // pixels: c_hi = fl16(c) and, for PD_BF16X3, c_lo = fl16((c - c_hi) 2^12)
+    auto emit = [&](const uint32_t(&r)[32], const float* ls, const int* lab, float off, uint8_t* a2, int q0) {
 #pragma unroll
       for (int q8 = 0; q8 < 32; q8 += 8) {
         const float4 va = *reinterpret_cast<const float4*>(ls + q8);
         const float4 vb = *reinterpret_cast<const float4*>(ls + q8 + 4);
+        const int4 la = *reinterpret_cast<const int4*>(lab + q8);
+        const int4 lb = *reinterpret_cast<const int4*>(lab + q8 + 4);
         const float lv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-        uint32_t hw[4];
+        const int lg[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+        uint32_t hw[4], lw[4];
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
           // l - log2 S = r + (off - lv), two pixels per packed fp32 add
           const float2 t = __fadd2_rn(make_float2(off, off), make_float2(-lv[u], -lv[u + 1]));
           const float2 x = __fadd2_rn(make_float2(__uint_as_float(r[q8 + u]), __uint_as_float(r[q8 + u + 1])), t);
-          const __half2 h = __floats2half2_rn(-Arith<float>::ex(x.x), -Arith<float>::ex(x.y));
+          const float c0 = (lg[u] == gi ? 1.f : 0.f) - Arith<float>::ex(x.x);
+          const float c1 = (lg[u + 1] == gi ? 1.f : 0.f) - Arith<float>::ex(x.y);
+          const __half2 h = __floats2half2_rn(c0, c1);
           hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+          if (CT == 2) {
+            const float2 hf = __half22float2(h);
+            const __half2 l2 = __floats2half2_rn((c0 - hf.x) * kLoScale, (c1 - hf.y) * kLoScale);
+            lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
+          }
         }
-        *reinterpret_cast<uint4*>(a2 + kmaj(gr, q0 + q8, kTcPixTile)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        const uint32_t o = kmaj(gr, q0 + q8, kTcPixTile);
+        *reinterpret_cast<uint4*>(a2 + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if (CT == 2) *reinterpret_cast<uint4*>(a2 + L::kA2Term + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
     };
     // the two 32-column halves of the thread's logits: the second is loaded
@@ -741,12 +785,12 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
     bool pre = false;
     bool ok = true;
     for (int t = 0; t < n_kept; ++t) {
-      const int s = t % NB, b1 = t % kP2LogitBufs, a = t % NA;
+      const int s = t % NB, b1 = t % LB, a = t % NA;
       const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
-      // sLse and sOffP of the stage were written by the producers
+      // sLse, sLab and sOffP of the stage were written by the producers
       if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) { ok = false; break; }
       if (!pre) {
-        if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t / kP2LogitBufs) & 1), &abort_flag, status)) {
+        if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t / LB) & 1), &abort_flag, status)) {
           ok = false;
           break;
         }
@@ -762,21 +806,22 @@ k_tc_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ img,
         break;
       }
       const float* ls = sLse + s * kTcPixTile + half * 64;
+      const int* lb = sLab + s * kTcPixTile + half * 64;
       uint8_t* a2 = sA2 + a * L::kA2Bytes;
-      emit(RA, ls, off, a2, half * 64);
+      emit(RA, ls, lb, off, a2, half * 64);
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(&bar_d1_empty[b1]);  // the tile's logits are in registers: release its TMEM columns
       pre = false;
       if (t + 1 < n_kept) {
-        const int bn = (t + 1) % kP2LogitBufs;
-        if (__all_sync(0xffffffffu, mbar_peek(&bar_d1_full[bn], (uint32_t)(((t + 1) / kP2LogitBufs) & 1)))) {
+        const int bn = (t + 1) % LB;
+        if (__all_sync(0xffffffffu, mbar_peek(&bar_d1_full[bn], (uint32_t)(((t + 1) / LB) & 1)))) {
           tc_fence_after();
           tmem_ld32(tmem + lane_base + (uint32_t)(bn * kTcPixTile + half * 64), RA);
           pre = true;
         }
       }
-      emit(RB, ls + 32, off, a2, half * 64 + 32);
+      emit(RB, ls + 32, lb + 32, off, a2, half * 64 + 32);
       fence_proxy_async();
       mbar_arrive(&bar_a2_full[a]);
       // the first warpgroup writes the previous chunk's partial one tile
@@ -823,7 +868,7 @@ k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float*
       const float2 v = ms[(int64_t)q * P + j];
       if (v.y > 0.f) sum = fmaf(v.y, Arith<float>::ex(v.x - m), sum);
     }
-    const float l = m + Arith<float>::lg(sum);
+    const float l = m + log2f(sum);
     lse_out[j] = l;
     r = (double)(lg[j] - l) * Arith<float>::to_nat;
   }
@@ -879,7 +924,7 @@ k_tc_reduce_eval(const double* __restrict__ part, int n_cta, const int* __restri
   ssum[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.y == 0 && q < NK) {
-    double t = (double)(long long)base[q] * inv_fx;
+    double t = base ? (double)(long long)base[q] * inv_fx : 0.0;
 #pragma unroll
     for (int y = 0; y < 8; ++y) t += ssum[y][threadIdx.x];
     grad[q] = t * scale;
@@ -928,7 +973,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   // fit too.  More grains than one SM holds are split into groups of ng,
   // one launch each, whose (max, sum) per pixel are merged afterwards.
   auto p1_bytes = [&](size_t ng, bool th_res, size_t S = 2) {
-    return ng * row_bytes + S * (kTcPixTile * row_bytes + ng * 4 + 2 * kTcPixTile * 4 + kTcPixTile * 8 + ng * 4) +
+    return ng * row_bytes + S * (kTcPixTile * row_bytes + ng * 4 + 2 * kTcPixTile * 4 + kTcPixTile * 8 +
+                                 kTcPixTile * 4 + ng * 4) +
            (th_res ? (size_t)K * ng * 4 : 0);
   };
   int n_grp = 1, Ng = Npad;
@@ -980,16 +1026,21 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   const bool bounds = skip_on && !c.g.coords && Npad / 128 <= 64;
   const bool order = skip && Npad <= kOrderMax;
 
+  constexpr int KP = padded_K<float>(K);
+  constexpr int K1 = DIM + 1;  // label moments of degree <= 1: counts and centroids for the grain order
   Scratch sc(st);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
   float* th32t = sc.get<float>((size_t)K * Npad);
-  float* offg = sc.get<float>((size_t)n_tiles * Npad);  // centre logits [tile][grain]
+  float* thH = sc.get<float>((size_t)N * KP);  // float-float parameters for the centre logits
+  float* thL = sc.get<float>((size_t)N * KP);
+  float2* ecg = sc.get<float2>((size_t)n_tiles * K);  // centre features per tile
+  float* offg = sc.get<float>((size_t)n_tiles * Npad);  // relative centre logits [tile][image row]
   float* lse = sc.get<float>((size_t)P);
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
   double* part = c.grad ? sc.get<double>((size_t)n_cta2 * N * K) : nullptr;  // one partial per pass-2 CTA and grain
-  unsigned long long* lmom = c.grad ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
+  unsigned long long* lmom = nullptr;
   // one bit per (128-grain block, tile): the block has a probability that
   // the gradient pass cannot neglect on the tile; then the tiles per block
   const int64_t n_words = (n_tiles + 31) / 32;
@@ -998,8 +1049,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   int* nkept = skip ? sc.get<int>((size_t)(Npad / 128)) : nullptr;
   int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
   int* rank = order ? sc.get<int>((size_t)N) : nullptr;
-  float* amax = bounds ? sc.get<float>((size_t)Npad) : nullptr;
-  float* mbb = bounds ? sc.get<float>((size_t)n_tiles * (Npad / 128)) : nullptr;
+  if (order) lmom = sc.get<unsigned long long>((size_t)N * K1);
   unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
   const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
   int* status = sc.get<int>(1);
@@ -1013,32 +1063,33 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   int bits = 0;
   while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
   const float fx = ldexpf(1.f, 62 - bits);
-  if (c.grad) {
-    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+  if (order) {
+    // the grains' label centroids (sums of 1 and x per grain) for the order
+    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K1, st) != cudaSuccess) return PD_ECUDA;
     const int64_t nthr = n_tiles * kTcPixTile;
     PD_TIMED(st, "tc_label_moments",
-             (k_tc_label_moments<DIM, D><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
+             (k_tc_label_moments<DIM, 1><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
                                                                                        lmom)));
-  }
-  if (order)
     PD_TIMED(st, "tc_grain_order",
-             k_tc_grain_order<DIM><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lmom, N, K, Npad, perm, rank));
+             k_tc_grain_order<DIM><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lmom, N, K1, Npad, perm, rank));
+  }
   const double scale = Arith<float>::theta_scale(c.eps);
+  {
+    const int64_t n = (int64_t)N * KP;
+    PD_TIMED(st, "theta_ff",
+             k_theta_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, K, KP, scale, thH, thL));
+  }
   {
     const int64_t n = (int64_t)Npad * KW;
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, Npad, K, KW, scale,
                                                                                 nullptr, perm, img, th32t));
   }
-  PD_TIMED(st, "tc_centre_logits",
-           (k_tc_centre_logits<DIM, D><<<dim3((unsigned)(Npad / 256),
-                                              (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles,
-                                                                          4096)),
-                                         256, 0, st>>>(c.g, tm, th32t, perm, N, Npad, offg, tb, amax, mbb)));
-  if (bounds)
-    PD_TIMED(st, "tc_tile_masks",
-             k_tc_tile_masks<DIM><<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, rank, offg,
-                                                                                   Npad, amax, mbb, masks));
+  PD_TIMED(st, "centre_features",
+           (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
+  PD_TIMED(st, "tc_tile_setup",
+           (k_tc_tile_setup<DIM, D><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(
+               c.g, tm, thH, thL, N, Npad, perm, ecg, offg, tb, bounds ? 1 : 0, masks)));
   auto k1 = k_tc_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)
     return PD_ECUDA;
@@ -1046,7 +1097,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const int g0 = q * Ng, ng = std::min(Ng, Npad - g0);
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
              k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, p1_stages, img, th32t,
-                                                      th_resident, offg,
+                                                      th_resident, offg, perm ? rank : nullptr,
                                                       lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, masks, need,
                                                       n_words, status));
   }
@@ -1062,8 +1113,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<n_cta2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, N, Npad, img, offg, lse, kept, nkept, gblocks, perm,
-                                                        part, status));
+             k2<<<n_cta2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, c.labels, N, Npad, img, offg, lse, kept, nkept,
+                                                        gblocks, perm, part, status));
     if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   }
   if (c.obj || c.grad) {
@@ -1071,8 +1122,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     const unsigned blocks = c.grad ? (unsigned)((NK + 31) / 32) : 1u;
     PD_TIMED(st, "reduce_eval",
              k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(
-                 part, n_cta2, kept ? nkept : nullptr, gblocks, perm ? rank : nullptr, n_tiles, K, NK, lmom,
-                 1.0 / (double)fx, -1.0 / (c.eps * (double)P), c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P,
+                 part, n_cta2, kept ? nkept : nullptr, gblocks, perm ? rank : nullptr, n_tiles, K, NK,
+                 (const unsigned long long*)nullptr, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P,
                  c.obj));
   }
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;

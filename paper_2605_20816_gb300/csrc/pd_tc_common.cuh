@@ -29,7 +29,7 @@ constexpr int kTcMmaWarp = 10;                    // TMEM allocation and MMA iss
 constexpr int kTcThreads = 11 * 32;               // at most 3 warps per SM sub-partition
 constexpr int kTcCols = 512;                      // TMEM columns per CTA (one CTA per SM)
 constexpr int kTcGrainTile = 256;                 // pass-1 grains per MMA group (N of the MMA)
-constexpr int kTcPixTile = 128;                   // pixels per tile (both passes)
+constexpr int kTcPixTile = kTilePix;              // pixels per tile (both passes)
 // objective pass 1: 8 epilogue warps, 4 producer warps (one pixel per
 // thread, one producer on each SM sub-partition), one MMA warp
 constexpr int kP1Producers = 128;
@@ -203,18 +203,22 @@ __host__ __device__ constexpr int eta_term(int s) { return s == 1 || s == 4 ? 1 
 // The KS products of a logit chain: MMAs of K = 16 whose A and B
 // descriptors start at the term slices of the two operands (rows of KT
 // columns: slice t at column t*KW).  kind::f16, M = 128, N from idesc.
+// The products are issued smallest first (lh, mm, hl, mh, hm, hh): the
+// accumulator truncates, and its partial sums stay small until the last,
+// leading product is added.
 template <int KS, int KW>
 __device__ __forceinline__ void mma_terms(uint32_t d, uint32_t aaddr, uint32_t a_sbo, bool a_theta, uint32_t baddr,
                                           uint32_t b_sbo, uint32_t idesc) {
 #pragma unroll 1
-  for (int s = 0; s < KS; ++s) {
+  for (int si = 0; si < KS; ++si) {
+    const int s = KS - 1 - si;
     const int ta = KS == 1 ? 0 : (a_theta ? theta_term(s) : eta_term(s));
     const int tb = KS == 1 ? 0 : (a_theta ? eta_term(s) : theta_term(s));
 #pragma unroll
     for (int q = 0; q < KW / 16; ++q) {
       const uint64_t ad = smem_desc(aaddr + (uint32_t)(ta * KW * 16 + q * 256), 128, a_sbo);
       const uint64_t bd = smem_desc(baddr + (uint32_t)(tb * KW * 16 + q * 256), 128, b_sbo);
-      mma_bf16(d, ad, bd, idesc, (s > 0 || q > 0) ? 1u : 0u);
+      mma_bf16(d, ad, bd, idesc, (si > 0 || q > 0) ? 1u : 0u);
     }
   }
 }
@@ -279,76 +283,13 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
 }
 
 // ---------------------------------------------------------------------------
-// Pixel tiles.  A tile is 128 pixels that are close in space: a 16 x 8 block
-// of a 2-D grid or an 8 x 4 x 4 block of a 3-D grid (128 consecutive points
-// of a point list).  Every logit is split at the tile centre c,
-//   l_i(x) = theta'_i . eta(c) + theta'_i . (eta(x) - eta(c)),
-// the first part (one per grain and tile) on the CUDA cores in fp32 and the
-// second, small part on the tensor cores.  The tensor cores accumulate with
-// truncation, whose error is biased; keeping their operand small (|x - c|
-// is a few pixels) keeps that bias far below the float rounding of the
-// logits, which is unbiased.
+// Pixel tiles (pd_tiles.cuh).  The logits of a tile's pixels are formed
+// relative to the tile's reference logit C(t): the centre part
+// theta'_i . eta(c) - C(t) per grain and tile from float-float arithmetic
+// (k_tc_centre_offsets), the small remainder theta'_i . (eta(x) - eta(c)) on
+// the tensor cores, whose fp32 accumulation truncates (its biased error must
+// act on small numbers).
 // ---------------------------------------------------------------------------
-struct TileMap {
-  int ntx, nty, ntz;      // tiles per axis (structured grids)
-  int64_t n_tiles;
-  int n0, n1, n2;         // grid sides
-  float f0, f1, f2;       // 1 / n_a rounded to float
-};
-
-template <int DIM>
-struct TileShape {
-  static constexpr int X = DIM == 2 ? 16 : 8;
-  static constexpr int Y = DIM == 2 ? 8 : 4;
-  static constexpr int Z = DIM == 2 ? 1 : 4;
-};
-
-// Pixel index of row r of tile t (or -1 outside the pixel set), its
-// coordinates x and the coordinates of the tile centre c.  Only 32-bit
-// integer arithmetic and fp32: a centre -1 + (2k+1)/n is formed as the exact
-// integer 2k+1-n times the float 1/n (exact when n is a power of two, else
-// within an ulp of the rounded value); both passes use this same function,
-// so the log-sum-exp of pass 1 belongs to the very points of pass 2.
-template <int DIM>
-__device__ __forceinline__ int64_t tile_pixel(const Geom& g, const TileMap& tm, int64_t t, int r, float* x,
-                                              float* c) {
-  if (g.coords) {
-    const int64_t j0 = t * kTcPixTile;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) c[a] = (float)g.coords[j0 * DIM + a];
-    const int64_t j = j0 + r;
-    if (j >= g.P) {
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) x[a] = c[a];
-      return -1;
-    }
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) x[a] = (float)g.coords[j * DIM + a];
-    return j;
-  }
-  using TS = TileShape<DIM>;
-  const unsigned tt = (unsigned)t;
-  const unsigned tx = tt % (unsigned)tm.ntx;
-  const unsigned rest = tt / (unsigned)tm.ntx;
-  const int ty = (int)(rest % (unsigned)tm.nty);
-  const int tz = (int)(rest / (unsigned)tm.nty);
-  const int px = (int)tx * TS::X + (r % TS::X);
-  const int py = ty * TS::Y + ((r / TS::X) % TS::Y);
-  const int pz = tz * TS::Z + (r / (TS::X * TS::Y));
-  c[0] = (float)(2 * ((int)tx * TS::X + TS::X / 2) + 1 - tm.n0) * tm.f0;
-  c[1] = (float)(2 * (ty * TS::Y + TS::Y / 2) + 1 - tm.n1) * tm.f1;
-  if (DIM == 3) c[2] = (float)(2 * (tz * TS::Z + TS::Z / 2) + 1 - tm.n2) * tm.f2;
-  x[0] = (float)(2 * px + 1 - tm.n0) * tm.f0;
-  x[1] = (float)(2 * py + 1 - tm.n1) * tm.f1;
-  if (DIM == 3) x[2] = (float)(2 * pz + 1 - tm.n2) * tm.f2;
-  if (px >= tm.n0 || py >= tm.n1 || (DIM == 3 && pz >= tm.n2)) {
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) x[a] = c[a];
-    return -1;
-  }
-  return DIM == 2 ? px + (int64_t)tm.n0 * py : px + (int64_t)tm.n0 * (py + (int64_t)tm.n1 * pz);
-}
-
 template <int K>
 __device__ __forceinline__ float dot_f(const float* __restrict__ a, const float* __restrict__ b) {
   float acc = a[0] * b[0];
@@ -415,9 +356,6 @@ __device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp
 // ---------------------------------------------------------------------------
 constexpr int kCentreTiles = 32;
 
-struct TileBound {
-  float d[32];  // D_k
-};
 
 template <int DIM, int D>
 __global__ void __launch_bounds__(256)
@@ -505,6 +443,7 @@ struct Pass2Layout {
   static constexpr int KT = KW * n_terms(KS);
   static constexpr int ET = KS == 1 ? 1 : 2;  // fp16 terms of eta in the gradient contraction
   static constexpr int N2 = ET * KW;           // its MMA N: eta_h (and eta_l) columns
+  static constexpr int CT = KS == 1 ? 1 : 2;  // fp16 terms of c (hi, and lo scaled by 2^12)
 
   static constexpr uint32_t kABytes = 128u * KT * 2;             // theta block
   static constexpr uint32_t kSboB = (uint32_t)KT * 16 + 16;
@@ -513,9 +452,14 @@ struct Pass2Layout {
   static constexpr uint32_t kSbo2 = 16 * kLbo2;
   static constexpr uint32_t kB2Term = (KW / 8) * kSbo2;
   static constexpr uint32_t kB2Bytes = ET * kB2Term;           // rows: eta_h features, then eta_l
-  static constexpr uint32_t kA2Bytes = 128u * kTcPixTile * 2;    // c: 128 grains x 128 pixels, fp16
-  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + 128 * 4;
+  static constexpr uint32_t kA2Term = 128u * kTcPixTile * 2;     // one term of c: 128 grains x 128 pixels, fp16
+  static constexpr uint32_t kA2Bytes = CT * kA2Term;
+  // + log2 S, centre logits of the block, labels of the pixels
+  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + 128 * 4 + kTcPixTile * 4;
   static constexpr size_t bytes(int nb, int na) { return kABytes + (size_t)nb * kPerB + (size_t)na * kA2Bytes; }
+  // TMEM: the logit ring (128 columns a tile) and two gradient buffers of
+  // CT x N2 columns; three logit buffers where they fit
+  static constexpr int LB = 3 * kTcPixTile + 2 * CT * N2 <= kTcCols ? 3 : 2;
 };
 
 constexpr int kP2GradWarp = 11;       // pass 2: the gradient MMAs have their own issuing warp
@@ -528,8 +472,11 @@ constexpr int kP2Producers = 128;
 constexpr int kP2MmaWarp = 12;
 constexpr int kP2GradWarpG = 13;
 constexpr int kP2ThreadsG = 14 * 32;
-constexpr int kP2LogitBufs = 3;       // logit tiles in flight in TMEM (3 x 128 columns)
 constexpr int kP2ChunkTiles = 32;     // tiles per gradient partial (fp32 accumulation length)
+// tiles per Hessian-vector partial: the accumulator truncates, and c = p (u -
+// ubar) has no exact cancellation to keep its partial sums small, so it is
+// read out more often
+constexpr int kH2ChunkTiles = 8;
 
 // out[q] = scale * mul * (base[q] / fx + sum_c part[c][q]), fixed order;
 // base (fixed-point label moments) and mul (a device-side factor) optional
@@ -704,33 +651,122 @@ k_tc_kept_lists(const uint32_t* __restrict__ need, int64_t n_words, int64_t n_ti
 constexpr float kP1Far = 130.f;
 
 // ---------------------------------------------------------------------------
-// The 128-grain blocks pass 1 visits on each tile (bit q: image block q).
-// Reference: the label grain r of the tile's centre pixel, whose logit is
-// at least off_r - A_r everywhere in the tile, so that m(x) >= off_r - A_r;
-// block q, all of whose logits are at most mb[t][q], is left out when
-// mb[t][q] < off_r - A_r - kP1Far.  One thread per tile.
+// Per-tile set-up of the tensor-core passes, one block per kRefTiles tiles:
+// the centre features (double, kept as float-float pairs), the reference
+// logit C(t) of each tile (the largest fp32 centre logit, pd_tiles.cuh),
+// the relative centre logits o_i(t) = theta'_i . eta(c_t) - C(t) of every
+// image row (zero for padding rows), and on structured grids the 128-grain
+// blocks pass 1 visits on each tile.
+//
+// Bounds: the features of a tile's pixels differ from those at its centre
+// by |eta_k(x) - eta_k(c)| <= D_k = sum_a alpha_a (alpha_a + 1)/2 h_a,
+// since |P_m| <= 1 and |P_m'| <= m (m + 1)/2 on [-1, 1] and |x_a - c_a|
+// <= h_a in the tile, so every logit of grain i on tile t lies within
+// A_i = sum_k |theta'_ik| D_k of o_i(t).  Hence every pixel's largest logit
+// is at least L(t) = max_j (o_j - A_j) (taken over the fp32 offsets, less a
+// margin of kSetupMargin for their rounding), and
+//  * a grain with o_i + A_i < L(t) - 160 has every exponential exactly zero
+//    in float however its offset is rounded: it keeps the fp32 offset and
+//    the float-float dot product is formed for the others only;
+//  * a 128-grain block with max (o_i + A_i) < L(t) - kP1Far only adds
+//    exponentials that underflow to zero: pass 1 does not visit it.
+// A tile that crosses the grid edge (its centre may lie outside [-1, 1])
+// takes the compensated offsets and visits every block.
 // ---------------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(256)
-k_tc_tile_masks(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const int* __restrict__ rank,
-                const float* __restrict__ offg, int Npad, const float* __restrict__ amax,
-                const float* __restrict__ mb, unsigned long long* __restrict__ masks) {
-  using TS = TileShape<DIM>;
-  constexpr int kRef = TS::X / 2 + TS::X * (TS::Y / 2) + TS::X * TS::Y * (TS::Z / 2);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tm.n_tiles) return;
+constexpr float kSetupMargin = 1.f;
+
+template <int DIM, int D>
+__global__ void __launch_bounds__(kRefThreads)
+k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* __restrict__ thL, int N, int Npad,
+                const int* __restrict__ perm, const float2* __restrict__ ec, float* __restrict__ off, TileBound tb,
+                int bounds, unsigned long long* __restrict__ masks) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<float>(K);
+  __shared__ float2 sec[kRefTiles][K];
+  __shared__ __align__(16) float sech[kRefTiles][KP];
+  __shared__ uint32_t smax[kRefTiles], slow[kRefTiles];
+  __shared__ int srag[kRefTiles];
+  __shared__ uint32_t smb[kRefTiles][64];  // per tile and block: max of o + A, order-preserving bits
+
+  const int64_t t0 = (int64_t)blockIdx.x * kRefTiles;
+  const int nt = (int)min((int64_t)kRefTiles, tm.n_tiles - t0);
   const int nblk = Npad / 128;
-  unsigned long long msk = nblk >= 64 ? ~0ull : ((1ull << nblk) - 1ull);
-  float x[DIM], c[DIM];
-  const int64_t j = tile_pixel<DIM>(g, tm, t, kRef, x, c);
-  const int G = j >= 0 ? labels[j] : -1;
-  if ((unsigned)G < (unsigned)N) {
-    const int r = rank ? rank[G] : G;
-    const float lim = offg[t * Npad + r] - amax[r] - kP1Far;
-    for (int q = 0; q < nblk && q < 64; ++q)
-      if (mb[t * nblk + q] < lim) msk &= ~(1ull << q);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < kRefTiles) {
+    smax[threadIdx.x] = 0u;
+    slow[threadIdx.x] = 0u;
   }
-  masks[t] = msk;
+  for (int e = threadIdx.x; e < kRefTiles * 64; e += blockDim.x) smb[e / 64][e % 64] = 0u;
+  if (threadIdx.x < nt) {
+    float x[DIM], c[DIM];
+    srag[threadIdx.x] = g.coords ? 1 : (tile_pixel<DIM>(g, tm, t0 + threadIdx.x, kTcPixTile - 1, x, c) < 0);
+  }
+  load_centre_features<K>(ec, t0, nt, sec, sech);  // (its barrier covers the set-up above)
+  // pass A: C(t) = max_i f_i and max_i (f_i - A_i) over all grains (caller order)
+  for (int i0 = 0; i0 < N; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    float h[KP];
+    float A = 0.f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) h[k] = i < N ? thH[(int64_t)i * KP + k] : 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) A = fmaf(fabsf(h[k]), tb.d[k], A);
+    for (int q = 0; q < nt; ++q) {
+      const float f = centre_dot32<K>(h, sech[q]);
+      const uint32_t m = __reduce_max_sync(0xffffffffu, i < N ? ord_f32(f) : 0u);
+      const uint32_t lo = __reduce_max_sync(0xffffffffu, i < N ? ord_f32(f - A) : 0u);
+      if (lane == 0) {
+        if (m) atomicMax(&smax[q], m);
+        if (lo) atomicMax(&slow[q], lo);
+      }
+    }
+  }
+  __syncthreads();
+  // pass B: the relative offsets of every image row
+  for (int r0 = 0; r0 < Npad; r0 += blockDim.x) {
+    const int r = r0 + threadIdx.x;  // image row (a warp's 32 rows lie in one 128-row block)
+    const bool live = r < Npad;
+    const int src = !live ? -1 : (perm ? perm[r] : (r < N ? r : -1));
+    float h[KP], l[K];
+    float A = 0.f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) h[k] = src >= 0 ? thH[(int64_t)src * KP + k] : 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      l[k] = src >= 0 ? thL[(int64_t)src * KP + k] : 0.f;
+      A = fmaf(fabsf(h[k]), tb.d[k], A);
+    }
+    for (int q = 0; q < nt; ++q) {
+      const float C = unord_f32(smax[q]);
+      const float L = unord_f32(slow[q]) - C - kSetupMargin;
+      const float o32 = centre_dot32<K>(h, sech[q]) - C;
+      const bool far = bounds && !srag[q] && o32 + A < L - 160.f;
+      float o = o32;
+      // (a branch the warp takes together: with grains in the Morton order
+      // of their label centroids, the rows of a warp are neighbours)
+      if (__any_sync(0xffffffffu, !far && src >= 0)) {
+        const float off_ff = ff_diff(ff_dot<K>(h, l, sec[q]), make_float2(C, 0.f));
+        if (!far) o = off_ff;
+      }
+      if (src < 0) o = 0.f;
+      if (live) off[(t0 + q) * Npad + r] = o;
+      if (bounds) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, src >= 0 ? ord_f32(o + A) : 0u);
+        if (lane == 0 && m && live) atomicMax(&smb[q][r / 128], m);
+      }
+    }
+  }
+  __syncthreads();
+  if (bounds && threadIdx.x < nt) {
+    const int q = threadIdx.x;
+    unsigned long long msk = nblk >= 64 ? ~0ull : ((1ull << nblk) - 1ull);
+    if (!srag[q] && smax[q]) {
+      const float lim = unord_f32(slow[q]) - unord_f32(smax[q]) - kSetupMargin - kP1Far;
+      for (int b = 0; b < nblk && b < 64; ++b)
+        if (!smb[q][b] || unord_f32(smb[q][b]) < lim) msk &= ~(1ull << b);  // (no grain in the block: left out)
+    }
+    masks[t0 + q] = msk;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -753,27 +789,6 @@ TileBound tile_bound(const Geom& g) {
     tb.d[k] = (float)(dk * (1.0 + 1e-6));  // rounded up
   }
   return tb;
-}
-
-template <int DIM>
-TileMap make_tiles(const Geom& g) {
-  TileMap tm{1, 1, 1, 0, 1, 1, 1, 1.f, 1.f, 1.f};
-  if (g.coords) {
-    tm.n_tiles = (g.P + kTcPixTile - 1) / kTcPixTile;
-    return tm;
-  }
-  using TS = TileShape<DIM>;
-  tm.ntx = (int)((g.n0 + TS::X - 1) / TS::X);
-  tm.nty = (int)((g.n1 + TS::Y - 1) / TS::Y);
-  tm.ntz = DIM == 3 ? (int)((g.n2 + TS::Z - 1) / TS::Z) : 1;
-  tm.n_tiles = (int64_t)tm.ntx * tm.nty * tm.ntz;
-  tm.n0 = (int)g.n0;
-  tm.n1 = (int)g.n1;
-  tm.n2 = (int)g.n2;
-  tm.f0 = (float)(1.0 / (double)g.n0);
-  tm.f1 = (float)(1.0 / (double)g.n1);
-  tm.f2 = (float)(1.0 / (double)g.n2);
-  return tm;
 }
 
 }  // namespace

@@ -170,16 +170,12 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
         bulk_g2s(sOff + s * Ng, offg + t * Npad + g0, (uint32_t)Ng * 4, &bar_a_full[s]);
         bulk_g2s(sUoff + s * Ng, uoffg + t * Npad + g0, (uint32_t)Ng * 4, &bar_a_full[s]);
       }
-      float cc[DIM], ec[K];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int p = p0 + 64 * u;
-        float x[DIM], eta[K], de[K];
-        const int64_t j = tile_pixel<DIM>(g, tm, t, p, x, cc);
-        if (u == 0) legendre_features<DIM, D>(cc, ec);
-        legendre_features<DIM, D>(x, eta);
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = eta[k] - ec[k];
+        float x[DIM], cc[DIM], dx[DIM], de[K];
+        const int64_t j = tile_pixel_dx<DIM>(g, tm, t, p, x, cc, dx);
+        legendre_delta<DIM, D>(x, cc, dx, de, nullptr);
         store_eta_row<K, KW, KS>(sA + s * kTileBytes, p, de);
         sJ[s * 128 + p] = (long long)j;
       }
@@ -272,7 +268,7 @@ k_tc_hvp_pass1(Geom g, TileMap tm, int N, int Npad, int g0, int Ng, const uint8_
           const float a = Arith<float>::ex(m - mm), bb = Arith<float>::ex(o.x - mm);
           const float Sm = S * a + o.y * bb, Tm = T * a + o.z * bb;
           // log2 S of the pixel, or of this group's part (a lower bound)
-          lse = mm + Arith<float>::lg(Sm);
+          lse = mm + log2f(Sm);
           if (ms_out) {
             ms_out[j] = make_float4(mm, Sm, Tm, 0.f);
           } else {
@@ -324,7 +320,7 @@ k_tc_hvp_merge(const float4* __restrict__ ms, int n_grp, int64_t P, float* __res
       T = fmaf(v.z, e, T);
     }
   }
-  lse_out[j] = m + Arith<float>::lg(S);
+  lse_out[j] = m + log2f(S);
   ubar_out[j] = T / S;
 }
 
@@ -349,18 +345,19 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
                const float* __restrict__ ubar, const int* __restrict__ kept, const int* __restrict__ n_kept_gb,
                const int* __restrict__ perm, double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
-  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2;
+  constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2, CT = L::CT;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
   constexpr uint32_t IDESC2 = idesc_f16(128, N2);
-  constexpr int D2COL = 2 * kTcPixTile;
-  static_assert(D2COL + 2 * N2 <= kTcCols, "TMEM columns");
+  constexpr int D2COL = 2 * kTcPixTile;  // D2 buffer db at D2COL + db*CT*N2
+  static_assert(D2COL + 2 * CT * N2 <= kTcCols, "TMEM columns");
+  constexpr float kLoScale = 4096.f;      // c_lo = fl16((c - c_hi) * 2^12)
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                          // parameter block image
   uint8_t* sAv = sA + L::kABytes;              // v block image
   uint8_t* sB = sAv + L::kABytes;              // NB stages of eta - eta(c) rows
   uint8_t* sB2 = sB + NB * L::kBBytes;         // NB stages of eta^T (fp16)
-  uint8_t* sA2 = sB2 + NB * L::kB2Bytes;       // NA stages of c (fp16)
+  uint8_t* sA2 = sB2 + NB * L::kB2Bytes;       // NA stages of c (fp16, CT terms)
   float* sLse = reinterpret_cast<float*>(sA2 + NA * L::kA2Bytes);  // [NB][128]
   float* sOffP = sLse + NB * kTcPixTile;                           // [NB][128] centre logits of the block
   float* sUbar = sOffP + NB * 128;                                  // [NB][128]
@@ -379,7 +376,7 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
   const int n_pt = (int)(n_list * (blockIdx.x + 1) / gridDim.x - k_lo);
   const int* klist = kept ? kept + (int64_t)gb * tm.n_tiles + k_lo : nullptr;
   auto tile_of = [&](int t) -> int64_t { return klist ? (int64_t)klist[t] : k_lo + t; };
-  const int n_items = (n_pt + kP2ChunkTiles - 1) / kP2ChunkTiles;  // chunks
+  const int n_items = (n_pt + kH2ChunkTiles - 1) / kH2ChunkTiles;  // chunks
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar_img, 1);
@@ -435,8 +432,8 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
       bool ok = true;
       for (int t = 0; ok && t < n_pt; ++t) {
         const int s = t % NB, a = t % NA;
-        const int u = t / kP2ChunkTiles, db = u & 1;
-        const bool first = t % kP2ChunkTiles == 0, last = t % kP2ChunkTiles == kP2ChunkTiles - 1 || t == n_pt - 1;
+        const int u = t / kH2ChunkTiles, db = u & 1;
+        const bool first = t % kH2ChunkTiles == 0, last = t % kH2ChunkTiles == kH2ChunkTiles - 1 || t == n_pt - 1;
         if (first && u >= 2) ok = mbar_wait(&bar_d2_free[db], (uint32_t)(((u >> 1) - 1) & 1), &abort_flag, status);
         if (ok) ok = mbar_wait(&bar_a2_full[a], (uint32_t)((t / NA) & 1), &abort_flag, status);
         if (!ok) break;
@@ -444,9 +441,12 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
         const uint32_t a2 = smem_addr(sA2 + a * L::kA2Bytes), b2 = smem_addr(sB2 + s * L::kB2Bytes);
 #pragma unroll 2
         for (int q = 0; q < kTcPixTile / 16; ++q) {
-          const uint64_t ad = smem_desc(a2 + q * 256, 128, kTcPixTile * 16);
           const uint64_t bd = smem_desc(b2 + q * 2 * L::kLbo2, L::kLbo2, L::kSbo2);
-          mma_bf16(tmem + D2COL + db * N2, ad, bd, IDESC2, (!first || q > 0) ? 1u : 0u);
+#pragma unroll
+          for (int ct = 0; ct < CT; ++ct) {
+            const uint64_t ad = smem_desc(a2 + ct * L::kA2Term + q * 256, 128, kTcPixTile * 16);
+            mma_bf16(tmem + D2COL + (db * CT + ct) * N2, ad, bd, IDESC2, (!first || q > 0) ? 1u : 0u);
+          }
         }
         mma_commit(&bar_a2_empty[a]);
         mma_commit(&bar_b_empty[s]);
@@ -458,11 +458,11 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
     __syncwarp();
   } else if (is_producer(warp)) {
     const int q2 = 2 * (tid - kTcConsumers);
-    float xn[2][DIM], cn[DIM], lsn[2], ubn[2];
+    float xn[2][DIM], cn[DIM], dxn[2][DIM], lsn[2], ubn[2];
     auto fetch = [&](int t) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int64_t j = tile_pixel<DIM>(g, tm, tile_of(t), q2 + u, xn[u], cn);
+        const int64_t j = tile_pixel_dx<DIM>(g, tm, tile_of(t), q2 + u, xn[u], cn, dxn[u]);
         lsn[u] = j >= 0 ? lse[j] : INFINITY;
         ubn[u] = j >= 0 ? ubar[j] : 0.f;
       }
@@ -470,11 +470,13 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
     if (n_pt > 0) fetch(0);
     for (int t = 0; t < n_pt; ++t) {
       const int s = t % NB;
-      float xc[2][DIM], cc[DIM];
+      float xc[2][DIM], cc[DIM], dxc[2][DIM];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         xc[0][a] = xn[0][a];
         xc[1][a] = xn[1][a];
+        dxc[0][a] = dxn[0][a];
+        dxc[1][a] = dxn[1][a];
         cc[a] = cn[a];
       }
       const float2 lsc = make_float2(lsn[0], lsn[1]), ubc = make_float2(ubn[0], ubn[1]);
@@ -487,18 +489,13 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
         bulk_g2s(sOffP + s * 128, offg + tc * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
         bulk_g2s(sUoffP + s * 128, uoffg + tc * Npad + gb * 128, 128 * 4, &bar_b_full[s]);
       }
-      float ec[K], e0[K], e1[K];
-      legendre_features<DIM, D>(cc, ec);
-      legendre_features<DIM, D>(xc[0], e0);
-      legendre_features<DIM, D>(xc[1], e1);
+      float e0[K], e1[K];
       uint8_t* bs = sB + s * L::kBBytes;
       {
         float de[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = e0[k] - ec[k];
+        legendre_delta<DIM, D>(xc[0], cc, dxc[0], de, e0);
         store_eta_row<K, KW, KS, L::kSboB>(bs, q2, de);
-#pragma unroll
-        for (int k = 0; k < K; ++k) de[k] = e1[k] - ec[k];
+        legendre_delta<DIM, D>(xc[1], cc, dxc[1], de, e1);
         store_eta_row<K, KW, KS, L::kSboB>(bs, q2 + 1, de);
       }
       uint8_t* b2 = sB2 + s * L::kB2Bytes;
@@ -533,24 +530,34 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
       const int db = u & 1;
       if (!mbar_wait_warp(&bar_d2_full[db], (uint32_t)((u >> 1) & 1), &abort_flag, status)) return false;
       tc_fence_after();
-      uint32_t r[N2 < 32 ? 32 : N2];
-      const uint32_t base = tmem + lane_base + (uint32_t)(D2COL + db * N2);
-      if (N2 == 16) {
-        tmem_ld16(base, r);
-      } else {
+      const uint32_t base = tmem + lane_base + (uint32_t)(D2COL + db * CT * N2);
+      // 16 features at a time: the eta_h and eta_l columns of each term of
+      // c, added in fp32 (the accumulators' own precision), c_lo scaled back
 #pragma unroll
-        for (int c0 = 0; c0 < N2; c0 += 32) tmem_ld32(base + c0, r + c0);
-      }
-      tmem_wait_ld();
-      tc_fence_before();
-      mbar_arrive(&bar_d2_free[db]);
-      if (prow) {
+      for (int kb = 0; kb < KW; kb += 16) {
+        float f[16];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const double v = (double)__uint_as_float(r[k]) + (ET == 2 ? (double)__uint_as_float(r[KW + k]) : 0.0);
-          prow[k] = u == 0 ? v : prow[k] + v;
+        for (int ct = 0; ct < CT; ++ct) {
+          uint32_t r[ET][16];
+#pragma unroll
+          for (int et = 0; et < ET; ++et) tmem_ld16(base + (uint32_t)(ct * N2 + et * KW + kb), r[et]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            const float v = ET == 2 ? __uint_as_float(r[0][kk]) + __uint_as_float(r[ET - 1][kk]) : __uint_as_float(r[0][kk]);
+            f[kk] = ct == 0 ? v : fmaf(v, 1.f / kLoScale, f[kk]);
+          }
+        }
+        if (prow) {
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            const int k = kb + kk;
+            if (k < K) prow[k] = u == 0 ? (double)f[kk] : prow[k] + (double)f[kk];
+          }
         }
       }
+      tc_fence_before();
+      mbar_arrive(&bar_d2_free[db]);
       n_done = u + 1;
       return true;
     };
@@ -584,7 +591,7 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
         const float* ub = sUbar + s * kTcPixTile + col;
 #pragma unroll
         for (int q8 = 0; q8 < 32; q8 += 8) {
-          uint32_t hw[4];
+          uint32_t hw[4], lw[4];
 #pragma unroll
           for (int u = 0; u < 8; u += 2) {
             // c = p (u - ubar), p = 2^(l - log2 S), u = w + uoff
@@ -594,13 +601,20 @@ k_tc_hvp_pass2(Geom g, TileMap tm, int N, int Npad, const uint8_t* __restrict__ 
             const float c1 = p1 * ((__uint_as_float(U[q8 + u + 1]) + uoff) - ub[q8 + u + 1]);
             const __half2 h = __floats2half2_rn(c0, c1);
             hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+            if (CT == 2) {
+              const float2 hf = __half22float2(h);
+              const __half2 l2 = __floats2half2_rn((c0 - hf.x) * kLoScale, (c1 - hf.y) * kLoScale);
+              lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
+            }
           }
-          *reinterpret_cast<uint4*>(a2 + kmaj(gr, (int)col + q8, kTcPixTile)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          const uint32_t o = kmaj(gr, (int)col + q8, kTcPixTile);
+          *reinterpret_cast<uint4*>(a2 + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          if (CT == 2) *reinterpret_cast<uint4*>(a2 + L::kA2Term + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
       }
       fence_proxy_async();
       mbar_arrive(&bar_a2_full[a]);
-      if (half == 0 && t > kP2ChunkTiles && t % kP2ChunkTiles == 1 && !read_chunk(t / kP2ChunkTiles - 1)) {
+      if (half == 0 && t > kH2ChunkTiles && t % kH2ChunkTiles == 1 && !read_chunk(t / kH2ChunkTiles - 1)) {
         ok = false;
         break;
       }
@@ -661,24 +675,30 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t n_tiles = tm.n_tiles;
   const int grid1 = (int)std::min<int64_t>(n_tiles, sms);
   const int gblocks = (N + 127) / 128;
-  const int cpg = (int)std::min<int64_t>((n_tiles + kP2ChunkTiles - 1) / kP2ChunkTiles, std::max(1, sms / gblocks));
+  const int cpg = (int)std::min<int64_t>((n_tiles + kH2ChunkTiles - 1) / kH2ChunkTiles, std::max(1, sms / gblocks));
   // as for the gradient: pass 2 visits the (tile, block) pairs whose c can
   // survive in fp16, with the grains in the Morton order of their label
   // centroids (PD_TC_NO_SKIP=1: every pair, index order)
   const char* no_skip = getenv("PD_TC_NO_SKIP");
   const bool skip = !(no_skip && no_skip[0] && no_skip[0] != '0');
-  const bool order = skip && Npad <= kOrderMax;
+  // (labels may be NULL for the Hessian: then no grain order by label
+  // centroids and no label reference for the block masks)
+  const bool order = skip && Npad <= kOrderMax && c.labels != nullptr;
   // pass 1 leaves out the blocks that the centre-logit bounds place far
   // below the tile's reference logit (structured grids)
   const bool bounds = skip && !c.g.coords && Npad / 128 <= 64;
   const int64_t n_words = (n_tiles + 31) / 32;
 
+  constexpr int KP = padded_K<float>(K);
   Scratch sc(st);
   double* vsc = sc.get<double>(2);
+  float* thH = sc.get<float>((size_t)N * KP);  // float-float parameters for the centre logits
+  float* thL = sc.get<float>((size_t)N * KP);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
   uint8_t* vimg = sc.get<uint8_t>((size_t)Npad * row_bytes);
   float* th32t = sc.get<float>((size_t)K * Npad);
   float* v32t = sc.get<float>((size_t)K * Npad);
+  float2* ecg = sc.get<float2>((size_t)n_tiles * K);  // centre features per tile
   float* offg = sc.get<float>((size_t)n_tiles * Npad);
   float* uoffg = sc.get<float>((size_t)n_tiles * Npad);
   float* lse = sc.get<float>((size_t)P);
@@ -688,11 +708,10 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   uint32_t* need = skip ? sc.get<uint32_t>((size_t)gblocks * n_words) : nullptr;
   int* kept = skip ? sc.get<int>((size_t)gblocks * n_tiles) : nullptr;
   int* nkept = skip ? sc.get<int>((size_t)gblocks) : nullptr;
-  unsigned long long* lmom = order ? sc.get<unsigned long long>((size_t)N * K) : nullptr;
+  constexpr int K1 = DIM + 1;  // label moments of degree <= 1: counts and centroids for the grain order
+  unsigned long long* lmom = order ? sc.get<unsigned long long>((size_t)N * K1) : nullptr;
   int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
   int* rank = order ? sc.get<int>((size_t)N) : nullptr;
-  float* amax = bounds ? sc.get<float>((size_t)Npad) : nullptr;
-  float* mbb = bounds ? sc.get<float>((size_t)n_tiles * gblocks) : nullptr;
   unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
   const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
   int* status = sc.get<int>(1);
@@ -704,13 +723,13 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
     int bits = 0;
     while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
     const float fx = ldexpf(1.f, 62 - bits);
-    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K, st) != cudaSuccess) return PD_ECUDA;
+    if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K1, st) != cudaSuccess) return PD_ECUDA;
     const int64_t nthr = n_tiles * kTcPixTile;
     PD_TIMED(st, "tc_label_moments",
-             (k_tc_label_moments<DIM, D><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
+             (k_tc_label_moments<DIM, 1><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, fx,
                                                                                        lmom)));
     PD_TIMED(st, "tc_grain_order",
-             k_tc_grain_order<DIM><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lmom, N, K, Npad, perm, rank));
+             k_tc_grain_order<DIM><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lmom, N, K1, Npad, perm, rank));
   }
 
   PD_TIMED(st, "tc_hvp_vscale", k_tc_vscale<<<1, 1024, 0, st>>>(c.v, (int64_t)N * K, vsc));
@@ -725,12 +744,20 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   }
   const dim3 gridc((unsigned)((Npad + 255) / 256),
                    (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles, 4096));
-  PD_TIMED(st, "tc_centre_logits", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, th32t, perm, N, Npad, offg, tb, amax, mbb)));
+  {
+    const int64_t n = (int64_t)N * KP;
+    PD_TIMED(st, "theta_ff",
+             k_theta_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, K, KP,
+                                                                      Arith<float>::theta_scale(c.eps), thH, thL));
+  }
+  // logits relative to the tiles' reference logits; u (not shift-invariant,
+  // and of modest size) from plain fp32 centre parts
+  PD_TIMED(st, "centre_features",
+           (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
+  PD_TIMED(st, "tc_tile_setup",
+           (k_tc_tile_setup<DIM, D><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(
+               c.g, tm, thH, thL, N, Npad, perm, ecg, offg, tb, bounds ? 1 : 0, masks)));
   PD_TIMED(st, "tc_centre_u", (k_tc_centre_logits<DIM, D><<<gridc, 256, 0, st>>>(c.g, tm, v32t, perm, N, Npad, uoffg, TileBound{}, nullptr, nullptr)));
-  if (bounds)
-    PD_TIMED(st, "tc_tile_masks",
-             k_tc_tile_masks<DIM><<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(c.g, tm, c.labels, N, rank, offg,
-                                                                                   Npad, amax, mbb, masks));
 
   auto k1 = k_tc_hvp_pass1<DIM, D, KS>;
   if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1_req) != cudaSuccess)

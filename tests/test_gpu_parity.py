@@ -3,9 +3,11 @@
 Tolerances (derived from the arithmetic):
   FP64 mode: Phi within 1e-10 relative; gradient and Hessian-vector
              product within 1e-10 in ||.||_2 relative to the oracle's norm.
-  FP32 mode: logits carry float rounding of about K * 2^-24 * |logit|
-             (|logit| ~ |theta|/eps); Phi within 1e-5 relative and the
-             gradient within 1e-4 relative (norm) at the sizes tested.
+  FP32 mode: every logit of a 128-pixel tile is kept relative to the
+             tile's reference logit (centre parts in float-float, rounded
+             once), so the float quantities are small; Phi and the gradient
+             (and the Hessian-vector product) within 1e-5 relative (norm),
+             the bound the method's reduced-precision form is held to.
   labels:    bit-exact wherever the oracle's top-two gap is >= 1e-9.
 """
 import math
@@ -68,8 +70,9 @@ def test_objective_grad_fp32(shape, N, d, eps, scale):
     th = synth.random_theta(14, N, O.K(len(shape), d), scale)
     phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
     phi, grad = gpu_eval(shape, lab, N, th, d, eps, pd.PD_FP32)
+    print("fp32 %s N=%d d=%d: phi %.2e grad %.2e" % (shape, N, d, abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o)))
     assert abs(phi - phi_o) <= 1e-5 * abs(phi_o)
-    assert rel(grad, grad_o) <= 1e-4
+    assert rel(grad, grad_o) <= 1e-5
 
 
 def test_fully_ambiguous_exact():
@@ -116,8 +119,9 @@ def test_hvp(shape, N, d, eps, scale):
     v = synth.random_theta(17, N, K, 1.0)
     hv_o = O.hvp(g, lab, N, d, eps, th, v)
     grid = pd.Grid(shape)
-    for prec, tol in ((pd.PD_FP64, 1e-10), (pd.PD_FP32, 1e-4)):
+    for prec, tol in ((pd.PD_FP64, 1e-10), (pd.PD_FP32, 1e-5)):
         hv = pd.pd_hvp(grid, dev(lab), N, dev(th), dev(v), d, eps, prec=prec).cpu().numpy()
+        print("hvp prec %d %s: %.2e" % (prec, shape, rel(hv, hv_o)))
         assert rel(hv, hv_o) <= tol, (prec, rel(hv, hv_o))
 
 
@@ -215,4 +219,4 @@ def test_config2_full_size_fp32_and_fp64():
     phi32, grad32 = gpu_eval(shape, lab, N, th, d, eps, pd.PD_FP32)
     print("config2 fp32 rel err: phi %.3e grad %.3e" % (abs(phi32 - phi_o) / abs(phi_o), rel(grad32, grad_o)))
     assert abs(phi32 - phi_o) <= 1e-5 * abs(phi_o)
-    assert rel(grad32, grad_o) <= 1e-3
+    assert rel(grad32, grad_o) <= 1e-5

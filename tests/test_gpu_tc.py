@@ -1,9 +1,11 @@
 """Parity of the tensor-core (tcgen05) evaluation with the FP64 oracle.
 
 PD_BF16X3 splits the logit operands into three bf16 terms (about 24
-significant bits) and contracts the gradient with fp16 c against fp16
-hi + lo features: it must meet the FP32 tolerances (Phi 1e-5 relative,
-gradient 1e-4 in norm).
+significant bits), keeps every logit relative to its tile's reference logit,
+and contracts the gradient with c = delta - p in two fp16 terms (hi, and
+the remainder scaled by 2^12) against fp16 hi + lo features: it must meet
+the FP32 tolerances (Phi, gradient and Hessian-vector product within 1e-5
+relative).
 PD_BF16 rounds every operand to bf16 (8 significant bits): its logit error
 is about |theta| / eps * 2^-9, so it is checked at a loose bound scaled to
 that, and its error is reported by the benchmark.
@@ -49,8 +51,9 @@ def test_bf16x3_matches_oracle(shape, N, d, eps, scale):
     th = synth.random_theta(32, N, O.K(len(shape), d), scale)
     phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
     phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    print("bf16x3 %s N=%d d=%d: phi %.2e grad %.2e" % (shape, N, d, abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o)))
     assert abs(phi - phi_o) <= 1e-5 * abs(phi_o), (phi, phi_o)
-    assert rel(grad, grad_o) <= 1e-4, rel(grad, grad_o)
+    assert rel(grad, grad_o) <= 1e-5, rel(grad, grad_o)
 
 
 @pytest.mark.parametrize("shape,N,d,eps,scale", CASES)
@@ -108,9 +111,15 @@ def test_tc_skip_structured(shape, N, d, eps, monkeypatch):
     print("skip %s N=%d: phi %.2e grad %.2e vs oracle; vs all pairs: phi %.2e grad %.2e of the label part"
           % (shape, N, abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o), abs(phi - phi_a) / abs(phi_a), dgrad))
     # Phi of a sharp fit is near zero: its error is measured on the scale of
-    # the log-sum-exp, O(1)
+    # the log-sum-exp, O(1).  The tensor cores accumulate the logits'
+    # remainders theta'.(eta(x) - eta(c)) with truncation, an error of about
+    # 2^-23 A per logit for remainders up to A = sum_k |theta'_k| D_k: on the
+    # 40 x 36 x 30 grid at eps = 2e-3 a tile spans a fifth of the x-axis and
+    # A reaches about 600 (against 70 at 1024^2, eps = 1e-3), which the
+    # gradient bound of that case reflects
+    tol = 2e-5 if len(shape) == 3 else 1e-5
     assert abs(phi - phi_o) <= 1e-5 * max(1.0, abs(phi_o)), (phi, phi_o)
-    assert rel(grad, grad_o) <= 2e-3, rel(grad, grad_o)
+    assert rel(grad, grad_o) <= tol, rel(grad, grad_o)
     assert abs(phi - phi_a) <= 1e-6 * max(1.0, abs(phi_a))
     assert dgrad <= 2e-5, dgrad
     # deterministic
@@ -126,8 +135,8 @@ def test_tc_skip_structured(shape, N, d, eps, monkeypatch):
     hv_a = pd.pd_hvp(pd.Grid(shape), dev(lab), N, dev(th), dev(v), d, eps, prec=pd.PD_BF16X3).cpu().numpy()
     monkeypatch.delenv("PD_TC_NO_SKIP")
     print("skip %s N=%d: hvp %.2e vs oracle, %.2e vs all pairs" % (shape, N, rel(hv, hv_o), rel(hv, hv_a)))
-    assert rel(hv, hv_o) <= 1e-3, rel(hv, hv_o)
-    assert rel(hv, hv_a) <= 2e-5, rel(hv, hv_a)
+    assert rel(hv, hv_o) <= 1e-5, rel(hv, hv_o)
+    assert rel(hv, hv_a) <= 1e-5, rel(hv, hv_a)
 
 
 def test_tc_unsupported_shapes():
@@ -156,8 +165,9 @@ def test_tc_grain_groups(N, d):
     th = synth.random_theta(38, N, K, 0.02)
     phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
     phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
+    print("groups N=%d d=%d: phi %.2e grad %.2e" % (N, d, abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o)))
     assert abs(phi - phi_o) <= 1e-5 * abs(phi_o), (phi, phi_o)
-    assert rel(grad, grad_o) <= 1e-4, rel(grad, grad_o)
+    assert rel(grad, grad_o) <= 1e-5, rel(grad, grad_o)
 
 
 HVP_CASES = [
@@ -183,7 +193,7 @@ def test_bf16x3_hvp_matches_oracle(shape, N, d, eps, scale):
     hv = pd.pd_hvp(pd.Grid(shape), dev(lab), N, dev(th), dev(v), d, eps, prec=pd.PD_BF16X3)
     err = rel(hv.cpu().numpy(), hv_o)
     print("hvp bf16x3 %s N=%d d=%d: rel err %.2e" % (shape, N, d, err))
-    assert err <= 1e-3, err
+    assert err <= 1e-5, err
 
 
 @pytest.mark.slow
@@ -194,6 +204,6 @@ def test_config2_full_size_bf16x3():
     phi, grad = run(shape, lab, N, th, d, eps, pd.PD_BF16X3)
     print("config2 bf16x3 rel err: phi %.3e grad %.3e" % (abs(phi - phi_o) / abs(phi_o), rel(grad, grad_o)))
     assert abs(phi - phi_o) <= 1e-5 * abs(phi_o)
-    assert rel(grad, grad_o) <= 1e-3
+    assert rel(grad, grad_o) <= 1e-5
     phi16, grad16 = run(shape, lab, N, th, d, eps, pd.PD_BF16)
     print("config2 bf16 rel err: phi %.3e grad %.3e" % (abs(phi16 - phi_o) / abs(phi_o), rel(grad16, grad_o)))
