@@ -97,6 +97,10 @@ def _load():
             lib.or_newton_cg_fit.argtypes = [gp, ip, C.c_int, C.c_int, C.c_double, dp,
                                              C.c_int, C.c_int, C.c_double, dp,
                                              C.POINTER(FitReport)]
+            lib.or_theta_to_apd.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, dp, dp, dp, dp]
+            lib.or_anneal_fit.argtypes = [gp, ip, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                          C.c_int, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp, dp, dp,
+                                          C.POINTER(C.c_int)]
             lib.or_mlp_forward.argtypes = [C.c_int] * 5 + [dp] * 8
             lib.or_mlp_loss_grad.argtypes = [C.c_int] * 5 + [dp] * 14
             lib.or_mlp_loss_grad.restype = C.c_double
@@ -312,6 +316,41 @@ def newton_cg_fit(grid: Grid, labels, N: int, d: int, eps: float, theta0,
                                   _dp(trace), C.byref(rep))
     assert rc == 0
     return th, rep, trace[:rep.iters]
+
+
+def theta_to_apd(dim: int, d: int, theta, margin: float = 1e-3):
+    """Legendre theta (d = 1 or 2) -> physical parameters (y, w, A, lambda)
+    by eqs. pd-lr-to-phys / apd-lr-to-phys after the common shift A_i +
+    lambda Id of Sec. 5.5.3 (A is None for d = 1)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    N = th.shape[0]
+    y = np.empty((N, dim))
+    w = np.empty(N)
+    A = np.empty((N, dim, dim)) if d == 2 else None
+    lam = C.c_double(0.0)
+    rc = _load().or_theta_to_apd(dim, d, N, _dp(th), float(margin), _dp(y), _dp(w), _dp(A),
+                                 C.cast(C.pointer(lam), C.POINTER(C.c_double)))
+    if rc != 0:
+        raise ValueError("oracle: bad recovery arguments")
+    return y, w, A, lam.value
+
+
+def anneal_fit(grid: Grid, labels, N: int, d: int, eps0: float, factor: float, eps_min: float,
+               stage_iter: int, final_iter: int, theta0, m: int = 10, err_stop: bool = True,
+               max_stages: int = 64):
+    """eps annealing with Err^G-aligned stopping (the build's reading of the
+    future-work schedule of Secs. 5.2 and 5.5.4).  Returns (theta, stages),
+    stages a list of (eps, Phi, Err^G or -1, iterations)."""
+    lab = _labels(labels)
+    th = np.array(theta0, dtype=np.float64, copy=True, order="C")
+    se, sp, sr = np.zeros(max_stages), np.zeros(max_stages), np.zeros(max_stages)
+    si = np.zeros(max_stages, dtype=np.int32)
+    n = _load().or_anneal_fit(grid.ref, _ip(lab), N, d, float(eps0), float(factor), float(eps_min),
+                              int(stage_iter), int(final_iter), int(m), int(err_stop), _dp(th),
+                              int(max_stages), _dp(se), _dp(sp), _dp(sr),
+                              si.ctypes.data_as(C.POINTER(C.c_int)))
+    assert n > 0
+    return th, [(float(se[k]), float(sp[k]), float(sr[k]), int(si[k])) for k in range(n)]
 
 
 # ---------------------------------------------------------------------------

@@ -925,6 +925,202 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Linear parameters -> physical parameters (Sec. 2.3, eqs. pd-lr-to-phys   */
+/* and apd-lr-to-phys; Sec. 5.5.3).  The Legendre coefficients of degree    */
+/* d in {1, 2} are first written in monomials by solving T theta_L =        */
+/* theta_mono (T of or_mono_to_legendre is triangular: a monomial only      */
+/* involves Legendre products of lower or equal multi-index, so back        */
+/* substitution in the order of A_d solves it).  Then                       */
+/*   d = 1:  y = -theta_x / 2,  w = |theta_x|^2 / 4 - theta_1;              */
+/*   d = 2:  A_aa = theta_{x_a^2},  A_ab = theta_{x_a x_b} / 2,             */
+/*           after the common shift A_i + lambda Id (which changes no cell  */
+/*           boundary: it adds lambda |x|^2 to every h_i, Lemma 4.2),       */
+/*           y = -A^-1 theta_x / 2,  w = theta_x . A^-1 theta_x / 4 -       */
+/*           theta_1,                                                       */
+/* with lambda = max(0, margin - min_i lambda_min(A_i)) so that every      */
+/* shifted A_i has eigenvalues >= margin > 0 (the paper asks for lambda >   */
+/* -min_i lambda_min(A_i)).  Eigenvalues of the symmetric A_i by cyclic      */
+/* Jacobi rotations (textbook).  Outputs y [N][dim], w [N], A [N][dim][dim] */
+/* (d = 2 only) and lambda.                                                 */
+/* ------------------------------------------------------------------------ */
+static double sym_min_eig(int dim, const double* A) {
+  double a[3][3];
+  for (int r = 0; r < dim; ++r)
+    for (int c = 0; c < dim; ++c) a[r][c] = A[r * dim + c];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int r = 0; r < dim; ++r)
+      for (int c = r + 1; c < dim; ++c) off += a[r][c] * a[r][c];
+    if (off == 0.0) break;
+    for (int p = 0; p < dim; ++p)
+      for (int q = p + 1; q < dim; ++q) {
+        if (a[p][q] == 0.0) continue;
+        /* rotation that zeroes a[p][q] */
+        double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < dim; ++k) {
+          double akp = a[k][p], akq = a[k][q];
+          a[k][p] = cs * akp - sn * akq;
+          a[k][q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < dim; ++k) {
+          double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = cs * apk - sn * aqk;
+          a[q][k] = sn * apk + cs * aqk;
+        }
+      }
+  }
+  double m = a[0][0];
+  for (int r = 1; r < dim; ++r) m = a[r][r] < m ? a[r][r] : m;
+  return m;
+}
+
+/* solve M z = b for symmetric positive definite M (dim <= 3) by Gaussian
+ * elimination without pivoting (M is positive definite here) */
+static void spd_solve(int dim, const double* M, const double* b, double* z) {
+  double a[3][4];
+  for (int r = 0; r < dim; ++r) {
+    for (int c = 0; c < dim; ++c) a[r][c] = M[r * dim + c];
+    a[r][dim] = b[r];
+  }
+  for (int k = 0; k < dim; ++k)
+    for (int r = k + 1; r < dim; ++r) {
+      double f = a[r][k] / a[k][k];
+      for (int c = k; c <= dim; ++c) a[r][c] -= f * a[k][c];
+    }
+  for (int r = dim - 1; r >= 0; --r) {
+    double v = a[r][dim];
+    for (int c = r + 1; c < dim; ++c) v -= a[r][c] * z[c];
+    z[r] = v / a[r][r];
+  }
+}
+
+int or_theta_to_apd(int dim, int d, int N, const double* theta, double margin,
+                    double* y, double* w, double* A, double* lambda_out) {
+  if ((dim != 2 && dim != 3) || (d != 1 && d != 2) || N < 1 || !(margin > 0.0)) return -1;
+  int K = or_K(dim, d);
+  double* T = (double*)malloc(sizeof(double) * K * K);
+  double* mono = (double*)malloc(sizeof(double) * N * K);
+  or_mono_to_legendre(dim, d, T);
+  /* back substitution: T is upper triangular in the order of A_d */
+  for (int i = 0; i < N; ++i) {
+    const double* tl = theta + (size_t)i * K;
+    double* tm = mono + (size_t)i * K;
+    for (int b = K - 1; b >= 0; --b) {
+      double v = tl[b];
+      for (int a = b + 1; a < K; ++a) v -= T[b * K + a] * tm[a];
+      tm[b] = v / T[b * K + b];
+    }
+  }
+  int e[3];
+  double lambda = 0.0;
+  if (d == 2) {
+    /* A_i from the quadratic coefficients, then the common shift */
+    double min_eig = INFINITY;
+    for (int i = 0; i < N; ++i) {
+      double* Ai = A + (size_t)i * dim * dim;
+      for (int a = 0; a < dim; ++a)
+        for (int b = a; b < dim; ++b) {
+          for (int q = 0; q < dim; ++q) e[q] = 0;
+          e[a] += 1; e[b] += 1;
+          double c = mono[(size_t)i * K + alpha_index(dim, d, e)];
+          Ai[a * dim + b] = Ai[b * dim + a] = (a == b) ? c : 0.5 * c;
+        }
+      double m = sym_min_eig(dim, Ai);
+      if (m < min_eig) min_eig = m;
+    }
+    lambda = margin - min_eig > 0.0 ? margin - min_eig : 0.0;
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < dim; ++a) A[(size_t)i * dim * dim + a * dim + a] += lambda;
+  }
+  for (int i = 0; i < N; ++i) {
+    double bx[3], z[3];
+    for (int a = 0; a < dim; ++a) {
+      for (int q = 0; q < dim; ++q) e[q] = 0;
+      e[a] = 1;
+      bx[a] = mono[(size_t)i * K + alpha_index(dim, d, e)];
+    }
+    for (int q = 0; q < dim; ++q) e[q] = 0;
+    double t1 = mono[(size_t)i * K + alpha_index(dim, d, e)];
+    if (d == 1) {
+      /* eq. pd-lr-to-phys */
+      double s = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        y[(size_t)i * dim + a] = -0.5 * bx[a];
+        s += 0.25 * bx[a] * bx[a];
+      }
+      w[i] = s - t1;
+    } else {
+      /* eq. apd-lr-to-phys: z = A^-1 b, y = -z/2, w = b.z/4 - theta_1 */
+      spd_solve(dim, A + (size_t)i * dim * dim, bx, z);
+      double s = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        y[(size_t)i * dim + a] = -0.5 * z[a];
+        s += 0.25 * bx[a] * z[a];
+      }
+      w[i] = s - t1;
+    }
+  }
+  if (lambda_out) *lambda_out = lambda;
+  free(T); free(mono);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Annealing of eps with stopping aligned with Err^G (Sec. 5.2 and Sec.     */
+/* 5.5.4 leave both to future work; this is the build's reading).           */
+/* Stages k = 0, 1, ...: eps_k = max(eps_min, eps0 factor^k); stage k runs  */
+/* the ascent scheme (or_lbfgs_fit) at eps_k from the parameters the        */
+/* previous stage ended with -- the same diagram F_theta, made sharper by   */
+/* the smaller eps (Lemma 4.1: Phi_eps(theta) = Phi_1(theta / eps)) --, for  */
+/* stage_iter iterations, or final_iter at eps_min.  After a stage above    */
+/* eps_min and with err_stop, the schedule stops when the hard assignment   */
+/* reconstructs G: Phi > -log 2 / |Omega| certifies Err^G = 0 (Cor. 4.10), */
+/* else Err^G is computed by the arg-min assignment (Sec. 4).  Per stage:   */
+/* eps, Phi, Err^G (-1 where the certificate made it unnecessary) and the   */
+/* iterations; returns the number of stages (<= max_stages) or -1.          */
+/* ------------------------------------------------------------------------ */
+int or_anneal_fit(const or_grid* g, const int32_t* labels, int N, int d,
+                  double eps0, double factor, double eps_min, int stage_iter,
+                  int final_iter, int m, int err_stop, double* theta_io,
+                  int max_stages, double* st_eps, double* st_phi,
+                  double* st_err, int* st_iters) {
+  if (!(eps_min > 0.0) || !(factor > 0.0 && factor < 1.0) || max_stages < 1) return -1;
+  int K = or_K(g->dim, d);
+  int32_t* lab = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->P > 0 ? g->P : 1));
+  double eps = eps0 > eps_min ? eps0 : eps_min;
+  int k = 0;
+  for (; k < max_stages; ++k) {
+    int last = eps <= eps_min;
+    if (last) eps = eps_min;
+    or_fitreport rep;
+    if (or_lbfgs_fit(g, labels, N, d, eps, theta_io, last ? final_iter : stage_iter, m, 0.0, NULL, &rep)) {
+      free(lab);
+      return -1;
+    }
+    st_eps[k] = eps;
+    st_phi[k] = rep.phi;
+    st_err[k] = -1.0;
+    st_iters[k] = rep.iters;
+    if (last) { ++k; break; }
+    if (err_stop) {
+      if (rep.phi > -log(2.0) / (double)g->P) { ++k; break; }  /* Cor. 4.10 */
+      or_assign(g, N, d, 0, theta_io, lab, NULL);
+      int64_t miss = 0;
+      for (int64_t j = 0; j < g->P; ++j) miss += lab[j] != labels[j];
+      st_err[k] = (double)miss / (double)g->P;
+      if (miss == 0) { ++k; break; }
+    }
+    eps *= factor;
+  }
+  free(lab);
+  (void)K;
+  return k;
+}
+
+
+/* ------------------------------------------------------------------------ */
 /* Learned warm start: a multilayer perceptron with two ReLU hidden layers, */
 /*   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3,           */
 /* and the mean squared error L = (1/(B n_out)) sum (y - t)^2 with its      */
