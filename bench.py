@@ -58,6 +58,10 @@ def parse():
                     help="bf16x3 (default): tcgen05 logits with three-term bf16 operands, fp32 accumulation and "
                          "log-sum-exp, fp16 gradient operands, double final reductions; fp32: CUDA-core path")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-fit", action="store_true",
+                    help="skip the time-to-fit leg of the default run (about 100 s, mostly the FP64 reference fit)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP32, dense and early-parameter lines and the time-to-fit leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU oracle sample")
     ap.add_argument("--workload", default="config2", choices=["config2", "batched", "fit", "config3"],
@@ -96,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -117,7 +121,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -156,14 +160,16 @@ def make_workload_gpu(pd, torch):
     return grid, lab.astype(np.int32), n_eff, np.ascontiguousarray(th[used])
 
 
-def oracle_band(rows: int):
-    """A band of `rows` grid rows of the same workload, as an explicit point
-    list, labelled by the oracle (only the CPU legs call this).  Every
-    generated grain stays in the objective (the band alone would empty most
-    of them), so the cost per pixel is that of the whole workload."""
+def oracle_band(rows: int, r0=None):
+    """A band of `rows` grid rows of the same workload (starting at row r0,
+    centred by default), as an explicit point list labelled by the oracle
+    (only the CPU legs call this).  Every generated grain stays in the
+    objective (the band alone would empty most of them), so the cost per
+    pixel is that of the whole workload."""
     import oracle as O
     n1, n2 = SHAPE
-    r0 = (n2 - rows) // 2
+    if r0 is None:
+        r0 = (n2 - rows) // 2
     xs = -1.0 + (2.0 * np.arange(n1) + 1.0) / n1
     ys = -1.0 + (2.0 * np.arange(r0, r0 + rows) + 1.0) / n2
     X, Y = np.meshgrid(xs, ys, indexing="xy")
@@ -174,6 +180,37 @@ def oracle_band(rows: int):
     lab, _ = O.assign(g, N_GRAINS, DEG, th)
     lab = synth.boundary_noise(lab, (n1, rows), NOISE, SEED + 7)
     return O, g, lab.astype(np.int32), N_GRAINS, np.ascontiguousarray(th)
+
+
+def _oracle_worker(args):
+    """One host core: the oracle's objective+gradient on its own band, with
+    wall-clock start and end (the process pool is spawned, never forked)."""
+    rows, r0, barrier = args
+    O, g, lab, n, th = oracle_band(rows, r0)
+    barrier.wait()                          # every worker has built its band
+    t0 = time.time()
+    O.objective_grad(g, lab, n, DEG, EPS, th)
+    return t0, time.time(), g.P * n
+
+
+def cpu_oracle_all_cores(rows: int):
+    """The oracle on every host core at once: one spawned process per core,
+    each on its own band of `rows` rows; pairs of all bands over the wall time
+    from the first start to the last end."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    r0s = [(SHAPE[1] - rows) * q // max(1, cores - 1) for q in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man, ctx.Pool(cores) as pool:
+        barrier = man.Barrier(cores)
+        res = pool.map(_oracle_worker, [(rows, r0, barrier) for r0 in r0s], chunksize=1)
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    pairs = sum(r[2] for r in res)
+    return {"value": pairs / (t1 - t0), "unit": "pixel*grain/s", "cores": cores, "kind": "oracle",
+            "sample": "objective+gradient of the FP64 C oracle, one process per host core (%d), each on its "
+                      "own %d-row band (%d pixels x %d grains), %.1f s wall" % (cores, rows, rows * SHAPE[0],
+                                                                               N_GRAINS, t1 - t0)}
 
 
 def cpu_oracle_rate(target_s: float):
@@ -187,9 +224,16 @@ def cpu_oracle_rate(target_s: float):
     t = time.perf_counter()
     O.objective_grad(g, lab, n, DEG, EPS, th)
     dt = time.perf_counter() - t
-    return {"value": g.P * n / dt, "unit": "pixel*grain/s", "cores": 1, "kind": "oracle",
-            "sample": "objective+gradient of the FP64 C oracle (single thread) on a %d-row band "
-                      "(%d pixels x %d grains) of the same workload, %.1f s" % (rows, g.P, n, dt)}
+    one = {"value": g.P * n / dt, "unit": "pixel*grain/s", "cores": 1, "kind": "oracle",
+           "sample": "objective+gradient of the FP64 C oracle (single thread) on a %d-row band "
+                     "(%d pixels x %d grains) of the same workload, %.1f s" % (rows, g.P, n, dt)}
+    # every core: bands sized so that each process runs about as long
+    try:
+        one["all_cores"] = cpu_oracle_all_cores(max(2, rows))
+    except Exception as e:  # the single-thread figure stands on its own
+        one["all_cores"] = {"unavailable": repr(e)[:200]}
+    one["host_cores"] = os.cpu_count()
+    return one
 
 
 # ---------------------------------------------------------------------------
@@ -227,14 +271,32 @@ def run_reference(args):
     return 0
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
-# capture of the current code each (profiles/ summaries); None for kernels
-# without a capture of their current version
-NCU_TRAFFIC = {
-    "tc_bf16x3_lse_pass1": (21.20832e6, "profiles/tc_bf16x3_passes_config2.md"),
-    "tc_bf16x3_grad_pass2": (10.259712e6, "profiles/tc_bf16x3_passes_config2.md"),
-    "simt_grad_pass2": (8.44e6, "profiles/simt_grad_pass2_config2_fp32.md"),
-}
+def ncu_traffic():
+    """DRAM bytes (read + write) per launch of kernels captured with ncu:
+    the profile summaries under profiles/ carry lines
+        bench-traffic: kernel=<name> bytes_per_launch=<B> scale=<s> source_sha256=<h>
+    (B measured on the captured launch, s the factor to one launch of this
+    workload, 1 when the capture ran it).  A figure is used only while the
+    library's sources hash to h, i.e. for the very code that was measured;
+    otherwise the traffic is reported as null."""
+    from paper_2605_20816_gb300 import build
+    cur = build.source_hash()
+    out = {}
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return out
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, fn)) as f:
+            for line in f:
+                if "bench-traffic:" not in line:
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split("bench-traffic:", 1)[1].split() if "=" in t)
+                if kv.get("source_sha256") == cur and "kernel" in kv:
+                    out[kv["kernel"]] = (float(kv["bytes_per_launch"]) * float(kv.get("scale", "1")),
+                                         "profiles/" + fn)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -255,6 +317,47 @@ def job_value(world: int, pixels: int, grains: int, ms_step: float) -> float:
     """Pixel-grain pairs per second of all replicas (each evaluates the whole
     workload once per step: weak scaling)."""
     return world * pixels * grains / (ms_step * 1e-3)
+
+
+def time_steps(torch, fn, steps, flush):
+    """Device milliseconds per call of fn (CUDA events on the current stream,
+    L2 flushed before every call, untimed)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for q in range(steps):
+        flush.fill_(q & 0xFF)
+        ev[q][0].record(stream)
+        fn()
+        ev[q][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def time_to_fit(pd, grid, lab, N):
+    """Time to reach the FP64 plain fit's objective: Phi_ref is Phi after
+    1000 FP64 L-BFGS iterations from theta = 0 (the paper's budget, Sec.
+    5.2); a form has reached it when Phi >= Phi_ref - 1e-8 |Phi_ref|.  The
+    plain FP32 form and the BF16X3 (tensor-core) form each run a first phase
+    of up to 3000 iterations that leaves when its relative gain per
+    iteration drops below 1e-7, then FP64 refinement; a target met in the
+    first phase must hold in FP64."""
+    t = time.perf_counter()
+    _, ref = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=1000, prec=pd.PD_FP64)
+    rows = {"fp64_plain": {"seconds": time.perf_counter() - t, "iters": ref["iters"], "evals": ref["evals"],
+                           "phi": ref["phi"]}}
+    target = ref["phi"] - 1e-8 * abs(ref["phi"])
+    for name, prec in (("fp32_then_fp64", pd.PD_FP32), ("bf16x3_then_fp64", pd.PD_BF16X3)):
+        t = time.perf_counter()
+        _, rep = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=3000, prec=prec, refine_iter=1000, target_phi=target,
+                           switch_rtol=1e-7)
+        rows[name] = {"seconds": time.perf_counter() - t, "iters": rep["iters"], "iters_phase1": rep["iters_phase1"],
+                      "evals": rep["evals"], "phi": rep["phi"], "reached": rep["phi"] >= target}
+    ok = rows["fp32_then_fp64"]["reached"] and rows["bf16x3_then_fp64"]["reached"]
+    return {"phi_ref": ref["phi"], "target": target, "runs": rows,
+            "multiple_vs_fp32": rows["fp32_then_fp64"]["seconds"] / rows["bf16x3_then_fp64"]["seconds"] if ok else None}
 
 
 def run_ours(args):
@@ -344,6 +447,31 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     assert math.isfinite(float(h_obj.item()))
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        # the plain FP32 form (CUDA cores) on the same evaluation
+        n_x = max(5, min(args.steps, 50))
+        ms32 = time_steps(torch, lambda: pd.pd_objective_grad(grid, lab, N, th, DEG, EPS, prec=pd.PD_FP32,
+                                                             obj_out=obj, grad_out=grad), n_x, flush)
+        extras["fp32"] = {"ms_per_step": ms32, "value": P * N / (ms32 * 1e-3), "dtype": "f32",
+                          "what": "CUDA-core FP32 evaluation (tile-relative logits, float-float centre offsets)"}
+        # every pair visited: the pair skipping of the tensor-core passes off
+        os.environ["PD_TC_NO_SKIP"] = "1"
+        try:
+            msd = time_steps(torch, step, n_x, flush)
+        finally:
+            del os.environ["PD_TC_NO_SKIP"]
+        extras["dense"] = {"ms_per_step": msd, "value": P * N / (msd * 1e-3),
+                           "what": "the headline evaluation visiting every (tile, grain block) pair"}
+        # a parameter taken early in a fit (20 L-BFGS iterations from 0): a
+        # diffuse diagram, on which skipping leaves out fewer pairs
+        th_e, _ = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=20, prec=prec)
+        mse = time_steps(torch, lambda: pd.pd_objective_grad(grid, lab, N, th_e, DEG, EPS, prec=prec,
+                                                            obj_out=obj, grad_out=grad), n_x, flush)
+        extras["early_theta"] = {"ms_per_step": mse, "value": P * N / (mse * 1e-3),
+                                 "what": "the headline evaluation at theta after 20 L-BFGS iterations from 0"}
+        if not args.no_fit:
+            extras["time_to_fit"] = time_to_fit(pd, grid, lab, N)
     if rank != 0:
         return 0
     pk = peaks()
@@ -354,6 +482,7 @@ def run_ours(args):
     top = max(prof.items(), key=lambda kv: kv[1][1])
     name, (cnt, tot_ms) = top
     avg_s = tot_ms / cnt * 1e-3
+    traffic = ncu_traffic()
     if args.prec in ("fp32", "fp64"):
         # CUDA-core passes: bound by FMA issue; algorithmic work of either
         # pass is one K-long contraction, 2K flop per pixel-grain pair
@@ -361,8 +490,8 @@ def run_ours(args):
         peak = 2 * (units["ffma_per_s"] if args.prec == "fp32" else units["dfma_per_s"]) / 1e12
         achieved = algo / avg_s / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name, (None, None))[0],
-                "traffic_source": NCU_TRAFFIC.get(name, (None, None))[1],
+                "frac": achieved / peak, "traffic": traffic.get(name, (None, None))[0],
+                "traffic_source": traffic.get(name, (None, None))[1],
                 "peak_source": "measured %s FMA throughput x 2 flop (pd_microbench)" % args.prec.upper()}
     else:
         # tensor-core passes: the contractions run on tcgen05; each pass
@@ -372,8 +501,8 @@ def run_ours(args):
         peak = units["ex2_per_s"] / 1e12
         achieved = algo / avg_s / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name, (None, None))[0],
-                "traffic_source": NCU_TRAFFIC.get(name, (None, None))[1],
+                "frac": achieved / peak, "traffic": traffic.get(name, (None, None))[0],
+                "traffic_source": traffic.get(name, (None, None))[1],
                 "peak_source": "measured MUFU ex2 throughput (pd_microbench)"}
     # the whole evaluation against its binding unit: one exponential per
     # pixel-grain pair is the method's algorithmic minimum (the logits and
@@ -402,6 +531,10 @@ def run_ours(args):
         "unit_peaks": units,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
+    for k in ("fp32", "dense", "early_theta"):
+        if k in line:
+            line[k]["frac_of_ex2_peak"] = P * N / (line[k]["ms_per_step"] * 1e-3) / units["ex2_per_s"]
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -187,6 +187,24 @@ int pd_check_labels(const pd_grid* grid, const int32_t* labels, int N,
 int pd_theta_from_apd(int dim, int d, int N, const double* y, const double* w,
                       const double* A, double* theta_out);
 
+/* Host helper (Sec. 2.3, eqs. pd-lr-to-phys and apd-lr-to-phys; Sec. 5.5.3):
+ * the physical parameters of fitted Legendre coefficients of degree d = 1
+ * (power diagram: seeds y and weights w) or d = 2 (anisotropic power
+ * diagram: y, w and metrics A).  theta: host double[N][K_d], in any gauge.
+ * The coefficients are written in monomials, then for d = 2 every metric is
+ * shifted by the same lambda Id, lambda = max(0, margin - min_i
+ * lambda_min(A_i)) -- a common shift of all theta_i, which changes no cell
+ * (Lemma 4.2) -- so that every A_i has eigenvalues >= margin > 0, and
+ * y_i = -A_i^-1 b_i / 2, w_i = b_i . A_i^-1 b_i / 4 - theta_i,1 (b_i the
+ * linear coefficients).  For d = 1, y_i = -b_i / 2, w_i = |b_i|^2 / 4 -
+ * theta_i,1 (margin and A unused; the |x|^2 term common to a power diagram
+ * is not represented).  Outputs (host): y [N][dim], w [N], A [N][dim][dim]
+ * (d = 2), *lambda_out (may be NULL).  PD_ENOTSUP for other degrees,
+ * PD_EINVAL for a non-positive margin (d = 2) or NULL pointers, PD_ENAN for
+ * non-finite coefficients. */
+int pd_theta_to_apd(int dim, int d, int N, const double* theta, double margin, double* y, double* w, double* A,
+                    double* lambda_out);
+
 /* Synchronous: the moment heuristic of Sec. 5.5.2 (eqs. centroid-guess to
  * w-guess) as Legendre coefficients of degree d: centroids y', central
  * second moments B' (normalised by |G_i|), A' = B'^-1 (identity for d = 1,
@@ -220,6 +238,22 @@ typedef struct pd_fit_opts {
                          phase continues                                  */
   double switch_rtol; /* leave the first phase when the relative Phi gain
                          of an iteration is below this (0: never)          */
+  /* Annealing of eps (Secs. 5.2 and 5.5.4 leave the schedule to future
+   * work; this is the library's reading).  With anneal_eps0 > eps the fit
+   * runs in stages at eps_k = max(eps, anneal_eps0 * anneal_factor^k),
+   * k = 0, 1, ...: every stage above eps runs the first phase for
+   * anneal_iter iterations (no refinement, no target) from the parameters
+   * the previous stage ended with -- the same diagram, made sharper by the
+   * smaller eps (Lemma 4.1) --, and the stage at eps runs the phases as
+   * configured above.  With err_stop != 0 the schedule ends after a stage
+   * above eps once the hard assignment reconstructs G: when
+   * Phi > -log 2 / |Omega| (evaluated in FP64), which certifies Err^G = 0
+   * (Cor. 4.10), or else when the double-precision assignment finds no
+   * mismatch (report->status 5).  anneal_eps0 <= eps: no annealing. */
+  double anneal_eps0;
+  double anneal_factor; /* in (0, 1)                                        */
+  int anneal_iter;      /* iterations of each stage above eps (>= 1)        */
+  int err_stop;         /* stop the schedule once Err^G = 0                 */
 } pd_fit_opts;
 
 typedef struct pd_fit_report {
@@ -233,8 +267,11 @@ typedef struct pd_fit_report {
   int iters_phase1;   /* iterations of the first phase                     */
   int64_t evals;      /* objective+gradient evaluations                    */
   int64_t hvps;       /* Hessian-vector products                           */
-  int status;         /* 0 budget, 1 gtol, 2 line search stalled, 3 target */
+  int status;         /* 0 budget, 1 gtol, 2 line search stalled, 3 target,
+                         5 annealing stopped with Err^G = 0                */
   double seconds;     /* wall time of the call                             */
+  double eps_final;   /* eps of the last stage (eps without annealing)     */
+  int stages;         /* annealing stages run (1 without annealing)        */
 } pd_fit_report;
 
 /* Synchronous: maximise Phi over theta with the gauge theta_{N-1} = 0

@@ -42,6 +42,18 @@ def _stamp(src: str) -> str:
     return h.hexdigest()
 
 
+def source_hash() -> str:
+    """SHA-256 over every source file of the library (kernels, headers and
+    the C ABI header): profile summaries record it, so that a figure taken
+    from a capture is used only while the code it measured is unchanged."""
+    h = hashlib.sha256()
+    for p in _sources() + _headers():
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _nvcc():
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
         if cand and (os.path.sep not in cand or os.path.exists(cand)):

@@ -708,6 +708,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
   if (opts->method != PD_METHOD_LBFGS || opts->lbfgs_m < 1) return PD_ENOTSUP;
   if (opts->prec != PD_FP64 && opts->prec != PD_FP32) return PD_ENOTSUP;
   if (opts->init != PD_INIT_ZERO && opts->init != PD_INIT_GIVEN) return PD_ENOTSUP;
+  if (opts->anneal_eps0 > opts->eps) return PD_ENOTSUP;  // annealing: pd_fit only
   cudaStream_t st = (cudaStream_t)stream;
   const int K = basis_K(2, opts->d);
   for (int m = 0; m < n_maps; ++m) {

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -281,6 +282,135 @@ int pd_theta_from_apd(int dim, int d, int N, const double* y, const double* w, c
                       double* theta_out) {
   if ((dim == 2 && d > 64) || (dim == 3 && d > 64)) return PD_ENOTSUP;
   return theta_from_apd_host(dim, d, N, y, w, A, theta_out);
+}
+
+// Coefficient of t^n in P_m(t) (textbook closed form):
+// P_m(t) = 2^-m sum_{k <= m/2} (-1)^k C(m, k) C(2m - 2k, m) t^(m - 2k).
+static double legendre_power_coeff(int m, int n) {
+  if (n > m || ((m - n) & 1)) return 0.0;
+  const int k = (m - n) / 2;
+  auto binom = [](int a, int b) {
+    double v = 1.0;
+    for (int q = 1; q <= b; ++q) v = v * (double)(a - b + q) / (double)q;
+    return v;
+  };
+  double v = binom(m, k) * binom(2 * m - 2 * k, m);
+  for (int q = 0; q < m; ++q) v *= 0.5;
+  return (k & 1) ? -v : v;
+}
+
+// Smallest eigenvalue of a symmetric 2x2 or 3x3 matrix (closed forms: the
+// quadratic's smaller root; the trigonometric solution of the cubic).
+static double sym_lambda_min(int dim, const double* A) {
+  if (dim == 2) {
+    const double m = 0.5 * (A[0] + A[3]), h = 0.5 * (A[0] - A[3]);
+    return m - sqrt(h * h + A[1] * A[1]);
+  }
+  const double p1 = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+  const double q = (A[0] + A[4] + A[8]) / 3.0;
+  const double p2 = (A[0] - q) * (A[0] - q) + (A[4] - q) * (A[4] - q) + (A[8] - q) * (A[8] - q) + 2.0 * p1;
+  if (p2 == 0.0) return q;
+  const double p = sqrt(p2 / 6.0);
+  double B[9];
+  for (int r = 0; r < 9; ++r) B[r] = (A[r] - (r % 4 == 0 ? q : 0.0)) / p;
+  const double detB = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                      B[2] * (B[3] * B[7] - B[4] * B[6]);
+  double r = 0.5 * detB;
+  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+  const double phi = acos(r) / 3.0;
+  return q + 2.0 * p * cos(phi + 2.0 * M_PI / 3.0);
+}
+
+int pd_theta_to_apd(int dim, int d, int N, const double* theta, double margin, double* y, double* w, double* A,
+                    double* lambda_out) {
+  if ((dim != 2 && dim != 3) || N < 1 || !theta || !y || !w) return PD_EINVAL;
+  if (d != 1 && d != 2) return PD_ENOTSUP;
+  if (d == 2 && (!A || !(margin > 0.0) || !isfinite(margin))) return PD_EINVAL;
+  const int K = basis_K(dim, d);
+  const std::vector<int> al = alpha_table(dim, d);
+  auto index_of = [&](int e0, int e1, int e2) {
+    for (int k = 0; k < K; ++k)
+      if (al[k * dim] == e0 && al[k * dim + 1] == e1 && (dim == 2 || al[k * dim + 2] == e2)) return k;
+    return -1;
+  };
+  // monomial coefficients: h = sum_a theta_a prod_ax P_{a_ax}(x_ax)
+  //                           = sum_b (sum_a theta_a prod_ax c(a_ax, b_ax)) x^b
+  std::vector<double> mono((size_t)N * K, 0.0);
+  for (int i = 0; i < N; ++i)
+    for (int b = 0; b < K; ++b) {
+      double v = 0.0;
+      for (int a = 0; a < K; ++a) {
+        double c = 1.0;
+        for (int ax = 0; ax < dim && c != 0.0; ++ax) c *= legendre_power_coeff(al[a * dim + ax], al[b * dim + ax]);
+        v += c * theta[(size_t)i * K + a];
+      }
+      mono[(size_t)i * K + b] = v;
+    }
+  for (double v : mono)
+    if (!isfinite(v)) return PD_ENAN;
+  double lambda = 0.0;
+  if (d == 2) {
+    double lmin = INFINITY;
+    for (int i = 0; i < N; ++i) {
+      double* Ai = A + (size_t)i * dim * dim;
+      for (int a = 0; a < dim; ++a)
+        for (int b = a; b < dim; ++b) {
+          int e[3] = {0, 0, 0};
+          e[a] += 1;
+          e[b] += 1;
+          const double c = mono[(size_t)i * K + index_of(e[0], e[1], e[2])];
+          Ai[a * dim + b] = Ai[b * dim + a] = a == b ? c : 0.5 * c;
+        }
+      lmin = std::min(lmin, sym_lambda_min(dim, Ai));
+    }
+    // the common shift A_i + lambda Id of every grain leaves the diagram
+    // unchanged (Lemma 4.2) and makes every A_i positive definite
+    lambda = std::max(0.0, margin - lmin);
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < dim; ++a) A[(size_t)i * dim * dim + a * dim + a] += lambda;
+  }
+  for (int i = 0; i < N; ++i) {
+    double bx[3], z[3];
+    for (int a = 0; a < dim; ++a) {
+      int e[3] = {0, 0, 0};
+      e[a] = 1;
+      bx[a] = mono[(size_t)i * K + index_of(e[0], e[1], e[2])];
+    }
+    const double t1 = mono[(size_t)i * K + index_of(0, 0, 0)];
+    if (d == 1) {  // eq. pd-lr-to-phys
+      double s = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        y[(size_t)i * dim + a] = -0.5 * bx[a];
+        s += 0.25 * bx[a] * bx[a];
+      }
+      w[i] = s - t1;
+      continue;
+    }
+    // eq. apd-lr-to-phys: z = A^-1 b (adjugate over determinant), y = -z/2,
+    // w = b.z / 4 - theta_1
+    const double* M = A + (size_t)i * dim * dim;
+    if (dim == 2) {
+      const double det = M[0] * M[3] - M[1] * M[2];
+      z[0] = (M[3] * bx[0] - M[1] * bx[1]) / det;
+      z[1] = (-M[2] * bx[0] + M[0] * bx[1]) / det;
+    } else {
+      const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+      const double c11 = M[0] * M[8] - M[2] * M[6], c12 = M[1] * M[6] - M[0] * M[7], c22 = M[0] * M[4] - M[1] * M[3];
+      const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+      // symmetric: the adjugate is symmetric too
+      z[0] = (c00 * bx[0] + c01 * bx[1] + c02 * bx[2]) / det;
+      z[1] = (c01 * bx[0] + c11 * bx[1] + c12 * bx[2]) / det;
+      z[2] = (c02 * bx[0] + c12 * bx[1] + c22 * bx[2]) / det;
+    }
+    double s = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      y[(size_t)i * dim + a] = -0.5 * z[a];
+      s += 0.25 * bx[a] * z[a];
+    }
+    w[i] = s - t1;
+  }
+  if (lambda_out) *lambda_out = lambda;
+  return PD_OK;
 }
 
 int pd_heuristic_init(const pd_grid* grid, const int32_t* labels, int N, int d, double* theta_out,

@@ -70,6 +70,7 @@ class Problem : public Evaluator {
     if (h_grad_) cudaFreeHost(h_grad_);
   }
   bool ok() const { return sc_.ok() && h_theta_ && h_v_ && h_grad_; }
+  void set_eps(double e) { eps_ = e; }
   int n_free() const override { return (N_ - 1) * K_; }
   int K() const { return K_; }
 
@@ -429,6 +430,10 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
   if (opts->method != PD_METHOD_LBFGS && opts->method != PD_METHOD_NEWTON_CG) return PD_EINVAL;
   if (opts->method == PD_METHOD_LBFGS && opts->lbfgs_m < 1) return PD_EINVAL;
   if (pd_K(grid->dim, opts->d) < 0) return PD_EINVAL;
+  const bool anneal = opts->anneal_eps0 > opts->eps;
+  if (anneal && (!isfinite(opts->anneal_eps0) || !(opts->anneal_factor > 0.0 && opts->anneal_factor < 1.0) ||
+                 opts->anneal_iter < 1))
+    return PD_EINVAL;
   if ((grid->dim == 2 && opts->d > PD_MAX_DEGREE_2D) || (grid->dim == 3 && opts->d > PD_MAX_DEGREE_3D))
     return PD_ENOTSUP;
   memset(report, 0, sizeof(*report));
@@ -455,15 +460,56 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
         cudaStreamSynchronize(st) != cudaSuccess)
       return PD_ECUDA;
   }
+  // the ascent scheme, in stages of decreasing eps when annealing
   FitState fs;
-  rc = fit_run(pb, th, N, K, *opts, &fs);
-  if (rc) return rc;
+  int stages = 0, iters = 0, iters_phase1 = 0, status = 0;
+  double eps_k = anneal ? opts->anneal_eps0 : opts->eps;
+  for (;;) {
+    const bool last = eps_k <= opts->eps;
+    if (last) eps_k = opts->eps;
+    pb.set_eps(eps_k);
+    pd_fit_opts so = *opts;
+    so.eps = eps_k;
+    if (!last) {
+      so.max_iter = opts->anneal_iter;
+      so.refine_iter = 0;
+      so.target_phi = -INFINITY;
+      so.switch_rtol = 0.0;
+    }
+    rc = fit_run(pb, th, N, K, so, &fs);
+    if (rc) return rc;
+    ++stages;
+    iters += fs.iters;
+    iters_phase1 += last ? fs.iters_phase1 : fs.iters;
+    status = fs.status;
+    // the stage's parameters (gauge-fixed) start the next stage
+    for (size_t q = 0; q < fs.cur.x.size(); ++q) th[q] = fs.cur.x[q];
+    for (int k = 0; k < K; ++k) th[(size_t)(N - 1) * K + k] = 0.0;
+    if (last) break;
+    if (opts->err_stop) {
+      // Err^G = 0: certified by Phi > -log 2 / |Omega| (Cor. 4.10, Phi in
+      // FP64), else counted by the double-precision assignment
+      double f64 = fs.cur.f;
+      if (fs.final_prec != PD_FP64) {
+        rc = pb.eval(fs.cur.x, PD_FP64, &f64, nullptr);
+        if (rc) return rc;
+      }
+      bool done = -f64 > -log(2.0) / (double)g.P;
+      if (!done) {
+        int64_t miss = 0;
+        rc = pb.mismatch(fs.cur.x, &miss);
+        if (rc) return rc;
+        done = miss == 0;
+      }
+      if (done) {
+        status = 5;
+        break;
+      }
+    }
+    eps_k *= opts->anneal_factor;
+  }
   Point& cur = fs.cur;
   const int prec = fs.final_prec;
-  const int status = fs.status;
-  PhaseResult r1, r2;
-  r1.iters = fs.iters_phase1;
-  r2.iters = fs.iters - fs.iters_phase1;
   // final report in double precision
   double f_final = cur.f;
   std::vector<double> gfin = cur.g;
@@ -479,11 +525,13 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
   report->phi = -f_final;
   report->gnorm = sqrt(dot(gfin, gfin));
   report->err = (double)miss / (double)g.P;
-  report->iters = r1.iters + r2.iters;
-  report->iters_phase1 = r1.iters;
+  report->iters = iters;
+  report->iters_phase1 = iters_phase1;
   report->evals = pb.evals;
   report->hvps = pb.hvps;
   report->status = status;
+  report->eps_final = eps_k;
+  report->stages = stages;
   report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   return isfinite(report->phi) ? PD_OK : PD_ENAN;
 }

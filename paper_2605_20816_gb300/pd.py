@@ -45,13 +45,14 @@ class pd_fit_opts(C.Structure):
     _fields_ = [("d", C.c_int), ("eps", C.c_double), ("init", C.c_int), ("method", C.c_int),
                 ("max_iter", C.c_int), ("lbfgs_m", C.c_int), ("max_cg", C.c_int), ("prec", C.c_int),
                 ("refine_iter", C.c_int), ("gtol", C.c_double), ("target_phi", C.c_double),
-                ("switch_rtol", C.c_double)]
+                ("switch_rtol", C.c_double), ("anneal_eps0", C.c_double), ("anneal_factor", C.c_double),
+                ("anneal_iter", C.c_int), ("err_stop", C.c_int)]
 
 
 class pd_fit_report(C.Structure):
     _fields_ = [("phi", C.c_double), ("gnorm", C.c_double), ("err", C.c_double), ("iters", C.c_int),
                 ("iters_phase1", C.c_int), ("evals", C.c_int64), ("hvps", C.c_int64), ("status", C.c_int),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("eps_final", C.c_double), ("stages", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,6 +87,7 @@ def lib():
             L.pd_moments.argtypes = [gp, vp, ip, ip, vp, vp, vp]
             L.pd_check_labels.argtypes = [gp, vp, ip, vp]
             L.pd_theta_from_apd.argtypes = [ip, ip, ip, vp, vp, vp, vp]
+            L.pd_theta_to_apd.argtypes = [ip, ip, ip, vp, dbl, vp, vp, vp, C.POINTER(C.c_double)]
             L.pd_heuristic_init.argtypes = [gp, vp, ip, ip, vp, vp]
             L.pd_fit.argtypes = [gp, vp, ip, C.POINTER(pd_fit_opts), vp, C.POINTER(pd_fit_report), vp]
             L.pd_prof_enable.argtypes = [ip]
@@ -271,6 +273,23 @@ def pd_theta_from_apd(dim: int, d: int, y, w, A=None):
     return out
 
 
+def pd_theta_to_apd(dim: int, d: int, theta, margin: float = 1e-3):
+    """Host conversion of Legendre theta [N, K] (d = 1 or 2; numpy or CPU
+    tensor) to physical parameters.  Returns (y [N, dim], w [N], A [N, dim,
+    dim] or None, lambda) as CPU float64 tensors and a float."""
+    th = torch.as_tensor(theta, dtype=torch.float64).contiguous()
+    N = int(th.shape[0])
+    y = torch.empty((N, dim), dtype=torch.float64)
+    w = torch.empty(N, dtype=torch.float64)
+    A = torch.empty((N, dim, dim), dtype=torch.float64) if d == 2 else None
+    lam = C.c_double(0.0)
+    rc = lib().pd_theta_to_apd(dim, d, N, C.c_void_p(th.data_ptr()), float(margin), C.c_void_p(y.data_ptr()),
+                               C.c_void_p(w.data_ptr()), None if A is None else C.c_void_p(A.data_ptr()),
+                               C.byref(lam))
+    _check(rc, "pd_theta_to_apd")
+    return y, w, A, lam.value
+
+
 def pd_heuristic_init(grid: Grid, labels: torch.Tensor, N: int, d: int) -> torch.Tensor:
     out = torch.empty((N, pd_K(grid.dim, d)), dtype=torch.float64, device="cuda")
     _check(lib().pd_heuristic_init(grid.ref, _ptr(labels), N, d, _ptr(out), _stream()), "pd_heuristic_init")
@@ -280,12 +299,14 @@ def pd_heuristic_init(grid: Grid, labels: torch.Tensor, N: int, d: int) -> torch
 def pd_fit(grid: Grid, labels: torch.Tensor, N: int, d: int, eps: float, theta: torch.Tensor | None = None,
            init: int = PD_INIT_ZERO, method: int = PD_METHOD_LBFGS, max_iter: int = 1000, lbfgs_m: int = 10,
            max_cg: int = 50, prec: int = PD_FP64, refine_iter: int = 0, gtol: float = 0.0,
-           target_phi: float = -math.inf, switch_rtol: float = 0.0):
+           target_phi: float = -math.inf, switch_rtol: float = 0.0, anneal_eps0: float = 0.0,
+           anneal_factor: float = 0.5, anneal_iter: int = 100, err_stop: bool = False):
     """Returns (theta [N, K] CUDA float64, report dict)."""
     K = pd_K(grid.dim, d)
     th = torch.zeros((N, K), dtype=torch.float64, device="cuda") if theta is None else theta.clone().contiguous()
     opts = pd_fit_opts(d, float(eps), init, method, max_iter, lbfgs_m, max_cg, prec, refine_iter, gtol,
-                       target_phi, switch_rtol)
+                       target_phi, switch_rtol, float(anneal_eps0), float(anneal_factor), int(anneal_iter),
+                       1 if err_stop else 0)
     rep = pd_fit_report()
     _check(lib().pd_fit(grid.ref, _ptr(labels), N, C.byref(opts), _ptr(th), C.byref(rep), _stream()), "pd_fit")
     return th, rep.as_dict()

@@ -240,3 +240,64 @@ def test_heuristic_theta_diagram(oracle, d):
     sure = gap > 1e-9
     assert sure.mean() > 0.99
     np.testing.assert_array_equal(got[sure], np.argmin(cost, 1)[sure])
+
+
+def centres_3d(shape):
+    n0, n1, n2 = shape
+    idx = np.arange(n0 * n1 * n2)
+    k = [idx % n0, (idx // n0) % n1, idx // (n0 * n1)]
+    return np.stack([-1.0 + (2.0 * k[a] + 1.0) / shape[a] for a in range(3)], 1)
+
+
+def test_heuristic_formulas_3d(oracle):
+    # the 3-D branch of the heuristic (the paper states it in 2-D; the
+    # reading: A' = B'^-1 of the 3x3 central second moments, w' = sqrt(det
+    # A') |G_i| / (|Omega| 4 pi / 3), the ellipsoid volume in place of pi),
+    # against numpy's mean, covariance, inverse and determinant
+    shape, N = (14, 12, 10), 6
+    y0, w0, A0 = synth.apd_params(17, N, dim=3)
+    g = oracle.Grid(shape)
+    lab, _ = oracle.assign(g, N, 2, oracle.theta_from_apd(3, 2, y0, w0, A0))
+    lab, N, _ = synth.compact(lab)
+    X = centres_3d(shape)
+    y, w, A = oracle.heuristic_params(g, lab, N, anisotropic=True)
+    for i in range(N):
+        Xi = X[lab == i]
+        np.testing.assert_allclose(y[i], Xi.mean(0), atol=1e-14)
+        B = np.cov(Xi.T, bias=True)
+        np.testing.assert_allclose(A[i], np.linalg.inv(B), rtol=1e-9, atol=1e-9 * np.abs(np.linalg.inv(B)).max())
+        want_w = math.sqrt(np.linalg.det(np.linalg.inv(B))) * len(Xi) / (g.P * 4.0 * math.pi / 3.0)
+        assert abs(w[i] - want_w) < 1e-10 * want_w
+    # a collinear grain (B' singular) falls back to A' = Id (Sec. 5.5.2: "if B' is invertible")
+    lab2 = np.zeros(g.P, dtype=np.int32)
+    line = (X[:, 1] == X[0, 1]) & (X[:, 2] == X[0, 2])      # one row of voxels along x
+    lab2[line] = 1
+    _, _, A2 = oracle.heuristic_params(g, lab2, 2, anisotropic=True)
+    np.testing.assert_array_equal(A2[1], np.eye(3))
+
+
+def test_heuristic_theta_diagram_3d(oracle):
+    # the 3-D heuristic's parameters computed here from the formulas in numpy
+    # define an anisotropic power diagram; heuristic_theta (degree 2) must
+    # rasterise to it, which pins the 3-D conversion to Legendre as well
+    shape, N = (16, 14, 12), 7
+    y0, w0, A0 = synth.apd_params(19, N, dim=3)
+    g = oracle.Grid(shape)
+    lab, _ = oracle.assign(g, N, 2, oracle.theta_from_apd(3, 2, y0, w0, A0))
+    lab, N, _ = synth.compact(lab)
+    X = centres_3d(shape)
+    ys, ws, As = [], [], []
+    for i in range(N):
+        Xi = X[lab == i]
+        A = np.linalg.inv(np.cov(Xi.T, bias=True))
+        ys.append(Xi.mean(0))
+        As.append(A)
+        ws.append(math.sqrt(np.linalg.det(A)) * len(Xi) / (g.P * 4.0 * math.pi / 3.0))
+    ys, ws, As = np.array(ys), np.array(ws), np.array(As)
+    D = X[:, None, :] - ys[None]
+    cost = np.einsum("pna,nab,pnb->pn", D, As, D) - ws[None]
+    th = oracle.heuristic_theta(g, lab, N, 2)
+    got, gap = oracle.assign(g, N, 2, th)
+    sure = gap > 1e-9
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(got[sure], np.argmin(cost, 1)[sure])
