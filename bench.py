@@ -470,6 +470,21 @@ def run_ours(args):
                                                             obj_out=obj, grad_out=grad), n_x, flush)
         extras["early_theta"] = {"ms_per_step": mse, "value": P * N / (mse * 1e-3),
                                  "what": "the headline evaluation at theta after 20 L-BFGS iterations from 0"}
+        # the arg-min assignment with the mismatch count (Err^G), fast path
+        # (fp32 with a certified margin) and the double-precision kernel
+        mis = torch.empty((), dtype=torch.int64, device="cuda")
+        lab_out = torch.empty_like(lab)
+
+        def assign():
+            pd.pd_assign(grid, N, DEG, th, ref_labels=lab, out=lab_out, mismatch_out=mis)
+        msa = time_steps(torch, assign, n_x, flush)
+        os.environ["PD_ASSIGN_FP64"] = "1"
+        try:
+            msa64 = time_steps(torch, assign, max(3, n_x // 10), flush)
+        finally:
+            del os.environ["PD_ASSIGN_FP64"]
+        extras["assign"] = {"ms": msa, "ms_fp64_kernel": msa64, "err": int(mis.item()) / P,
+                            "what": "arg-min assignment and Err^G at the generating parameters"}
         if not args.no_fit:
             extras["time_to_fit"] = time_to_fit(pd, grid, lab, N)
     if rank != 0:

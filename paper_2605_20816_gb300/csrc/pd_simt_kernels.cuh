@@ -729,6 +729,145 @@ k_assign(Geom g, int N, const double* __restrict__ theta, int32_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Fast arg-min assignment: an fp32 pass with a certified margin, double
+// precision for the pixels where the margin is not met.
+//
+// |P_m| <= 1 on [-1, 1], so every feature satisfies |eta_k(x)| <= 1 and
+// every h_i(x) = theta_i . eta(x) computed in fp32 (fp32 parameters, fp32
+// features from the recurrence, an fma chain) lies within
+//   E = C 2^-24 max_i sum_k |theta_ik|,  C = 2 (K + 8 D + 8),
+// of its exact value (the dot product contributes about K units of
+// rounding, the rounding of theta one, the recurrence and the tensor
+// products at most about 8 (D + 1); C doubles that).  A pixel whose fp32
+// best and second-best values are more than 2E apart has the same arg-min
+// in exact arithmetic, hence in double: its fp32 label is final.  The others
+// are listed and assigned by the double-precision arg-min (smallest index on
+// ties), so every label equals that of the double-precision kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_assign_prep(const double* __restrict__ theta, int N, int K, int KP, float* __restrict__ th32,
+              float* __restrict__ margin, int* __restrict__ count, float c_bound) {
+  __shared__ double smax[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double l1 = 0.0;
+    for (int k = 0; k < K; ++k) l1 += fabs(theta[(int64_t)i * K + k]);
+    m = fmax(m, l1);
+  }
+  for (int64_t q = threadIdx.x; q < (int64_t)N * KP; q += blockDim.x) {
+    const int i = (int)(q / KP), k = (int)(q % KP);
+    th32[q] = k < K ? (float)theta[(int64_t)i * K + k] : 0.f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, smax[w]);
+    // twice the bound E (the two values compared), rounded up; NaN parameters
+    // make it NaN, and no pixel is certified
+    *margin = (float)(2.0 * c_bound * ldexp(mx, -24) * (1.0 + 1e-6));
+    *count = 0;
+  }
+}
+
+template <int DIM, int D>
+__global__ void __launch_bounds__(kAssignThreads)
+k_assign32(Geom g, int N, const float* __restrict__ th32, const float* __restrict__ margin, int32_t* __restrict__ out,
+           const int32_t* __restrict__ ref, unsigned long long* __restrict__ mismatch, int* __restrict__ list,
+           int* __restrict__ count) {
+  constexpr int K = basis_K(DIM, D);
+  constexpr int KP = padded_K<float>(K);
+  __shared__ __align__(16) float sth[kAssignGT * KP];
+  __shared__ int swarp[kAssignThreads / 32];
+  const int64_t j = (int64_t)blockIdx.x * kAssignThreads + threadIdx.x;
+  float x[DIM], eta[K];
+  if (j < g.P) {
+    pixel_coords<DIM>(g, j, x);
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = 0.f;
+  }
+  legendre_features<DIM, D>(x, eta);
+  float best = INFINITY, second = INFINITY;
+  int bi = 0;
+  for (int g0 = 0; g0 < N; g0 += kAssignGT) {
+    const int gn = min(kAssignGT, N - g0);
+    __syncthreads();
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(th32 + (int64_t)g0 * KP);
+      uint4* dst = reinterpret_cast<uint4*>(sth);
+      for (int e = threadIdx.x; e < gn * KP / 4; e += kAssignThreads) dst[e] = src[e];
+    }
+    __syncthreads();
+    for (int i = 0; i < gn; ++i) {
+      const float h = dot_k<K>(sth + i * KP, eta);
+      if (h < best) {
+        second = best;
+        best = h;
+        bi = g0 + i;
+      } else if (h < second) {
+        second = h;
+      }
+    }
+  }
+  int miss = 0;
+  if (j < g.P) {
+    if (second - best > *margin) {  // certified (false for NaN)
+      out[j] = bi;
+      if (ref) miss = ref[j] != bi;
+    } else {
+      list[atomicAdd(count, 1)] = (int)j;
+    }
+  }
+  if (mismatch) {
+    const int wsum = __popc(__ballot_sync(0xffffffffu, miss));
+    if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < kAssignThreads / 32; ++w) tot += swarp[w];
+      if (tot) atomicAdd(mismatch, (unsigned long long)tot);
+    }
+  }
+}
+
+// The listed pixels by the double-precision arg-min (one thread a pixel,
+// parameters from the caches; a grid-stride loop over the device count).
+template <int DIM, int D>
+__global__ void __launch_bounds__(256)
+k_assign64_list(Geom g, int N, const double* __restrict__ theta, const int* __restrict__ list,
+                const int* __restrict__ count, int32_t* __restrict__ out, const int32_t* __restrict__ ref,
+                unsigned long long* __restrict__ mismatch) {
+  constexpr int K = basis_K(DIM, D);
+  const int n = *count;
+  int miss = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int64_t j = list[q];
+    double x[DIM], eta[K];
+    pixel_coords<DIM>(g, j, x);
+    legendre_features<DIM, D>(x, eta);
+    double best = INFINITY;
+    int bi = 0;
+    for (int i = 0; i < N; ++i) {
+      const double h = dot_k<K>(theta + (int64_t)i * K, eta);
+      if (h < best) {
+        best = h;
+        bi = i;
+      }
+    }
+    out[j] = bi;
+    if (ref) miss += ref[j] != bi;
+  }
+  if (mismatch) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) miss += __shfl_down_sync(0xffffffffu, miss, o);
+    if ((threadIdx.x & 31) == 0 && miss) atomicAdd(mismatch, (unsigned long long)miss);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Features (testing aid): eta_out[j][k].
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int D>

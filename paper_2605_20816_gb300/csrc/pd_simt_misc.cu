@@ -1,5 +1,7 @@
 // pd_simt_misc.cu -- launchers of the assignment, feature, moment and label
 // kernels, and the precision/dimension dispatch of the CUDA-core evaluation.
+#include <stdlib.h>
+
 #include "pd_simt_kernels.cuh"
 
 namespace pd {
@@ -51,10 +53,43 @@ int assign_simt(const Geom& g, int dim, int d, int N, const double* theta, int32
   if (mismatch && cudaMemsetAsync(mismatch, 0, sizeof(int64_t), st) != cudaSuccess) return PD_ECUDA;
   if (g.P == 0) return PD_OK;
   const unsigned blocks = (unsigned)((g.P + kAssignThreads - 1) / kAssignThreads);
+  unsigned long long* mis = reinterpret_cast<unsigned long long*>(ref ? mismatch : nullptr);
+  // the exact gap needs every pixel in double; labels alone take the fp32
+  // pass with its certified margin and double only where it is not met
+  // (PD_ASSIGN_FP64=1 in the environment forces the double kernel)
+  const char* force = getenv("PD_ASSIGN_FP64");
+  // (structured grids only: the margin rests on |eta_k| <= 1, which needs
+  // coordinates in [-1, 1], and a point list may hold others)
+  const bool fast = !gap && !g.coords && !(force && force[0] && force[0] != '0');
+  Scratch sc(st);
+  float* th32 = nullptr;
+  float* margin = nullptr;
+  int* count = nullptr;
+  int* list = nullptr;
+  if (fast) {
+    th32 = sc.get<float>((size_t)N * 36);  // rows of padded_K<float>(K) <= 36 floats (K <= 36)
+    margin = sc.get<float>(1);
+    count = sc.get<int>(1);
+    list = sc.get<int>((size_t)g.P);
+    if (!sc.ok()) return PD_ENOMEM;
+    if (g.P > INT32_MAX) return PD_ENOTSUP;
+  }
   bool ok = dispatch_dim_deg(dim, d, [&](auto dimc, auto degc) {
     constexpr int DIM = decltype(dimc)::value;
     constexpr int D = decltype(degc)::value;
-    PD_TIMED(st, "assign", k_assign<DIM, D><<<blocks, kAssignThreads, 0, st>>>(g, N, theta, out, gap, ref, reinterpret_cast<unsigned long long*>(ref ? mismatch : nullptr)));
+    if (!fast) {
+      PD_TIMED(st, "assign", k_assign<DIM, D><<<blocks, kAssignThreads, 0, st>>>(g, N, theta, out, gap, ref, mis));
+      return;
+    }
+    constexpr int K = basis_K(DIM, D);
+    constexpr int KP = padded_K<float>(K);
+    const float c_bound = 2.f * (float)(K + 8 * D + 8);
+    PD_TIMED(st, "assign_prep", k_assign_prep<<<1, 1024, 0, st>>>(theta, N, K, KP, th32, margin, count, c_bound));
+    PD_TIMED(st, "assign32", (k_assign32<DIM, D><<<blocks, kAssignThreads, 0, st>>>(g, N, th32, margin, out, ref, mis,
+                                                                                    list, count)));
+    const int grid2 = device_sm_count() * 4;
+    PD_TIMED(st, "assign64_list",
+             (k_assign64_list<DIM, D><<<grid2, 256, 0, st>>>(g, N, theta, list, count, out, ref, mis)));
   });
   if (!ok) return PD_ENOTSUP;
   return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;

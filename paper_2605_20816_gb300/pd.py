@@ -233,11 +233,14 @@ def pd_hvp(grid: Grid, labels, N: int, theta: torch.Tensor, v: torch.Tensor, d: 
 
 
 def pd_assign(grid: Grid, N: int, d: int, theta: torch.Tensor, want_gap: bool = False,
-              ref_labels: torch.Tensor | None = None):
+              ref_labels: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              mismatch_out: torch.Tensor | None = None):
     """Returns (labels int32 [P], gap float64 [P] or None, mismatch int64 0-d or None)."""
-    lab = torch.empty(grid.P, dtype=torch.int32, device="cuda")
+    lab = out if out is not None else torch.empty(grid.P, dtype=torch.int32, device="cuda")
     gap = torch.empty(grid.P, dtype=torch.float64, device="cuda") if want_gap else None
-    mis = torch.empty((), dtype=torch.int64, device="cuda") if ref_labels is not None else None
+    mis = None
+    if ref_labels is not None:
+        mis = mismatch_out if mismatch_out is not None else torch.empty((), dtype=torch.int64, device="cuda")
     _check(lib().pd_assign(grid.ref, N, d, _ptr(theta), _ptr(lab), _ptr(gap), _ptr(ref_labels), _ptr(mis),
                            _stream()), "pd_assign")
     return lab, gap, mis

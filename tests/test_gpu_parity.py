@@ -220,3 +220,50 @@ def test_config2_full_size_fp32_and_fp64():
     print("config2 fp32 rel err: phi %.3e grad %.3e" % (abs(phi32 - phi_o) / abs(phi_o), rel(grad32, grad_o)))
     assert abs(phi32 - phi_o) <= 1e-5 * abs(phi_o)
     assert rel(grad32, grad_o) <= 1e-5
+
+
+@pytest.mark.parametrize("shape,N,d,scale", [((64, 64), 8, 2, 1.0), ((57, 43), 200, 4, 1.0), ((11, 9, 7), 30, 3, 1.0),
+                                             ((40, 30), 150, 7, 1.0), ((200, 190), 300, 4, 0.01),
+                                             ((20, 20), 40, 2, 0.0)])
+def test_assign_fast_path_equals_double(shape, N, d, scale, monkeypatch):
+    # labels without the gap take the fp32 pass with a certified margin and
+    # double precision only where the margin is not met: every label must
+    # equal the double-precision kernel's, ties (a duplicate grain, theta = 0)
+    # included, and so must the mismatch count
+    th = synth.random_theta(23, N, O.K(len(shape), d), scale)
+    if N > 2:
+        th[2] = th[1]
+    g = O.Grid(shape)
+    ref = synth.random_labels(24, g.P, N)
+    grid = pd.Grid(shape)
+    lab, _, mis = pd.pd_assign(grid, N, d, dev(th), ref_labels=dev(ref))
+    monkeypatch.setenv("PD_ASSIGN_FP64", "1")
+    lab64, _, mis64 = pd.pd_assign(grid, N, d, dev(th), ref_labels=dev(ref))
+    monkeypatch.delenv("PD_ASSIGN_FP64")
+    np.testing.assert_array_equal(lab.cpu().numpy(), lab64.cpu().numpy())
+    assert int(mis.item()) == int(mis64.item())
+    lab_o, gap_o = O.assign(g, N, d, th)
+    sure = gap_o >= 1e-9
+    np.testing.assert_array_equal(lab.cpu().numpy()[sure], lab_o[sure])
+
+
+@pytest.mark.slow
+def test_assign_fast_path_config2_full_size(monkeypatch):
+    # 1024 x 1024, N = 485 degree-4 diagram: the fast assignment against the
+    # double-precision kernel on every pixel, and its time
+    shape, d = (1024, 1024), 4
+    g, lab_ref, N, th = poly_problem(shape, 500, d, seed=synth.SEED_BASE + 1, noise=0.02)
+    grid, dth, dref = pd.Grid(shape), dev(th), dev(lab_ref)
+    lab, _, mis = pd.pd_assign(grid, N, d, dth, ref_labels=dref)
+    monkeypatch.setenv("PD_ASSIGN_FP64", "1")
+    lab64, _, mis64 = pd.pd_assign(grid, N, d, dth, ref_labels=dref)
+    monkeypatch.delenv("PD_ASSIGN_FP64")
+    assert torch.equal(lab, lab64)
+    assert int(mis.item()) == int(mis64.item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        pd.pd_assign(grid, N, d, dth, ref_labels=dref)
+    e1.record()
+    torch.cuda.synchronize()
+    print("config2 fast assignment: %.3f ms, mismatch %d" % (e0.elapsed_time(e1) / 5, int(mis.item())))
