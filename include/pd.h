@@ -43,6 +43,7 @@
 #ifndef PD_H_
 #define PD_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -152,6 +153,46 @@ int pd_objective_grad(const pd_grid* grid, const int32_t* labels, int N,
 int pd_hvp(const pd_grid* grid, const int32_t* labels, int N,
            const double* theta, const double* v, const pd_eval_opts* opts,
            double* hv_out, void* stream);
+
+/* ---- plans: repeated evaluations on one pixel set and label map -------- */
+/* The ascent of Sec. 5.2 evaluates Phi, its gradient and Hessian-vector
+ * products hundreds of times on the same pixel set Omega and the same label
+ * map G, only theta (and eps, when annealed) changing.  A plan does the
+ * parts that depend on Omega and G alone once: it sizes and allocates all
+ * scratch of an evaluation up front (one device allocation), and its first
+ * evaluation leaves in that scratch the Legendre features of every tile
+ * centre (Omega only) and, for the tensor-core precisions, the grain order
+ * (Morton order of the label centroids, G only), which later evaluations
+ * reuse.  Plan evaluations allocate nothing and return results bitwise equal
+ * to pd_objective_grad / pd_hvp with the same arguments.
+ *
+ * pd_plan_create: grid, labels, N, d and prec as for pd_objective_grad
+ * (N >= 2, P >= 1); flags = 0, or PD_PLAN_HVP to also reserve the scratch of
+ * pd_plan_hvp.  The plan keeps a copy of *grid and the pointers grid->coords
+ * and labels (device, borrowed): both must stay allocated and unchanged
+ * until pd_plan_destroy.  Allocates with cudaMalloc on the current device
+ * (PD_ENOMEM when that fails) and writes the handle to *plan_out (host);
+ * on failure *plan_out is NULL and nothing is held.
+ * pd_plan_objective_grad / pd_plan_hvp: theta (and v) device double[N][K],
+ * eps > 0 finite; outputs as for pd_objective_grad (obj_out or grad_out may
+ * be NULL, not both) and pd_hvp; pd_plan_hvp on a plan created without
+ * PD_PLAN_HVP returns PD_EINVAL.  Calls on one plan share its scratch: they
+ * must not overlap on the GPU (one stream, or ordered by the caller) and
+ * must not run from several host threads at once.  Calls on different
+ * plans are independent.
+ * pd_plan_scratch_bytes: the device bytes the plan holds (host *bytes_out).
+ * pd_plan_destroy: frees the plan (cudaFree, which waits for the device);
+ * NULL is a no-op. */
+typedef struct pd_plan pd_plan;
+#define PD_PLAN_HVP 1
+int pd_plan_create(const pd_grid* grid, const int32_t* labels, int N, int d,
+                   int prec, int flags, pd_plan** plan_out);
+int pd_plan_objective_grad(pd_plan* plan, const double* theta, double eps,
+                           double* obj_out, double* grad_out, void* stream);
+int pd_plan_hvp(pd_plan* plan, const double* theta, const double* v,
+                double eps, double* hv_out, void* stream);
+int pd_plan_scratch_bytes(const pd_plan* plan, size_t* bytes_out);
+void pd_plan_destroy(pd_plan* plan);
 
 /* Arg-min assignment F_theta (Sec. 2.1, eq. Li_def), computed in double:
  * labels_out[j] = the smallest i attaining min_i theta_i . eta(x_j).
@@ -301,32 +342,48 @@ typedef struct pd_map {
 typedef struct pd_batch pd_batch;
 
 /* Synchronous: builds a plan that evaluates eq. (Phi) and eq. (grad) of all
- * maps (same degree, eps and precision; PD_FP64 or PD_FP32) with one
- * persistent launch per pass, every pass working through a list of (map,
- * pixel block) and (map, pixel chunk, grain tile) items, heaviest maps
- * first; the whole evaluation is captured once as a CUDA graph.  With
- * autotune != 0 the pass-2 chunking and the persistent grid size are chosen
- * by timing five candidates on the first plan of a (degree, precision,
- * batch size, total work) class; the choice is cached for the process.
- * The plan owns its scratch (allocated here, freed by pd_batch_destroy). */
+ * maps (same degree, eps and precision).
+ * PD_FP64 / PD_FP32: one persistent launch per pass, every pass working
+ * through a list of (map, pixel block) and (map, pixel chunk, grain tile)
+ * items, heaviest maps first; the whole evaluation is captured once as a
+ * CUDA graph.  With autotune != 0 the pass-2 chunking and the persistent
+ * grid size are chosen by timing five candidates on the first plan of a
+ * (degree, precision, batch size, total work) class; the choice is cached
+ * for the process.
+ * PD_BF16 / PD_BF16X3: every map gets the plan of a single-map evaluation
+ * (see pd_plan_create; the first evaluation, run here at theta = 0 into the
+ * plan's own buffers, leaves its centre features and grain order), and the
+ * evaluations of all maps are captured as one CUDA graph in which the maps
+ * run on parallel chains (each map, heaviest first, on the chain with the
+ * least pixels x grains so far).  With autotune != 0 the number of chains
+ * (1, 2, 4 or 8) is chosen by timing the graph at theta = 0, else 4.  A
+ * map's results are bitwise those of pd_objective_grad on that map.
+ * The plan owns its scratch (allocated here, freed by pd_batch_destroy).
+ * PD_EINVAL for an invalid precision; PD_ENOTSUP for a degree the
+ * precision does not support. */
 int pd_batch_create(int n_maps, const pd_map* maps, const pd_eval_opts* opts,
                     int autotune, pd_batch** out);
 /* Enqueues one replay of the plan's graph on the stream: every active map's
  * Phi and gradient from its current theta.  Replays on one plan must not
- * overlap (they share the plan's scratch). */
+ * overlap (they share the plan's scratch).  On the tensor cores, while some
+ * map is inactive, the active maps' evaluations are launched directly on
+ * the same chains instead of the graph. */
 int pd_batch_eval(pd_batch* batch, void* stream);
-/* Which maps the next replays evaluate: active[m] != 0 (host int32[n_maps],
- * copied asynchronously on the stream).  All maps are active initially. */
+/* Which maps the next replays evaluate: active[m] != 0 (host int32[n_maps];
+ * CUDA cores: copied asynchronously on the stream; tensor cores: read
+ * before the call returns).  All maps are active initially. */
 int pd_batch_set_active(pd_batch* batch, const int32_t* active, void* stream);
-/* The tuning choice of the plan and the measured milliseconds per replay. */
+/* The tuning choice of the plan (CUDA cores: chunk factor and occupancy
+ * divisor; tensor cores: the number of chains in *chunk_factor, 0 in
+ * *occ_div) and the measured milliseconds per replay (0 without tuning). */
 int pd_batch_info(const pd_batch* batch, int* chunk_factor, int* occ_div,
                   double* tuned_ms);
 /* Synchronises the device and frees the plan. */
 void pd_batch_destroy(pd_batch* batch);
 
-/* Synchronous: the ascent scheme of pd_fit (L-BFGS only; PD_FP64 or PD_FP32
- * first phase with optional FP64 refinement; init PD_INIT_ZERO or
- * PD_INIT_GIVEN) for every map at once.  Each map runs its own optimiser
+/* Synchronous: the ascent scheme of pd_fit (L-BFGS only; a first phase in
+ * any precision with optional FP64 refinement; init PD_INIT_ZERO or
+ * PD_INIT_GIVEN, e.g. a learned warm start) for every map at once.  Each map runs its own optimiser
  * on a host thread; their objective/gradient requests are served together,
  * one graph replay per round for all maps that are waiting.  theta_io[m]:
  * device double[N_m][K], in (PD_INIT_GIVEN) and out (gauge-fixed).

@@ -3,6 +3,13 @@
 // with launch shapes chosen by a small autotuner; and the lockstep batched
 // ascent scheme built on it (pd_fit_batched).
 //
+// On the tensor cores (PD_BF16, PD_BF16X3) every map has a plan of the
+// single-map evaluation (pd_plan.cu: scratch, centre features and grain
+// order made once), and the evaluations of all maps are captured as one
+// graph in which the maps run on a few parallel chains, heaviest first,
+// each map on the chain with the least work so far; the autotuner picks the
+// number of chains.  A map's results are those of a single-map call.
+//
 // Work items: pass 1 = (map, 512-pixel block), pass 2 = (map, pixel chunk,
 // 128-grain tile); in FP32 the pixels are the tiles of the single-map FP32
 // evaluation (pd_tiles.cuh): pass 1 = (map, block of four tiles), pass 2 =
@@ -193,9 +200,11 @@ k_batch_reduce_parts(const BatchMapDev* __restrict__ maps, int K, double eps, co
 // The plan: device tables, scratch, the captured graph.
 // ---------------------------------------------------------------------------
 struct Tune {
-  int chunk_factor;  // pass-2 CTAs per SM the chunking aims at (single-map default: 6)
-  int occ_div;       // persistent grid = SMs x occupancy / occ_div
+  int chunk_factor;  // pass-2 CTAs per SM the chunking aims at (single-map default: 6);
+                     // tensor cores: the number of parallel chains
+  int occ_div;       // persistent grid = SMs x occupancy / occ_div (tensor cores: unused, 0)
 };
+constexpr int kMaxChains = 8;
 
 struct BatchKey {
   int d, prec, nmap_bucket, work_bucket;
@@ -226,6 +235,18 @@ struct pd_batch {
   bool tuned = false;
   cudaGraphExec_t exec = nullptr;
   int occ1 = 1, occ2 = 1;
+  // tensor-core precisions
+  std::vector<pd::PlanCore> plans;  // one per map
+  std::vector<int> order;           // maps by decreasing pixels x grains
+  std::vector<int> chain;           // map -> chain
+  std::vector<int32_t> h_active;    // host copy of the active flags
+  bool all_active = true;
+  int n_chains = 1;
+  cudaStream_t cst[pd::kMaxChains] = {};
+  cudaEvent_t fork = nullptr, join[pd::kMaxChains] = {};
+  double* tc_zero = nullptr;        // theta = 0 for the tuning replays (largest N x K)
+  double* tc_out = nullptr;         // outputs of the tuning replays (Phi per map, then gradients)
+  std::vector<size_t> tc_off;       // gradient offset of each map in tc_out
 };
 
 namespace pd {
@@ -434,6 +455,135 @@ int build_plan(pd_batch* b, const Tune& tu) {
   return rc;
 }
 
+bool is_tc(int prec) { return prec == PD_BF16 || prec == PD_BF16X3; }
+
+// Chains for the tensor-core maps: heaviest map first, each on the chain
+// with the least work so far.
+void assign_chains(pd_batch* b, int n_chains) {
+  b->n_chains = n_chains;
+  b->chain.assign(b->n_maps, 0);
+  std::vector<double> load(n_chains, 0.0);
+  for (int m : b->order) {
+    const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->chain[m] = c;
+    load[c] += (double)b->maps[m].grid.P * (double)b->maps[m].N;
+  }
+}
+
+// Enqueues the evaluations of the maps (all, or the active ones) on the
+// chains, forked from and joined back to st; `tuning` evaluates theta = 0
+// into the plan's own outputs instead of the maps' buffers.
+int tc_enqueue(pd_batch* b, cudaStream_t st, bool tuning, bool only_active) {
+  if (cudaEventRecord(b->fork, st) != cudaSuccess) return PD_ECUDA;
+  for (int c = 0; c < b->n_chains; ++c)
+    if (cudaStreamWaitEvent(b->cst[c], b->fork, 0) != cudaSuccess) return PD_ECUDA;
+  int rc = PD_OK;
+  for (int m : b->order) {
+    if (only_active && !b->h_active[m]) continue;
+    const pd_map& mp = b->maps[m];
+    const double* th = tuning ? b->tc_zero : mp.theta;
+    double* obj = tuning ? b->tc_out + m : mp.obj_out;
+    double* grad = tuning ? b->tc_out + b->tc_off[m] : mp.grad_out;
+    rc = plan_eval(&b->plans[m], th, b->eps, obj, grad, b->cst[b->chain[m]]);
+    if (rc) break;
+  }
+  // (the chains join back even after an error, so that a capture can end)
+  for (int c = 0; c < b->n_chains; ++c)
+    if (cudaEventRecord(b->join[c], b->cst[c]) != cudaSuccess || cudaStreamWaitEvent(st, b->join[c], 0) != cudaSuccess)
+      rc = rc ? rc : PD_ECUDA;
+  return rc;
+}
+
+// Captures the tensor-core evaluation of all maps as the plan's graph.
+int tc_capture(pd_batch* b, bool tuning) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PD_ECUDA;
+  cudaGraph_t graph = nullptr;
+  int rc = PD_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PD_ECUDA;
+  if (rc == PD_OK) {
+    rc = tc_enqueue(b, cs, tuning, false);
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess && rc == PD_OK) rc = PD_ECUDA;
+  }
+  if (rc == PD_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) rc = PD_ECUDA;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (rc) cudaGetLastError();
+  return rc;
+}
+
+void tc_free(pd_batch* b) {
+  for (auto& p : b->plans) plan_free(&p);
+  b->plans.clear();
+  for (int c = 0; c < kMaxChains; ++c) {
+    if (b->cst[c]) cudaStreamDestroy(b->cst[c]);
+    if (b->join[c]) cudaEventDestroy(b->join[c]);
+    b->cst[c] = nullptr;
+    b->join[c] = nullptr;
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  b->fork = nullptr;
+  cudaFree(b->tc_zero);
+  cudaFree(b->tc_out);
+  b->tc_zero = b->tc_out = nullptr;
+}
+
+double time_plan(pd_batch* b, int reps);
+
+// The tensor-core batch: plans, chains, tuning, the graph.
+int tc_build(pd_batch* b, int autotune) {
+  b->plans.assign(b->n_maps, PlanCore{});
+  size_t max_nk = 1, tot = (size_t)b->n_maps;
+  b->tc_off.assign(b->n_maps, 0);
+  for (int m = 0; m < b->n_maps; ++m) {
+    Geom g;
+    validate_grid(&b->maps[m].grid, &g);
+    const int rc = plan_init(&b->plans[m], g, 2, b->maps[m].labels, b->maps[m].N, b->d, b->prec, false);
+    if (rc) return rc;
+    const size_t nk = (size_t)b->maps[m].N * b->K;
+    max_nk = std::max(max_nk, nk);
+    b->tc_off[m] = tot;
+    tot += nk;
+  }
+  if (cudaMalloc(&b->tc_zero, sizeof(double) * max_nk) != cudaSuccess ||
+      cudaMalloc(&b->tc_out, sizeof(double) * tot) != cudaSuccess) {
+    cudaGetLastError();
+    return PD_ENOMEM;
+  }
+  if (cudaMemset(b->tc_zero, 0, sizeof(double) * max_nk) != cudaSuccess) return PD_ECUDA;
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return PD_ECUDA;
+  for (int c = 0; c < kMaxChains; ++c)
+    if (cudaStreamCreateWithFlags(&b->cst[c], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming) != cudaSuccess)
+      return PD_ECUDA;
+  // one direct evaluation of every map leaves its centre features and grain
+  // order in its plan, so that the graph holds only the per-call work
+  assign_chains(b, 1);
+  int rc = tc_enqueue(b, 0, true, false);
+  if (rc) return rc;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PD_ECUDA;
+  int best = 4;
+  if (autotune) {
+    double best_ms = 1e30;
+    for (int nc : {1, 2, 4, 8}) {
+      assign_chains(b, nc);
+      rc = tc_capture(b, true);
+      if (rc) return rc;
+      const double ms = time_plan(b, 3);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = nc;
+      }
+    }
+    b->tuned_ms = best_ms;
+  }
+  assign_chains(b, best);
+  b->tune = Tune{best, 0};
+  return tc_capture(b, false);
+}
+
 double time_plan(pd_batch* b, int reps) {
   cudaStream_t st;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -463,7 +613,7 @@ extern "C" int pd_batch_create(int n_maps, const pd_map* maps, const pd_eval_opt
   if (!out || n_maps < 1 || !maps || !opts) return PD_EINVAL;
   *out = nullptr;
   if (!(opts->eps > 0.0) || !isfinite(opts->eps) || opts->d < 1) return PD_EINVAL;
-  if (opts->prec != PD_FP64 && opts->prec != PD_FP32) return PD_ENOTSUP;
+  if (opts->prec < PD_FP64 || opts->prec > PD_BF16X3) return PD_EINVAL;
   if (opts->d > PD_MAX_DEGREE_2D) return PD_ENOTSUP;
   for (int m = 0; m < n_maps; ++m) {
     Geom g;
@@ -488,6 +638,22 @@ extern "C" int pd_batch_create(int n_maps, const pd_map* maps, const pd_eval_opt
   }
   std::vector<int> ones(n_maps, 1);
   cudaMemcpy(b->d_active, ones.data(), sizeof(int) * n_maps, cudaMemcpyHostToDevice);
+  b->h_active.assign(n_maps, 1);
+  b->order.resize(n_maps);
+  for (int m = 0; m < n_maps; ++m) b->order[m] = m;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
+    return (double)maps[a].grid.P * maps[a].N > (double)maps[c].grid.P * maps[c].N;
+  });
+  if (is_tc(b->prec)) {
+    const int rc = tc_build(b, autotune);
+    b->tuned = autotune != 0;
+    if (rc) {
+      pd_batch_destroy(b);
+      return rc;
+    }
+    *out = b;
+    return PD_OK;
+  }
   if (b->prec == PD_FP64) occupancy<double>(b);
   else occupancy<float>(b);
   // autotune: the pass-2 chunking and the persistent grid size, cached per
@@ -540,11 +706,22 @@ extern "C" int pd_batch_create(int n_maps, const pd_map* maps, const pd_eval_opt
 
 extern "C" int pd_batch_eval(pd_batch* b, void* stream) {
   if (!b || !b->exec) return PD_EINVAL;
+  // tensor cores with some maps inactive: the active maps' evaluations are
+  // launched directly (the graph runs all maps)
+  if (is_tc(b->prec) && !b->all_active) return tc_enqueue(b, (cudaStream_t)stream, false, true);
   return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? PD_OK : PD_ECUDA;
 }
 
 extern "C" int pd_batch_set_active(pd_batch* b, const int32_t* active, void* stream) {
   if (!b || !active) return PD_EINVAL;
+  if (is_tc(b->prec)) {
+    b->all_active = true;
+    for (int m = 0; m < b->n_maps; ++m) {
+      b->h_active[m] = active[m] != 0;
+      b->all_active = b->all_active && b->h_active[m];
+    }
+    return PD_OK;
+  }
   return cudaMemcpyAsync(b->d_active, active, sizeof(int) * b->n_maps, cudaMemcpyHostToDevice,
                          (cudaStream_t)stream) == cudaSuccess
              ? PD_OK
@@ -562,6 +739,7 @@ extern "C" int pd_batch_info(const pd_batch* b, int* chunk_factor, int* occ_div,
 extern "C" void pd_batch_destroy(pd_batch* b) {
   if (!b) return;
   cudaDeviceSynchronize();
+  tc_free(b);
   free_plan_device(b);
   cudaFree(b->d_counters);
   cudaFree(b->d_active);
@@ -579,9 +757,9 @@ namespace {
 
 class Coordinator {
  public:
-  Coordinator(int n_maps, std::vector<int> Ns, int K, pd_batch* plan32, pd_batch* plan64, double* d_theta,
+  Coordinator(int n_maps, std::vector<int> Ns, int K, pd_batch* plan_lo, pd_batch* plan64, double* d_theta,
               double* d_obj, double* d_grad, cudaStream_t st)
-      : n_(n_maps), Ns_(std::move(Ns)), K_(K), plan32_(plan32), plan64_(plan64), d_theta_(d_theta),
+      : n_(n_maps), Ns_(std::move(Ns)), K_(K), plan_lo_(plan_lo), plan64_(plan64), d_theta_(d_theta),
         d_obj_(d_obj), d_grad_(d_grad), st_(st), running_(n_maps) {
     off_.resize(n_ + 1, 0);
     for (int m = 0; m < n_; ++m) off_[m + 1] = off_[m] + (size_t)Ns_[m] * K_;
@@ -617,24 +795,24 @@ class Coordinator {
 
  private:
   void run_round() {  // with mu_ held
-    std::vector<int32_t> a32(n_, 0), a64(n_, 0);
-    bool any32 = false, any64 = false;
+    std::vector<int32_t> alo(n_, 0), a64(n_, 0);
+    bool anylo = false, any64 = false;
     for (int m = 0; m < n_; ++m) {
       if (want_[m] == PD_FP64) {
         a64[m] = 1;
         any64 = true;
       } else if (want_[m] >= 0) {
-        a32[m] = 1;
-        any32 = true;
+        alo[m] = 1;
+        anylo = true;
       }
     }
     int rc = PD_OK;
     if (cudaMemcpyAsync(d_theta_, h_theta_.data(), sizeof(double) * h_theta_.size(), cudaMemcpyHostToDevice, st_) !=
         cudaSuccess)
       rc = PD_ECUDA;
-    if (rc == PD_OK && any32) {
-      rc = pd_batch_set_active(plan32_, a32.data(), st_);
-      if (rc == PD_OK) rc = pd_batch_eval(plan32_, st_);
+    if (rc == PD_OK && anylo) {
+      rc = pd_batch_set_active(plan_lo_, alo.data(), st_);
+      if (rc == PD_OK) rc = pd_batch_eval(plan_lo_, st_);
     }
     if (rc == PD_OK && any64) {
       rc = pd_batch_set_active(plan64_, a64.data(), st_);
@@ -657,7 +835,7 @@ class Coordinator {
   int n_;
   std::vector<int> Ns_;
   int K_;
-  pd_batch *plan32_, *plan64_;
+  pd_batch *plan_lo_, *plan64_;
   double *d_theta_, *d_obj_, *d_grad_;
   cudaStream_t st_;
   std::vector<size_t> off_;
@@ -706,7 +884,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
   const auto t0 = std::chrono::steady_clock::now();
   if (n_maps < 1 || !maps || !theta_io || !opts || !reports) return PD_EINVAL;
   if (opts->method != PD_METHOD_LBFGS || opts->lbfgs_m < 1) return PD_ENOTSUP;
-  if (opts->prec != PD_FP64 && opts->prec != PD_FP32) return PD_ENOTSUP;
+  if (opts->prec < PD_FP64 || opts->prec > PD_BF16X3) return PD_EINVAL;
   if (opts->init != PD_INIT_ZERO && opts->init != PD_INIT_GIVEN) return PD_ENOTSUP;
   if (opts->anneal_eps0 > opts->eps) return PD_ENOTSUP;  // annealing: pd_fit only
   cudaStream_t st = (cudaStream_t)stream;
@@ -734,10 +912,10 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
     bm[m].obj_out = d_obj + m;
     bm[m].grad_out = d_grad + off[m];
   }
-  pd_eval_opts e32{opts->d, opts->eps, PD_FP32}, e64{opts->d, opts->eps, PD_FP64};
-  pd_batch *p32 = nullptr, *p64 = nullptr;
+  pd_eval_opts elo{opts->d, opts->eps, opts->prec}, e64{opts->d, opts->eps, PD_FP64};
+  pd_batch *plo = nullptr, *p64 = nullptr;
   int rc = PD_OK;
-  if (opts->prec == PD_FP32) rc = pd_batch_create(n_maps, bm.data(), &e32, 1, &p32);
+  if (opts->prec != PD_FP64) rc = pd_batch_create(n_maps, bm.data(), &elo, 1, &plo);
   if (rc == PD_OK) rc = pd_batch_create(n_maps, bm.data(), &e64, 1, &p64);
   std::vector<std::vector<double>> th0(n_maps);
   for (int m = 0; rc == PD_OK && m < n_maps; ++m) {
@@ -747,7 +925,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
       rc = PD_ECUDA;
   }
   if (rc) {
-    pd_batch_destroy(p32);
+    pd_batch_destroy(plo);
     pd_batch_destroy(p64);
     cudaFree(d_theta);
     cudaFree(d_grad);
@@ -756,7 +934,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
   }
   std::vector<int> Ns(n_maps);
   for (int m = 0; m < n_maps; ++m) Ns[m] = maps[m].N;
-  Coordinator co(n_maps, Ns, K, p32, p64, d_theta, d_obj, d_grad, st);
+  Coordinator co(n_maps, Ns, K, plo, p64, d_theta, d_obj, d_grad, st);
   std::vector<int> rcs(n_maps, PD_OK);
   std::vector<std::thread> threads;
   threads.reserve(n_maps);
@@ -812,7 +990,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
   cudaFree(d_lab);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int m = 0; m < n_maps; ++m) reports[m].seconds = secs;
-  pd_batch_destroy(p32);
+  pd_batch_destroy(plo);
   pd_batch_destroy(p64);
   cudaFree(d_theta);
   cudaFree(d_grad);

@@ -64,7 +64,7 @@ int validate_grid(const pd_grid* grid, Geom* g) {
   return PD_OK;
 }
 
-static bool degree_ok(int dim, int d) {
+bool degree_ok(int dim, int d) {
   if (d < 1) return false;
   return dim == 2 ? d <= PD_MAX_DEGREE_2D : (dim == 3 ? d <= PD_MAX_DEGREE_3D : false);
 }

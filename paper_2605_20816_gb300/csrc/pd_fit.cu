@@ -46,9 +46,10 @@ namespace {
 
 class Problem : public Evaluator {
  public:
-  Problem(const pd_grid* grid, const Geom& g, const int32_t* labels, int N, int d, double eps,
+  // hvp: the fit takes Hessian-vector products (Newton-CG)
+  Problem(const pd_grid* grid, const Geom& g, const int32_t* labels, int N, int d, double eps, bool hvp,
           cudaStream_t st)
-      : grid_(grid), g_(g), labels_(labels), N_(N), d_(d), K_(basis_K(grid->dim, d)), eps_(eps), st_(st),
+      : grid_(grid), g_(g), labels_(labels), N_(N), d_(d), K_(basis_K(grid->dim, d)), eps_(eps), hvp_(hvp), st_(st),
         sc_(st) {
     d_theta_ = sc_.get<double>((size_t)N * K_);
     d_grad_ = sc_.get<double>((size_t)N * K_);
@@ -65,6 +66,7 @@ class Problem : public Evaluator {
     if (cudaMallocHost((void**)&h_grad_, sizeof(double) * (nk + 1)) != cudaSuccess) h_grad_ = nullptr;
   }
   ~Problem() override {
+    for (PlanCore& p : plans_) plan_free(&p);
     if (h_theta_) cudaFreeHost(h_theta_);
     if (h_v_) cudaFreeHost(h_v_);
     if (h_grad_) cudaFreeHost(h_grad_);
@@ -78,9 +80,10 @@ class Problem : public Evaluator {
   int eval(const Vec& x, int prec, double* f, Vec* gf) override {
     int rc = upload(x, d_theta_, h_theta_);
     if (rc) return rc;
-    EvalCall c{g_, grid_->dim, d_, N_, prec, eps_, labels_, d_theta_, nullptr, d_obj_, gf ? d_grad_ : nullptr,
-               nullptr};
-    rc = (prec == PD_BF16 || prec == PD_BF16X3) ? eval_tc(c, st_) : eval_simt(c, st_);
+    PlanCore* pl = nullptr;
+    rc = plan(prec, &pl);
+    if (rc) return rc;
+    rc = plan_eval(pl, d_theta_, eps_, d_obj_, gf ? d_grad_ : nullptr, st_);
     if (rc) return rc;
     const size_t nk = (size_t)N_ * K_;
     double* h_phi = h_grad_ + nk;
@@ -104,8 +107,10 @@ class Problem : public Evaluator {
     if (rc) return rc;
     rc = upload(v, d_v_, h_v_);
     if (rc) return rc;
-    EvalCall c{g_, grid_->dim, d_, N_, prec, eps_, labels_, d_theta_, d_v_, nullptr, nullptr, d_grad_};
-    rc = (prec == PD_BF16 || prec == PD_BF16X3) ? eval_tc(c, st_) : eval_simt(c, st_);
+    PlanCore* pl = nullptr;
+    rc = plan(prec, &pl);
+    if (rc) return rc;
+    rc = plan_hvp(pl, d_theta_, d_v_, eps_, d_grad_, st_);
     if (rc) return rc;
     if (cudaMemcpyAsync(h_grad_, d_grad_, sizeof(double) * (size_t)N_ * K_, cudaMemcpyDeviceToHost, st_) !=
         cudaSuccess)
@@ -136,6 +141,23 @@ class Problem : public Evaluator {
   }
 
  private:
+  // the plan of precision prec, made on first use: the scratch of every
+  // evaluation in that precision, and the centre features and grain order
+  // computed once for the whole fit
+  int plan(int prec, PlanCore** out) {
+    if (prec < PD_FP64 || prec > PD_BF16X3) return PD_EINVAL;
+    PlanCore& p = plans_[prec];
+    if (!p.mem) {
+      const int rc = plan_init(&p, g_, grid_->dim, labels_, N_, d_, prec, hvp_);
+      if (rc) {
+        plan_free(&p);
+        return rc;
+      }
+    }
+    *out = &p;
+    return PD_OK;
+  }
+
   // free blocks x -> full [N][K] with the last block zero, through the
   // pinned staging buffer h (asynchronous: every caller synchronises the
   // stream before it returns, so h is not rewritten while in flight)
@@ -152,7 +174,9 @@ class Problem : public Evaluator {
   const int32_t* labels_;
   int N_, d_, K_;
   double eps_;
+  bool hvp_;
   cudaStream_t st_;
+  PlanCore plans_[PD_BF16X3 + 1];
   Scratch sc_;
   double *d_theta_, *d_grad_, *d_v_, *d_obj_;
   int64_t* d_mis_;
@@ -442,7 +466,7 @@ extern "C" int pd_fit(const pd_grid* grid, const int32_t* labels, int N, const p
   rc = pd_check_labels(grid, labels, N, stream);
   if (rc) return rc;
 
-  Problem pb(grid, g, labels, N, opts->d, opts->eps, st);
+  Problem pb(grid, g, labels, N, opts->d, opts->eps, opts->method == PD_METHOD_NEWTON_CG, st);
   if (!pb.ok()) return PD_ENOMEM;
   const int K = pb.K();
 

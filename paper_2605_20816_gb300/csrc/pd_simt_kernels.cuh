@@ -975,8 +975,9 @@ int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* t
                                                                       Arith<float>::theta_scale(c.eps), thH, thL));
   if (hvp)
     PD_TIMED(st, "scale_theta", k_copy_pad<float><<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(c.v, N, K, KP, vS));
-  PD_TIMED(st, "centre_features",
-           (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ec)));
+  if (!(c.plan && c.plan->features))
+    PD_TIMED(st, "centre_features",
+             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ec)));
   PD_TIMED(st, "tile_refs",
            (k_tile_refs<K><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(thH, N, n_tiles, ec, ref)));
   const dim3 grid2(nch, gtiles);
@@ -1006,6 +1007,7 @@ int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* t
                                                                                        hvp ? c.hv : c.grad));
   }
   if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+  if (c.plan) c.plan->features = true;
   return PD_OK;
 }
 
@@ -1033,17 +1035,25 @@ int eval_simt_tiles(const EvalCall& c, cudaStream_t st) {
   const int64_t tpc = tiles_per_chunk(n_tiles, gtiles, sms);
   const int nch = (int)((n_tiles + tpc - 1) / tpc);
 
-  Scratch sc(st);
+  // (a plan makes every allocation on every call, so that its arena keeps
+  // the centre features at the same place)
+  const bool all = c.plan != nullptr;
+  Scratch sc(st, c.plan);
   float* thH = sc.get<float>((size_t)N * KP);
   float* thL = sc.get<float>((size_t)N * KP);
   float* vS = hvp ? sc.get<float>((size_t)N * KP) : nullptr;
   float2* ec = sc.get<float2>((size_t)n_tiles * K);
   float2* ref = sc.get<float2>((size_t)n_tiles);
-  float* lse = (want_grad || hvp) ? sc.get<float>((size_t)P) : nullptr;
+  float* lse = (want_grad || hvp || all) ? sc.get<float>((size_t)P) : nullptr;
   float* ubar = hvp ? sc.get<float>((size_t)P) : nullptr;
-  double* objp = (!hvp && c.obj) ? sc.get<double>((size_t)blocks1) : nullptr;
-  double* part = (want_grad || hvp) ? sc.get<double>((size_t)nch * N * K) : nullptr;
+  double* objp = (!hvp && (c.obj || all)) ? sc.get<double>((size_t)blocks1) : nullptr;
+  double* part = (want_grad || hvp || all) ? sc.get<double>((size_t)nch * N * K) : nullptr;
   if (!sc.ok()) return PD_ENOMEM;
+  if (sc.sizing()) {
+    c.plan->need = sc.used();
+    return PD_OK;
+  }
+  if (!c.obj) objp = nullptr;
   return launch_simt_tiles<DIM, D>(c, tm, thH, thL, vS, ec, ref, lse, ubar, objp, part, tpc, st);
 }
 
@@ -1066,14 +1076,19 @@ int eval_simt_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t ppc = ((tiles + nch - 1) / nch) * kPixTile;
   const int nch_eff = (int)((P + ppc - 1) / ppc);
 
-  Scratch sc(st);
+  const bool all = c.plan != nullptr;  // a plan makes every allocation on every call
+  Scratch sc(st, c.plan);
   T* thS = sc.get<T>((size_t)N * KP);
   T* vS = hvp ? sc.get<T>((size_t)N * KP) : nullptr;
-  T* lse = (want_grad || hvp) ? sc.get<T>((size_t)P) : nullptr;
+  T* lse = (want_grad || hvp || all) ? sc.get<T>((size_t)P) : nullptr;
   T* ubar = hvp ? sc.get<T>((size_t)P) : nullptr;
-  double* objp = (!hvp && c.obj) ? sc.get<double>((size_t)blocks1) : nullptr;
-  double* part = (want_grad || hvp) ? sc.get<double>((size_t)nch_eff * N * K) : nullptr;
+  double* objp = (!hvp && (c.obj || all)) ? sc.get<double>((size_t)blocks1) : nullptr;
+  double* part = (want_grad || hvp || all) ? sc.get<double>((size_t)nch_eff * N * K) : nullptr;
   if (!sc.ok()) return PD_ENOMEM;
+  if (sc.sizing()) {
+    c.plan->need = sc.used();
+    return PD_OK;
+  }
 
   const double tscale = Arith<T>::theta_scale(c.eps);
   const int64_t nth = (int64_t)N * KP;

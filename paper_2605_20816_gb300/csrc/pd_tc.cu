@@ -1028,7 +1028,10 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
 
   constexpr int KP = padded_K<float>(K);
   constexpr int K1 = DIM + 1;  // label moments of degree <= 1: counts and centroids for the grain order
-  Scratch sc(st);
+  // (a plan makes every allocation on every call, so that its arena keeps
+  // the centre features and the grain order at the same place)
+  const bool all = c.plan != nullptr;
+  Scratch sc(st, c.plan);
   uint8_t* img = sc.get<uint8_t>((size_t)Npad * row_bytes);
   float* th32t = sc.get<float>((size_t)K * Npad);
   float* thH = sc.get<float>((size_t)N * KP);  // float-float parameters for the centre logits
@@ -1039,21 +1042,29 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
-  double* part = c.grad ? sc.get<double>((size_t)n_cta2 * N * K) : nullptr;  // one partial per pass-2 CTA and grain
-  unsigned long long* lmom = nullptr;
+  double* part = (c.grad || all) ? sc.get<double>((size_t)n_cta2 * N * K) : nullptr;  // one partial per pass-2 CTA and grain
   // one bit per (128-grain block, tile): the block has a probability that
   // the gradient pass cannot neglect on the tile; then the tiles per block
   const int64_t n_words = (n_tiles + 31) / 32;
-  uint32_t* need = skip ? sc.get<uint32_t>((size_t)(Npad / 128) * n_words) : nullptr;
-  int* kept = skip ? sc.get<int>((size_t)(Npad / 128) * n_tiles) : nullptr;
-  int* nkept = skip ? sc.get<int>((size_t)(Npad / 128)) : nullptr;
-  int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
-  int* rank = order ? sc.get<int>((size_t)N) : nullptr;
-  if (order) lmom = sc.get<unsigned long long>((size_t)N * K1);
-  unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
-  const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
+  uint32_t* need = (skip || all) ? sc.get<uint32_t>((size_t)(Npad / 128) * n_words) : nullptr;
+  int* kept = (skip || all) ? sc.get<int>((size_t)(Npad / 128) * n_tiles) : nullptr;
+  int* nkept = (skip || all) ? sc.get<int>((size_t)(Npad / 128)) : nullptr;
+  int* perm = (order || all) ? sc.get<int>((size_t)Npad) : nullptr;
+  int* rank = (order || all) ? sc.get<int>((size_t)N) : nullptr;
+  unsigned long long* lmom = (order || all) ? sc.get<unsigned long long>((size_t)N * K1) : nullptr;
+  unsigned long long* masks = (bounds || all) ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
+  if (sc.sizing()) {
+    c.plan->need = sc.used();
+    return PD_OK;
+  }
+  if (!skip) need = nullptr, kept = nullptr, nkept = nullptr;
+  if (!order) perm = nullptr, rank = nullptr;
+  if (!bounds) masks = nullptr;
+  const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
+  const bool have_features = c.plan && c.plan->features;
+  const bool have_order = c.plan && c.plan->order;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
   if (need && cudaMemsetAsync(need, 0, sizeof(uint32_t) * (size_t)(Npad / 128) * n_words, st) != cudaSuccess)
     return PD_ECUDA;
@@ -1063,7 +1074,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   int bits = 0;
   while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
   const float fx = ldexpf(1.f, 62 - bits);
-  if (order) {
+  if (order && !have_order) {
     // the grains' label centroids (sums of 1 and x per grain) for the order
     if (cudaMemsetAsync(lmom, 0, sizeof(unsigned long long) * N * K1, st) != cudaSuccess) return PD_ECUDA;
     const int64_t nthr = n_tiles * kTcPixTile;
@@ -1085,8 +1096,9 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
              k_tc_theta_image<KS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, Npad, K, KW, scale,
                                                                                 nullptr, perm, img, th32t));
   }
-  PD_TIMED(st, "centre_features",
-           (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
+  if (!have_features)
+    PD_TIMED(st, "centre_features",
+             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
   PD_TIMED(st, "tc_tile_setup",
            (k_tc_tile_setup<DIM, D><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(
                c.g, tm, thH, thL, N, Npad, perm, ecg, offg, tb, bounds ? 1 : 0, masks)));
@@ -1126,7 +1138,12 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
                  (const unsigned long long*)nullptr, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P,
                  c.obj));
   }
-  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+  if (c.plan) {
+    c.plan->features = true;
+    c.plan->order = c.plan->order || order;
+  }
+  return PD_OK;
 }
 
 template <int KS>

@@ -674,6 +674,7 @@ constexpr float kP1Far = 130.f;
 // takes the compensated offsets and visits every block.
 // ---------------------------------------------------------------------------
 constexpr float kSetupMargin = 1.f;
+constexpr int kSetupChunk = 512;  // image rows per chunk of passes B and C (a multiple of 128)
 
 template <int DIM, int D>
 __global__ void __launch_bounds__(kRefThreads)
@@ -686,7 +687,11 @@ k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* 
   __shared__ __align__(16) float sech[kRefTiles][KP];
   __shared__ uint32_t smax[kRefTiles], slow[kRefTiles];
   __shared__ int srag[kRefTiles];
-  __shared__ uint32_t smb[kRefTiles][64];  // per tile and block: max of o + A, order-preserving bits
+  __shared__ uint32_t smb[kRefTiles][64];        // per tile and block: max of o + A, order-preserving bits
+  __shared__ float so[kRefTiles][kSetupChunk];   // offsets of the chunk's rows
+  __shared__ float sA[kSetupChunk];              // A of the chunk's rows (-1: no grain)
+  __shared__ uint32_t slist[kRefTiles * kSetupChunk];  // (tile, row) pairs that take the float-float offset
+  __shared__ int scount;
 
   const int64_t t0 = (int64_t)blockIdx.x * kRefTiles;
   const int nt = (int)min((int64_t)kRefTiles, tm.n_tiles - t0);
@@ -721,38 +726,60 @@ k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* 
       }
     }
   }
-  __syncthreads();
-  // pass B: the relative offsets of every image row
-  for (int r0 = 0; r0 < Npad; r0 += blockDim.x) {
-    const int r = r0 + threadIdx.x;  // image row (a warp's 32 rows lie in one 128-row block)
-    const bool live = r < Npad;
-    const int src = !live ? -1 : (perm ? perm[r] : (r < N ? r : -1));
-    float h[KP], l[K];
-    float A = 0.f;
+  // passes B and C, per chunk of image rows
+  for (int r0 = 0; r0 < Npad; r0 += kSetupChunk) {
+    const int nr = min(kSetupChunk, Npad - r0);  // a multiple of 128: whole warps in every loop below
+    __syncthreads();  // pass A's maxima are complete; the previous chunk is written out
+    if (threadIdx.x == 0) scount = 0;
+    __syncthreads();
+    // pass B: the fp32 offset of every (tile, row); the rows whose offset
+    // can matter (not far below the tile's reference) are listed for the
+    // float-float offset, so that only they pay for it
+    for (int rr = threadIdx.x; rr < nr; rr += blockDim.x) {
+      const int r = r0 + rr;
+      const int src = perm ? perm[r] : (r < N ? r : -1);
+      float h[KP];
+      float A = 0.f;
 #pragma unroll
-    for (int k = 0; k < KP; ++k) h[k] = src >= 0 ? thH[(int64_t)src * KP + k] : 0.f;
+      for (int k = 0; k < KP; ++k) h[k] = src >= 0 ? thH[(int64_t)src * KP + k] : 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      l[k] = src >= 0 ? thL[(int64_t)src * KP + k] : 0.f;
-      A = fmaf(fabsf(h[k]), tb.d[k], A);
-    }
-    for (int q = 0; q < nt; ++q) {
-      const float C = unord_f32(smax[q]);
-      const float L = unord_f32(slow[q]) - C - kSetupMargin;
-      const float o32 = centre_dot32<K>(h, sech[q]) - C;
-      const bool far = bounds && !srag[q] && o32 + A < L - 160.f;
-      float o = o32;
-      // (a branch the warp takes together: with grains in the Morton order
-      // of their label centroids, the rows of a warp are neighbours)
-      if (__any_sync(0xffffffffu, !far && src >= 0)) {
-        const float off_ff = ff_diff(ff_dot<K>(h, l, sec[q]), make_float2(C, 0.f));
-        if (!far) o = off_ff;
+      for (int k = 0; k < K; ++k) A = fmaf(fabsf(h[k]), tb.d[k], A);
+      sA[rr] = src >= 0 ? A : -1.f;
+      for (int q = 0; q < nt; ++q) {
+        const float C = unord_f32(smax[q]);
+        const float L = unord_f32(slow[q]) - C - kSetupMargin;
+        const float o32 = centre_dot32<K>(h, sech[q]) - C;
+        const bool far = bounds && !srag[q] && o32 + A < L - 160.f;
+        const bool near = src >= 0 && !far;
+        const unsigned bal = __ballot_sync(0xffffffffu, near);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&scount, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (near) slist[base + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)q << 16) | (uint32_t)rr;
+        so[q][rr] = src >= 0 ? o32 : 0.f;
       }
-      if (src < 0) o = 0.f;
-      if (live) off[(t0 + q) * Npad + r] = o;
-      if (bounds) {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, src >= 0 ? ord_f32(o + A) : 0u);
-        if (lane == 0 && m && live) atomicMax(&smb[q][r / 128], m);
+    }
+    __syncthreads();
+    const int cnt = scount;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int q = (int)(slist[e] >> 16), rr = (int)(slist[e] & 0xffffu);
+      const int r = r0 + rr;
+      const int src = perm ? perm[r] : r;
+      const float C = unord_f32(smax[q]);
+      so[q][rr] = ff_diff(ff_dot<K>(thH + (int64_t)src * KP, thL + (int64_t)src * KP, sec[q]), make_float2(C, 0.f));
+    }
+    __syncthreads();
+    // pass C: write the chunk out, and the block maxima of o + A
+    for (int rr = threadIdx.x; rr < nr; rr += blockDim.x) {
+      const int r = r0 + rr;  // (a warp's 32 rows lie in one 128-row block)
+      const float A = sA[rr];
+      for (int q = 0; q < nt; ++q) {
+        const float o = so[q][rr];
+        off[(t0 + q) * Npad + r] = o;
+        if (bounds) {
+          const uint32_t m = __reduce_max_sync(0xffffffffu, A >= 0.f ? ord_f32(o + A) : 0u);
+          if (lane == 0 && m) atomicMax(&smb[q][r / 128], m);
+        }
       }
     }
   }

@@ -690,7 +690,10 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   const int64_t n_words = (n_tiles + 31) / 32;
 
   constexpr int KP = padded_K<float>(K);
-  Scratch sc(st);
+  // (a plan makes every allocation on every call, so that its arena keeps
+  // the centre features and the grain order at the same place)
+  const bool all = c.plan != nullptr;
+  Scratch sc(st, c.plan);
   double* vsc = sc.get<double>(2);
   float* thH = sc.get<float>((size_t)N * KP);  // float-float parameters for the centre logits
   float* thL = sc.get<float>((size_t)N * KP);
@@ -705,21 +708,30 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   float* ubar = sc.get<float>((size_t)P);
   float4* ms = n_grp > 1 ? sc.get<float4>((size_t)n_grp * P) : nullptr;
   double* part = sc.get<double>((size_t)cpg * N * K);  // one partial per pass-2 CTA and grain
-  uint32_t* need = skip ? sc.get<uint32_t>((size_t)gblocks * n_words) : nullptr;
-  int* kept = skip ? sc.get<int>((size_t)gblocks * n_tiles) : nullptr;
-  int* nkept = skip ? sc.get<int>((size_t)gblocks) : nullptr;
+  uint32_t* need = (skip || all) ? sc.get<uint32_t>((size_t)gblocks * n_words) : nullptr;
+  int* kept = (skip || all) ? sc.get<int>((size_t)gblocks * n_tiles) : nullptr;
+  int* nkept = (skip || all) ? sc.get<int>((size_t)gblocks) : nullptr;
   constexpr int K1 = DIM + 1;  // label moments of degree <= 1: counts and centroids for the grain order
-  unsigned long long* lmom = order ? sc.get<unsigned long long>((size_t)N * K1) : nullptr;
-  int* perm = order ? sc.get<int>((size_t)Npad) : nullptr;
-  int* rank = order ? sc.get<int>((size_t)N) : nullptr;
-  unsigned long long* masks = bounds ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
-  const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
+  unsigned long long* lmom = (order || all) ? sc.get<unsigned long long>((size_t)N * K1) : nullptr;
+  int* perm = (order || all) ? sc.get<int>((size_t)Npad) : nullptr;
+  int* rank = (order || all) ? sc.get<int>((size_t)N) : nullptr;
+  unsigned long long* masks = (bounds || all) ? sc.get<unsigned long long>((size_t)n_tiles) : nullptr;
   int* status = sc.get<int>(1);
   if (!sc.ok()) return PD_ENOMEM;
+  if (sc.sizing()) {
+    c.plan->need = sc.used();
+    return PD_OK;
+  }
+  if (!skip) need = nullptr, kept = nullptr, nkept = nullptr;
+  if (!order) perm = nullptr, rank = nullptr;
+  if (!bounds) masks = nullptr;
+  const TileBound tb = bounds ? tile_bound<DIM, D>(c.g) : TileBound{};
+  const bool have_features = c.plan && c.plan->features;
+  const bool have_order = c.plan && c.plan->order;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PD_ECUDA;
   if (need && cudaMemsetAsync(need, 0, sizeof(uint32_t) * (size_t)gblocks * n_words, st) != cudaSuccess)
     return PD_ECUDA;
-  if (order) {
+  if (order && !have_order) {
     int bits = 0;
     while (bits < 62 && ((int64_t)1 << bits) <= P) ++bits;
     const float fx = ldexpf(1.f, 62 - bits);
@@ -752,8 +764,9 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   }
   // logits relative to the tiles' reference logits; u (not shift-invariant,
   // and of modest size) from plain fp32 centre parts
-  PD_TIMED(st, "centre_features",
-           (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
+  if (!have_features)
+    PD_TIMED(st, "centre_features",
+             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
   PD_TIMED(st, "tc_tile_setup",
            (k_tc_tile_setup<DIM, D><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(
                c.g, tm, thH, thL, N, Npad, perm, ecg, offg, tb, bounds ? 1 : 0, masks)));
@@ -783,7 +796,12 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
   PD_TIMED(st, "reduce_parts",
            k_tc_reduce_grad<<<(unsigned)((NK + 31) / 32), dim3(32, kRedPhases), 0, st>>>(
                part, cpg, NK, nullptr, 0.0, -1.0 / (c.eps * c.eps * (double)P), vsc, c.hv));
-  return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+  if (c.plan) {
+    c.plan->features = true;
+    c.plan->order = c.plan->order || order;
+  }
+  return PD_OK;
 }
 
 template <int KS>

@@ -116,6 +116,12 @@ def lib():
             L.pd_mlp_targets.argtypes = [vp, ip, ip, vp, vp]
             L.pd_warm_start.argtypes = [vp, gp, vp, ip, ip, C.c_double, ip, vp, C.POINTER(C.c_double), vp]
             L.pd_selftest_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int), vp]
+            L.pd_plan_create.argtypes = [gp, vp, ip, ip, ip, ip, C.POINTER(vp)]
+            L.pd_plan_objective_grad.argtypes = [vp, vp, dbl, vp, vp, vp]
+            L.pd_plan_hvp.argtypes = [vp, vp, vp, dbl, vp, vp]
+            L.pd_plan_scratch_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+            L.pd_plan_destroy.argtypes = [vp]
+            L.pd_plan_destroy.restype = None
             L.pd_release.argtypes = []
             L.pd_release.restype = None
             _lib = L
@@ -313,6 +319,57 @@ def pd_fit(grid: Grid, labels: torch.Tensor, N: int, d: int, eps: float, theta: 
     rep = pd_fit_report()
     _check(lib().pd_fit(grid.ref, _ptr(labels), N, C.byref(opts), _ptr(th), C.byref(rep), _stream()), "pd_fit")
     return th, rep.as_dict()
+
+
+PD_PLAN_HVP = 1
+
+
+class Plan:
+    """A pd_plan: repeated objective/gradient (and, with hvp=True,
+    Hessian-vector) evaluations on one pixel set and label map, with all
+    scratch allocated once.  The caller keeps grid and labels alive and
+    unchanged while the plan is used."""
+
+    def __init__(self, grid: Grid, labels: torch.Tensor, N: int, d: int, prec: int = PD_BF16X3,
+                 hvp: bool = False):
+        self._keep = (grid, labels)
+        self.N, self.d, self.K = int(N), int(d), pd_K(grid.dim, d)
+        h = C.c_void_p()
+        _check(lib().pd_plan_create(grid.ref, _ptr(labels), self.N, self.d, int(prec),
+                                    PD_PLAN_HVP if hvp else 0, C.byref(h)), "pd_plan_create")
+        self.h = h
+
+    def objective_grad(self, theta: torch.Tensor, eps: float, want_grad: bool = True, obj_out=None,
+                       grad_out=None):
+        """(Phi as a 0-d CUDA float64 tensor, grad [N, K] or None)."""
+        obj = obj_out if obj_out is not None else torch.empty((), dtype=torch.float64, device="cuda")
+        grad = None
+        if want_grad:
+            grad = grad_out if grad_out is not None else torch.empty_like(theta, dtype=torch.float64)
+        _check(lib().pd_plan_objective_grad(self.h, _ptr(theta), float(eps), _ptr(obj), _ptr(grad), _stream()),
+               "pd_plan_objective_grad")
+        return obj, grad
+
+    def hvp(self, theta: torch.Tensor, v: torch.Tensor, eps: float, out=None):
+        hv = out if out is not None else torch.empty_like(theta, dtype=torch.float64)
+        _check(lib().pd_plan_hvp(self.h, _ptr(theta), _ptr(v), float(eps), _ptr(hv), _stream()), "pd_plan_hvp")
+        return hv
+
+    def scratch_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(lib().pd_plan_scratch_bytes(self.h, C.byref(n)), "pd_plan_scratch_bytes")
+        return n.value
+
+    def close(self):
+        if self.h:
+            lib().pd_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _map(grid: Grid, labels, N, theta=None, obj=None, grad=None):

@@ -1,6 +1,10 @@
 """Shared test helpers: seeded problems built from the synthetic generators
-with labels rasterised by the oracle (never by the CUDA path)."""
+with labels rasterised by the oracle (never by the CUDA path), and a probe
+of the device's default memory pool for the tests of allocation-free
+calls."""
 from __future__ import annotations
+
+import ctypes
 
 import numpy as np
 
@@ -39,3 +43,28 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+# CUmemPool_attribute values of the CUDA driver API
+USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8
+
+
+class DefaultPool:
+    """The current device's default stream-ordered memory pool, read through
+    the driver API: the pool that the library's stream-ordered scratch comes from."""
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, USED_MEM_HIGH, ctypes.byref(zero)) == 0

@@ -1,6 +1,7 @@
 """Batched evaluation of many grain maps (one persistent launch per pass,
-replayed as a CUDA graph) against single-map calls, and the lockstep
-batched fit against single-map fits."""
+replayed as a CUDA graph; on the tensor cores one graph of the maps'
+single-map evaluations on parallel chains) against single-map calls and
+the oracle, and the lockstep batched fit against single-map fits."""
 import math
 
 import numpy as np
@@ -29,7 +30,10 @@ def make_maps(n, d=3, seed=0, small=False):
     return maps
 
 
-@pytest.mark.parametrize("prec,tol", [(pd.PD_FP64, 1e-12), (pd.PD_FP32, 1e-6)])
+# on the tensor cores a map's evaluation in the batch is the single-map
+# evaluation itself: bitwise equal
+@pytest.mark.parametrize("prec,tol", [(pd.PD_FP64, 1e-12), (pd.PD_FP32, 1e-6), (pd.PD_BF16, 0.0),
+                                      (pd.PD_BF16X3, 0.0)])
 @pytest.mark.parametrize("autotune", [False, True])
 def test_batch_matches_single_map_calls(prec, tol, autotune):
     d, eps = 3, 2e-2
@@ -78,7 +82,28 @@ def test_batch_matches_oracle_and_is_reproducible():
     b.close()
 
 
-def test_inactive_maps_untouched():
+def test_tc_batch_matches_oracle():
+    # BF16X3 within the reduced-precision bound of the single-map tests
+    d, eps = 3, 2e-2
+    raw = make_maps(6, d=d, seed=9, small=True)
+    keep = []
+    for shape, lab, N, th in raw:
+        tt = dev(th)
+        keep.append((pd.Grid(shape), dev(lab), N, tt, torch.empty((), dtype=torch.float64, device="cuda"),
+                     torch.empty_like(tt)))
+    b = pd.Batch(keep, d, eps, prec=pd.PD_BF16X3, autotune=True)
+    b.eval()
+    torch.cuda.synchronize()
+    assert b.info()["chunk_factor"] in (1, 2, 4, 8)
+    for (shape, lab, N, th), (*_, o, g) in zip(raw, keep):
+        phi_o, grad_o = O.objective_grad(O.Grid(shape), lab, N, d, eps, th)
+        assert abs(o.item() - phi_o) <= 1e-6 * abs(phi_o)
+        assert np.linalg.norm(g.cpu().numpy() - grad_o) <= 1e-5 * np.linalg.norm(grad_o)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [pd.PD_FP32, pd.PD_BF16X3])
+def test_inactive_maps_untouched(prec):
     d, eps = 2, 5e-2
     raw = make_maps(4, d=d, seed=3, small=True)
     keep = []
@@ -86,7 +111,7 @@ def test_inactive_maps_untouched():
         tt = dev(th)
         keep.append((pd.Grid(shape), dev(lab), N, tt, torch.full((), 7.0, dtype=torch.float64, device="cuda"),
                      torch.full_like(tt, 7.0)))
-    b = pd.Batch(keep, d, eps, prec=pd.PD_FP32, autotune=False)
+    b = pd.Batch(keep, d, eps, prec=prec, autotune=False)
     b.set_active([1, 0, 1, 0])
     b.eval()
     torch.cuda.synchronize()
@@ -95,6 +120,11 @@ def test_inactive_maps_untouched():
             assert o.item() == 7.0 and bool(torch.all(g == 7.0))
         else:
             assert o.item() != 7.0
+    # all active again: the graph evaluates every map
+    b.set_active([1, 1, 1, 1])
+    b.eval()
+    torch.cuda.synchronize()
+    assert all(o.item() != 7.0 for *_, o, g in keep)
     b.close()
 
 
@@ -120,4 +150,12 @@ def test_fit_batched_reaches_single_map_optima():
     reps2 = pd.pd_fit_batched(maps, thetas2, d, eps, max_iter=300, prec=pd.PD_FP32, refine_iter=600,
                               switch_rtol=1e-7, gtol=1e-12)
     for r, s in zip(reps2, single):
+        assert abs(r["phi"] - s["phi"]) <= 1e-8 * abs(s["phi"]), (r, s)
+    # a BF16X3 phase on the tensor cores + FP64 refinement, warm-started from
+    # a short FP64 run: the same optima
+    thetas3 = [torch.zeros_like(t) for t in thetas]
+    pd.pd_fit_batched(maps, thetas3, d, eps, max_iter=20)
+    reps3 = pd.pd_fit_batched(maps, thetas3, d, eps, init=pd.PD_INIT_GIVEN, max_iter=300, prec=pd.PD_BF16X3,
+                              refine_iter=600, switch_rtol=1e-7, gtol=1e-12)
+    for r, s in zip(reps3, single):
         assert abs(r["phi"] - s["phi"]) <= 1e-8 * abs(s["phi"]), (r, s)

@@ -83,5 +83,10 @@ def test_warm_start_gain():
               "%.2fs (+%.2fs prediction), reached=%s" % (s, N, ref["phi"], plain["iters"], t_plain, phi0, scale,
                                                          warm["iters"], t_warm, t_ws, warm["status"] == 3))
         assert phi0 > -math.log(N)          # better than the fully ambiguous start
-        assert warm["phi"] > ref["phi"] - 1e-3 * abs(ref["phi"])
+        # the gain: the warm-started ascent reaches the plain fit's objective,
+        # in fewer iterations and less wall time (prediction included)
+        assert warm["status"] == 3, warm
+        assert warm["iters"] < plain["iters"], (warm["iters"], plain["iters"])
+        assert t_ws + t_warm < t_plain, (t_ws + t_warm, t_plain)
+    print("iterations plain / warm: %s" % [(r[0], r[1]) for r in rows])
     net.close()

@@ -5,8 +5,6 @@ is a fixed array inside the library, so it must give the same results as
 pd_objective_grad, call after call, even though every call reuses the same
 array.  This file is collected last so that a failure here does not stop a
 `-x` run before the other tests have run."""
-import ctypes
-
 import numpy as np
 import pytest
 import torch
@@ -14,32 +12,9 @@ import torch
 import oracle as O
 from paper_2605_20816_gb300 import pd, synth
 
+from helpers import USED_MEM_CURRENT, USED_MEM_HIGH, DefaultPool
+
 pytestmark = pytest.mark.gpu
-
-# CUmemPool_attribute values of the CUDA driver API
-_USED_MEM_CURRENT, _USED_MEM_HIGH = 7, 8
-
-
-class _DefaultPool:
-    """The current device's default stream-ordered memory pool, read through
-    the driver API: the pool pd_objective_grad's scratch would come from."""
-
-    def __init__(self):
-        self.cu = ctypes.CDLL("libcuda.so.1")
-        dev = ctypes.c_int()
-        assert self.cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
-        self.pool = ctypes.c_void_p()
-        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
-
-    def get(self, attr):
-        v = ctypes.c_uint64()
-        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
-        return v.value
-
-    def reset_high(self):
-        zero = ctypes.c_uint64(0)
-        assert self.cu.cuMemPoolSetAttribute(self.pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0
-
 
 def _problem(seed, shape, N, d, scale):
     g = O.Grid(shape)
@@ -60,13 +35,13 @@ def test_noalloc_matches_objective_grad_twice(prec, tol_phi, tol_grad):
         torch.cuda.synchronize()
         # the entry point's defining property: no device allocation, neither
         # from the driver's default pool nor from torch's allocator
-        pool = _DefaultPool()
-        used0 = pool.get(_USED_MEM_CURRENT)
+        pool = DefaultPool()
+        used0 = pool.get(USED_MEM_CURRENT)
         pool.reset_high()
         torch_allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
         pd.pd_objective_grad_noalloc(grid, lab, N, th, d, eps, prec=prec, obj_out=obj, grad_out=grad)
         torch.cuda.synchronize()
-        assert pool.get(_USED_MEM_HIGH) <= used0, (pool.get(_USED_MEM_HIGH), used0)
+        assert pool.get(USED_MEM_HIGH) <= used0, (pool.get(USED_MEM_HIGH), used0)
         assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == torch_allocs0
         a, b = obj.item(), want_obj.item()
         assert abs(a - b) <= tol_phi * abs(b), (call, a, b)
