@@ -707,25 +707,41 @@ k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* 
     srag[threadIdx.x] = g.coords ? 1 : (tile_pixel<DIM>(g, tm, t0 + threadIdx.x, kTcPixTile - 1, x, c) < 0);
   }
   load_centre_features<K>(ec, t0, nt, sec, sech);  // (its barrier covers the set-up above)
-  // pass A: C(t) = max_i f_i and max_i (f_i - A_i) over all grains (caller order)
-  for (int i0 = 0; i0 < N; i0 += blockDim.x) {
-    const int i = i0 + threadIdx.x;
+  // pass A: C(t) = max_i f_i and max_i (f_i - A_i) over all grains (caller
+  // order), as running maxima per thread (order-preserving bits, 0 =
+  // nothing) reduced once per tile and warp
+  uint32_t mo[kRefTiles], mlo[kRefTiles];
+#pragma unroll
+  for (int q = 0; q < kRefTiles; ++q) mo[q] = mlo[q] = 0u;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
     float h[KP];
+#pragma unroll
+    for (int k = 0; k < KP; k += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(thH + (int64_t)i * KP + k);
+      h[k] = v.x, h[k + 1] = v.y, h[k + 2] = v.z, h[k + 3] = v.w;
+    }
     float A = 0.f;
 #pragma unroll
-    for (int k = 0; k < KP; ++k) h[k] = i < N ? thH[(int64_t)i * KP + k] : 0.f;
-#pragma unroll
     for (int k = 0; k < K; ++k) A = fmaf(fabsf(h[k]), tb.d[k], A);
-    for (int q = 0; q < nt; ++q) {
-      const float f = centre_dot32<K>(h, sech[q]);
-      const uint32_t m = __reduce_max_sync(0xffffffffu, i < N ? ord_f32(f) : 0u);
-      const uint32_t lo = __reduce_max_sync(0xffffffffu, i < N ? ord_f32(f - A) : 0u);
+#pragma unroll
+    for (int q = 0; q < kRefTiles; ++q)
+      if (q < nt) {
+        const float f = centre_dot32<K>(h, sech[q]);
+        mo[q] = max(mo[q], ord_f32(f));
+        mlo[q] = max(mlo[q], ord_f32(f - A));
+        asm volatile("" ::: "memory");  // one tile at a time: no feature rows of later tiles held early
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < kRefTiles; ++q)
+    if (q < nt) {
+      const uint32_t m = __reduce_max_sync(0xffffffffu, mo[q]);
+      const uint32_t lo = __reduce_max_sync(0xffffffffu, mlo[q]);
       if (lane == 0) {
         if (m) atomicMax(&smax[q], m);
         if (lo) atomicMax(&slow[q], lo);
       }
     }
-  }
   // passes B and C, per chunk of image rows
   for (int r0 = 0; r0 < Npad; r0 += kSetupChunk) {
     const int nr = min(kSetupChunk, Npad - r0);  // a multiple of 128: whole warps in every loop below
@@ -735,29 +751,42 @@ k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* 
     // pass B: the fp32 offset of every (tile, row); the rows whose offset
     // can matter (not far below the tile's reference) are listed for the
     // float-float offset, so that only they pay for it
+    float Cq[kRefTiles], Lq[kRefTiles];
+#pragma unroll
+    for (int q = 0; q < kRefTiles; ++q) {
+      Cq[q] = unord_f32(smax[q]);
+      Lq[q] = unord_f32(slow[q]) - Cq[q] - kSetupMargin;
+    }
     for (int rr = threadIdx.x; rr < nr; rr += blockDim.x) {
       const int r = r0 + rr;
       const int src = perm ? perm[r] : (r < N ? r : -1);
       float h[KP];
-      float A = 0.f;
 #pragma unroll
-      for (int k = 0; k < KP; ++k) h[k] = src >= 0 ? thH[(int64_t)src * KP + k] : 0.f;
+      for (int k = 0; k < KP; k += 4) {
+        const float4 v = src >= 0 ? *reinterpret_cast<const float4*>(thH + (int64_t)src * KP + k)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        h[k] = v.x, h[k + 1] = v.y, h[k + 2] = v.z, h[k + 3] = v.w;
+      }
+      float A = 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) A = fmaf(fabsf(h[k]), tb.d[k], A);
       sA[rr] = src >= 0 ? A : -1.f;
-      for (int q = 0; q < nt; ++q) {
-        const float C = unord_f32(smax[q]);
-        const float L = unord_f32(slow[q]) - C - kSetupMargin;
-        const float o32 = centre_dot32<K>(h, sech[q]) - C;
-        const bool far = bounds && !srag[q] && o32 + A < L - 160.f;
-        const bool near = src >= 0 && !far;
-        const unsigned bal = __ballot_sync(0xffffffffu, near);
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&scount, __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (near) slist[base + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)q << 16) | (uint32_t)rr;
-        so[q][rr] = src >= 0 ? o32 : 0.f;
-      }
+#pragma unroll
+      for (int q = 0; q < kRefTiles; ++q)
+        if (q < nt) {
+          const float o32 = centre_dot32<K>(h, sech[q]) - Cq[q];
+          const bool far = bounds && !srag[q] && o32 + A < Lq[q] - 160.f;
+          const bool near = src >= 0 && !far;
+          const unsigned bal = __ballot_sync(0xffffffffu, near);
+          if (bal) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&scount, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (near) slist[base + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)q << 16) | (uint32_t)rr;
+          }
+          so[q][rr] = src >= 0 ? o32 : 0.f;
+          asm volatile("" ::: "memory");
+        }
     }
     __syncthreads();
     const int cnt = scount;
@@ -773,14 +802,16 @@ k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* 
     for (int rr = threadIdx.x; rr < nr; rr += blockDim.x) {
       const int r = r0 + rr;  // (a warp's 32 rows lie in one 128-row block)
       const float A = sA[rr];
-      for (int q = 0; q < nt; ++q) {
-        const float o = so[q][rr];
-        off[(t0 + q) * Npad + r] = o;
-        if (bounds) {
-          const uint32_t m = __reduce_max_sync(0xffffffffu, A >= 0.f ? ord_f32(o + A) : 0u);
-          if (lane == 0 && m) atomicMax(&smb[q][r / 128], m);
+#pragma unroll
+      for (int q = 0; q < kRefTiles; ++q)
+        if (q < nt) {
+          const float o = so[q][rr];
+          off[(t0 + q) * Npad + r] = o;
+          if (bounds) {
+            const uint32_t m = __reduce_max_sync(0xffffffffu, A >= 0.f ? ord_f32(o + A) : 0u);
+            if (lane == 0 && m) atomicMax(&smb[q][r / 128], m);
+          }
         }
-      }
     }
   }
   __syncthreads();
