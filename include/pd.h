@@ -329,7 +329,9 @@ int pd_fit(const pd_grid* grid, const int32_t* labels, int N,
 /* One grain map of a batch (2-D pixel sets).  Pointers are device pointers
  * owned by the caller and must stay valid while a batch built on them is
  * used.  theta, obj_out and grad_out are read/written by pd_batch_eval;
- * pd_fit_batched ignores them (it uses theta_io). */
+ * pd_fit_batched ignores them (it uses theta_io).  target_phi is read by
+ * pd_fit_batched only: this map's objective target (as pd_fit_opts'
+ * target_phi), or NaN to take opts->target_phi. */
 typedef struct pd_map {
   pd_grid grid;
   const int32_t* labels; /* [P], each in 0..N-1 */
@@ -337,6 +339,7 @@ typedef struct pd_map {
   const double* theta;   /* [N][K] */
   double* obj_out;       /* scalar Phi of this map */
   double* grad_out;      /* [N][K] grad Phi, or NULL */
+  double target_phi;     /* pd_fit_batched: per-map target, or NaN */
 } pd_map;
 
 typedef struct pd_batch pd_batch;

@@ -943,7 +943,9 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
       const int N = maps[m].N;
       BatchedMap ev(&co, m, N, K);
       FitState fs;
-      int r = fit_run(ev, th0[m], N, K, *opts, &fs);
+      pd_fit_opts om = *opts;
+      if (!isnan(maps[m].target_phi)) om.target_phi = maps[m].target_phi;
+      int r = fit_run(ev, th0[m], N, K, om, &fs);
       // final double-precision evaluation for the report
       if (r == PD_OK && fs.final_prec != PD_FP64) {
         std::vector<double> gf;

@@ -21,6 +21,7 @@
 
 #include "pd.h"
 #include "pd_internal.h"
+#include "pd_tc_common.cuh"
 
 struct pd_mlp {
   int n_in = 0, n_h1 = 0, n_h2 = 0, n_out = 0;
@@ -36,66 +37,180 @@ struct pd_mlp {
 namespace pd {
 namespace {
 
-constexpr int kGemmTile = 64;
-constexpr int kGemmK = 16;
-
-__device__ __forceinline__ float ld_f(const float* p) { return *p; }
-__device__ __forceinline__ float ld_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
+// ---------------------------------------------------------------------------
+// The network's GEMMs on the tensor cores (tcgen05.mma kind::f16, fp32
+// accumulation in TMEM).
+//
 // C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]) with A(m,k) = A[m*sam + k*sak],
 // B(k,n) = B[k*sbk + n*sbn]; EPI 0: plain, 1: ReLU, 2: multiply by
 // (mask[m*ldm + n] > 0) (ReLU derivative).  Split-K over blockIdx.z writes
 // slice z of C (C + z*M*ldc), k in [z*kchunk, (z+1)*kchunk).
+//
+// A CTA (4 warps) owns a 128 x kMmaN tile of C in TMEM.  The K range runs
+// in chunks of 32, staged by all threads into shared memory (two stages) in
+// the canonical K-major layout without swizzle: rows of A are the MMA's M
+// rows, rows of B its N rows.  A bf16 operand (the weights) is one term; an
+// fp32 operand (activations, gradients) is split into three bf16 terms
+// hi + mid + lo (each the bf16 rounding of what the previous ones leave),
+// which hold it to about 2^-24 relative, and the products are those of
+// the terms whose weight reaches 2^-16 of the leading one (hh, hm, mh, hl,
+// mm, lh: six for fp32 x fp32; three for fp32 x bf16), smallest first: the
+// products of the network's bf16 weights with fp32 data, accumulated in
+// fp32, as the CUDA cores would form them.  One thread issues the MMAs;
+// every wait on the MMAs is bounded (a wait that gives up makes the tile
+// NaN).
+// ---------------------------------------------------------------------------
+constexpr int kMmaN = 64;        // N of the MMA (columns of the C tile)
+constexpr int kMmaKC = 32;       // K per staged chunk
+constexpr int kGemmThreads = 128;
+constexpr uint32_t kStageA = 128 * kMmaKC * 2;    // bytes of one A term per stage
+constexpr uint32_t kStageB = kMmaN * kMmaKC * 2;  // bytes of one B term per stage
+
+template <typename T>
+__host__ __device__ constexpr int gemm_terms() { return std::is_same<T, float>::value ? 3 : 1; }
+template <typename TA, typename TB>
+__host__ __device__ constexpr uint32_t gemm_stage_bytes() {
+  return gemm_terms<TA>() * kStageA + gemm_terms<TB>() * kStageB;
+}
+
+// bf16 terms of a value: three for fp32, the value itself for bf16.
+__device__ __forceinline__ void bf16_terms(float a, __nv_bfloat16* t) {
+  t[0] = __float2bfloat16_rn(a);
+  const float r1 = a - __bfloat162float(t[0]);
+  t[1] = __float2bfloat16_rn(r1);
+  t[2] = __float2bfloat16_rn(r1 - __bfloat162float(t[1]));
+}
+__device__ __forceinline__ void bf16_terms(__nv_bfloat16 a, __nv_bfloat16* t) { t[0] = a; }
+
+// Stages rows x kMmaKC values of an operand: value (r, kk) = X[(row0 + r) *
+// sr + (k0 + kk) * sk] (zero outside rows < nrows, k < ke), term t at
+// dst + t * term_bytes, K-major (row width kMmaKC).
+template <typename T>
+__device__ __forceinline__ void stage_operand(const T* __restrict__ X, int64_t sr, int64_t sk, int row0, int nrows,
+                                              int k0, int ke, int rows, uint8_t* dst, uint32_t term_bytes) {
+  constexpr int NT = gemm_terms<T>();
+  const int n = rows * kMmaKC;
+  // consecutive threads along the unit-stride index: coalesced loads
+  const bool k_fast = sk == 1;
+  for (int e = threadIdx.x; e < n; e += kGemmThreads) {
+    const int r = k_fast ? e / kMmaKC : e % rows;
+    const int kk = k_fast ? e % kMmaKC : e / rows;
+    const int row = row0 + r, k = k0 + kk;
+    __nv_bfloat16 t[3];
+    if (row < nrows && k < ke) {
+      bf16_terms(X[(int64_t)row * sr + (int64_t)k * sk], t);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NT; ++q) t[q] = __float2bfloat16_rn(0.f);
+    }
+    const uint32_t o = kmaj(r, kk, kMmaKC);
+#pragma unroll
+    for (int q = 0; q < NT; ++q) *reinterpret_cast<__nv_bfloat16*>(dst + q * term_bytes + o) = t[q];
+  }
+}
+
 template <typename TA, typename TB, int EPI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kGemmThreads)
 k_gemm(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
        int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, const __nv_bfloat16* __restrict__ bias,
        const float* __restrict__ mask, int64_t ldm, int kchunk) {
-  __shared__ float As[kGemmK][kGemmTile + 4];
-  __shared__ float Bs[kGemmK][kGemmTile + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * kGemmTile, n0 = blockIdx.x * kGemmTile;
+  constexpr int NTA = gemm_terms<TA>(), NTB = gemm_terms<TB>();
+  constexpr uint32_t kStage = gemm_stage_bytes<TA, TB>();
+  extern __shared__ __align__(128) uint8_t gsm[];
+  __shared__ uint64_t bar_mma[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kMmaN;
   const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  float acc[4][4] = {};
-  for (int k0 = kb; k0 < ke; k0 += kGemmK) {
-    for (int e = threadIdx.x; e < kGemmTile * kGemmK; e += 256) {
-      const int r = e / kGemmK, c = e % kGemmK;
-      const int m = m0 + r, k = k0 + c;
-      As[c][r] = (m < M && k < ke) ? ld_f(A + (int64_t)m * sam + (int64_t)k * sak) : 0.f;
-      const int n = n0 + r;
-      Bs[c][r] = (n < N && k < ke) ? ld_f(B + (int64_t)k * sbk + (int64_t)n * sbn) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kGemmK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = As[kk][ty * 4 + i];
-        b[i] = Bs[kk][tx * 4 + i];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+  const int n_chunks = ke > kb ? (ke - kb + kMmaKC - 1) / kMmaKC : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  float* Cz = C + (int64_t)blockIdx.z * M * ldc;
+  if (warp == 0) tmem_alloc(&tmem_slot, kMmaN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  constexpr uint32_t idesc = idesc_bf16(128, kMmaN);
+  bool ok = true;
+  int issued = 0;  // chunks whose MMAs were issued and committed
+  for (int c = 0; c < n_chunks; ++c) {
+    const int s = c & 1;
+    // the stage is free once the MMAs of chunk c - 2 have read it
+    if (c >= 2) ok = mbar_wait(&bar_mma[s], (uint32_t)(((c - 2) >> 1) & 1), &abort_flag, nullptr) && ok;
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    uint8_t* sa = gsm + s * kStage;
+    uint8_t* sb = sa + NTA * kStageA;
+    const int k0 = kb + c * kMmaKC;
+    stage_operand<TA>(A, sam, sak, m0, M, k0, ke, 128, sa, kStageA);
+    stage_operand<TB>(B, sbn, sbk, n0, N, k0, ke, kMmaN, sb, kStageB);
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sb);
+      uint32_t acc = c > 0 ? 1u : 0u;  // the tile's first product initialises the accumulator
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
+      for (int kk = 0; kk < kMmaKC; kk += 16) {
+        // products hh, hm, mh, hl, mm, lh (the available ones), smallest first
+#pragma unroll
+        for (int p = 5; p >= 0; --p) {
+          const int ta = p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0);
+          const int tb = p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0);
+          if (ta >= NTA || tb >= NTB) continue;
+          const uint64_t da = smem_desc(a0 + ta * kStageA + (uint32_t)kk * 16u, 128u, kMmaKC * 16u);
+          const uint64_t db = smem_desc(b0 + tb * kStageB + (uint32_t)kk * 16u, 128u, kMmaKC * 16u);
+          mma_bf16(tmem, da, db, idesc, acc);
+          acc = 1u;
+        }
+      }
+      mma_commit(&bar_mma[s]);
+    }
+    issued = c + 1;
+  }
+  // all MMAs of the tile complete (the last commit covers them all)
+  if (issued > 0) {
+    const int c = issued - 1;
+    if (ok) ok = mbar_wait(&bar_mma[c & 1], (uint32_t)((c >> 1) & 1), &abort_flag, nullptr);
+    else if (threadIdx.x == 0) mbar_wait_drain(&bar_mma[c & 1], (uint32_t)((c >> 1) & 1));
+  }
+  ok = __syncthreads_and(ok);
+  tc_fence_after();
+  // epilogue: warp w holds rows m0 + 32 w + lane
+  float* Cz = C + (int64_t)blockIdx.z * M * ldc;
+  const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < kMmaN; c0 += 32) {
+    uint32_t r[32];
+    if (n_chunks > 0 && ok) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      tmem_wait_ld();
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(ok ? 0.f : __int_as_float(0x7fc00000));
+    }
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx * 4 + j;
+    for (int j = 0; j < 32; ++j) {
+      const int n = n0 + c0 + j;
       if (n >= N) continue;
-      float v = acc[i][j];
+      float v = __uint_as_float(r[j]);
       if (bias) v += __bfloat162float(bias[n]);
       if (EPI == 1) v = fmaxf(v, 0.f);
       if (EPI == 2) v = mask[(int64_t)m * ldm + n] > 0.f ? v : 0.f;
       Cz[(int64_t)m * ldc + n] = v;
     }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kMmaN);
   }
 }
 
@@ -238,12 +353,15 @@ template <typename TA, typename TB, int EPI>
 int gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
          int64_t sbn, float* C, int64_t ldc, const __nv_bfloat16* bias, const float* mask, int64_t ldm,
          int splits = 1) {
-  const int kchunk = ((K + splits - 1) / splits + kGemmK - 1) / kGemmK * kGemmK;
-  const int sz = (K + kchunk - 1) / kchunk;
-  dim3 grid((N + kGemmTile - 1) / kGemmTile, (M + kGemmTile - 1) / kGemmTile, sz);
-  PD_TIMED(st, "mlp_gemm",
-           (k_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, mask, ldm,
-                                                       kchunk)));
+  const int kchunk = ((K + splits - 1) / splits + kMmaKC - 1) / kMmaKC * kMmaKC;
+  const int sz = std::max(1, (K + kchunk - 1) / kchunk);
+  dim3 grid((N + kMmaN - 1) / kMmaN, (M + 127) / 128, sz);
+  constexpr int smem = 2 * (int)gemm_stage_bytes<TA, TB>();
+  auto k = k_gemm<TA, TB, EPI>;
+  // (a failure here is left in the runtime's last error, which the callers check)
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+  PD_TIMED(st, "mlp_gemm_tc",
+           (k<<<grid, kGemmThreads, smem, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, mask, ldm, kchunk)));
   return sz;
 }
 

@@ -60,7 +60,7 @@ class pd_fit_report(C.Structure):
 
 class pd_map(C.Structure):
     _fields_ = [("grid", pd_grid), ("labels", C.c_void_p), ("N", C.c_int), ("theta", C.c_void_p),
-                ("obj_out", C.c_void_p), ("grad_out", C.c_void_p)]
+                ("obj_out", C.c_void_p), ("grad_out", C.c_void_p), ("target_phi", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -372,8 +372,8 @@ class Plan:
             pass
 
 
-def _map(grid: Grid, labels, N, theta=None, obj=None, grad=None):
-    return pd_map(grid.c, _ptr(labels), int(N), _ptr(theta), _ptr(obj), _ptr(grad))
+def _map(grid: Grid, labels, N, theta=None, obj=None, grad=None, target_phi=math.nan):
+    return pd_map(grid.c, _ptr(labels), int(N), _ptr(theta), _ptr(obj), _ptr(grad), float(target_phi))
 
 
 class Batch:
@@ -417,11 +417,13 @@ class Batch:
 
 def pd_fit_batched(maps, thetas, d: int, eps: float, init: int = PD_INIT_ZERO, max_iter: int = 1000,
                    lbfgs_m: int = 10, prec: int = PD_FP64, refine_iter: int = 0, gtol: float = 0.0,
-                   target_phi: float = -math.inf, switch_rtol: float = 0.0):
-    """maps = [(grid, labels, N)], thetas = [CUDA float64 [N, K]] (in/out).
+                   target_phi: float = -math.inf, switch_rtol: float = 0.0, targets=None):
+    """maps = [(grid, labels, N)], thetas = [CUDA float64 [N, K]] (in/out),
+    targets = per-map objective targets (None: target_phi for all).
     Returns the list of per-map report dicts."""
     n = len(maps)
-    arr = (pd_map * n)(*[_map(g, lab, N) for g, lab, N in maps])
+    tg = [math.nan] * n if targets is None else [float(t) for t in targets]
+    arr = (pd_map * n)(*[_map(g, lab, N, target_phi=t) for (g, lab, N), t in zip(maps, tg)])
     ths = (C.c_void_p * n)(*[t.data_ptr() for t in thetas])
     opts = pd_fit_opts(d, float(eps), init, PD_METHOD_LBFGS, max_iter, lbfgs_m, 50, prec, refine_iter, gtol,
                        target_phi, switch_rtol)
