@@ -750,30 +750,48 @@ extern "C" void pd_batch_destroy(pd_batch* b) {
 // Lockstep batched ascent: one host thread per map runs the same optimiser
 // as pd_fit; every objective/gradient request goes to a coordinator that,
 // once all running maps have asked, evaluates all of them with one replay
-// of the batch graph (maps that are not asking are masked off).
+// of the batch graph (maps that are not asking are masked off).  A batch
+// plan is built when a round first needs its precision (the FP64 plan only
+// once some map refines), autotuned only for batches of at least
+// kTuneMaps maps (the timing costs more than it saves on a few maps), and
+// the trial parameters and results pass through pinned host buffers.
 // ---------------------------------------------------------------------------
 namespace pd {
 namespace {
 
+constexpr int kTuneMaps = 16;
+
 class Coordinator {
  public:
-  Coordinator(int n_maps, std::vector<int> Ns, int K, pd_batch* plan_lo, pd_batch* plan64, double* d_theta,
-              double* d_obj, double* d_grad, cudaStream_t st)
-      : n_(n_maps), Ns_(std::move(Ns)), K_(K), plan_lo_(plan_lo), plan64_(plan64), d_theta_(d_theta),
-        d_obj_(d_obj), d_grad_(d_grad), st_(st), running_(n_maps) {
+  // maps: the batch with theta/obj/grad pointing into d_theta/d_obj/d_grad
+  Coordinator(const std::vector<pd_map>& maps, int K, int d, double eps, double* d_theta, double* d_obj,
+              double* d_grad, cudaStream_t st)
+      : n_((int)maps.size()), K_(K), d_(d), eps_(eps), maps_(maps), d_theta_(d_theta), d_obj_(d_obj),
+        d_grad_(d_grad), st_(st), running_((int)maps.size()) {
     off_.resize(n_ + 1, 0);
-    for (int m = 0; m < n_; ++m) off_[m + 1] = off_[m] + (size_t)Ns_[m] * K_;
-    h_theta_.assign(off_[n_], 0.0);
-    h_grad_.assign(off_[n_], 0.0);
-    h_obj_.assign(n_, 0.0);
+    for (int m = 0; m < n_; ++m) off_[m + 1] = off_[m] + (size_t)maps_[m].N * K_;
+    if (cudaMallocHost((void**)&h_theta_, sizeof(double) * std::max<size_t>(off_[n_], 1)) != cudaSuccess ||
+        cudaMallocHost((void**)&h_grad_, sizeof(double) * std::max<size_t>(off_[n_], 1)) != cudaSuccess ||
+        cudaMallocHost((void**)&h_obj_, sizeof(double) * n_) != cudaSuccess) {
+      cudaGetLastError();
+      ok_ = false;
+    }
     want_.assign(n_, -1);
   }
+  ~Coordinator() {
+    for (pd_batch* b : plans_)
+      if (b) pd_batch_destroy(b);
+    if (h_theta_) cudaFreeHost(h_theta_);
+    if (h_grad_) cudaFreeHost(h_grad_);
+    if (h_obj_) cudaFreeHost(h_obj_);
+  }
+  bool ok() const { return ok_; }
   int64_t rounds = 0;
 
   // called from map m's thread; theta/grad are full [N][K] blocks
   int eval(int m, int prec, const double* theta, double* phi, double* grad) {
     std::unique_lock<std::mutex> lk(mu_);
-    memcpy(&h_theta_[off_[m]], theta, sizeof(double) * Ns_[m] * K_);
+    memcpy(&h_theta_[off_[m]], theta, sizeof(double) * maps_[m].N * K_);
     want_[m] = prec;
     ++waiting_;
     const int64_t my_round = round_;
@@ -784,7 +802,7 @@ class Coordinator {
     }
     if (rc_) return rc_;
     *phi = h_obj_[m];
-    memcpy(grad, &h_grad_[off_[m]], sizeof(double) * Ns_[m] * K_);
+    memcpy(grad, &h_grad_[off_[m]], sizeof(double) * maps_[m].N * K_);
     return PD_OK;
   }
   void finish() {
@@ -794,34 +812,38 @@ class Coordinator {
   }
 
  private:
+  // the batch plan of a precision, built on first use
+  int plan(int prec, pd_batch** out) {
+    if (!plans_[prec]) {
+      pd_eval_opts eo{d_, eps_, prec};
+      const int rc = pd_batch_create(n_, maps_.data(), &eo, n_ >= kTuneMaps ? 1 : 0, &plans_[prec]);
+      if (rc) return rc;
+    }
+    *out = plans_[prec];
+    return PD_OK;
+  }
+
   void run_round() {  // with mu_ held
-    std::vector<int32_t> alo(n_, 0), a64(n_, 0);
-    bool anylo = false, any64 = false;
-    for (int m = 0; m < n_; ++m) {
-      if (want_[m] == PD_FP64) {
-        a64[m] = 1;
-        any64 = true;
-      } else if (want_[m] >= 0) {
-        alo[m] = 1;
-        anylo = true;
-      }
-    }
+    std::vector<int32_t> act(n_);
     int rc = PD_OK;
-    if (cudaMemcpyAsync(d_theta_, h_theta_.data(), sizeof(double) * h_theta_.size(), cudaMemcpyHostToDevice, st_) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(d_theta_, h_theta_, sizeof(double) * off_[n_], cudaMemcpyHostToDevice, st_) != cudaSuccess)
       rc = PD_ECUDA;
-    if (rc == PD_OK && anylo) {
-      rc = pd_batch_set_active(plan_lo_, alo.data(), st_);
-      if (rc == PD_OK) rc = pd_batch_eval(plan_lo_, st_);
-    }
-    if (rc == PD_OK && any64) {
-      rc = pd_batch_set_active(plan64_, a64.data(), st_);
-      if (rc == PD_OK) rc = pd_batch_eval(plan64_, st_);
+    // one replay per precision that some waiting map asked for
+    for (int prec = PD_FP64; rc == PD_OK && prec <= PD_BF16X3; ++prec) {
+      bool any = false;
+      for (int m = 0; m < n_; ++m) {
+        act[m] = want_[m] == prec;
+        any = any || act[m];
+      }
+      if (!any) continue;
+      pd_batch* b = nullptr;
+      rc = plan(prec, &b);
+      if (rc == PD_OK) rc = pd_batch_set_active(b, act.data(), st_);
+      if (rc == PD_OK) rc = pd_batch_eval(b, st_);
     }
     if (rc == PD_OK &&
-        (cudaMemcpyAsync(h_obj_.data(), d_obj_, sizeof(double) * n_, cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
-         cudaMemcpyAsync(h_grad_.data(), d_grad_, sizeof(double) * h_grad_.size(), cudaMemcpyDeviceToHost, st_) !=
-             cudaSuccess))
+        (cudaMemcpyAsync(h_obj_, d_obj_, sizeof(double) * n_, cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
+         cudaMemcpyAsync(h_grad_, d_grad_, sizeof(double) * off_[n_], cudaMemcpyDeviceToHost, st_) != cudaSuccess))
       rc = PD_ECUDA;
     if (rc == PD_OK && cudaStreamSynchronize(st_) != cudaSuccess) rc = PD_ECUDA;
     rc_ = rc;
@@ -832,14 +854,15 @@ class Coordinator {
     cv_.notify_all();
   }
 
-  int n_;
-  std::vector<int> Ns_;
-  int K_;
-  pd_batch *plan_lo_, *plan64_;
+  int n_, K_, d_;
+  double eps_;
+  std::vector<pd_map> maps_;
+  pd_batch* plans_[PD_BF16X3 + 1] = {};
   double *d_theta_, *d_obj_, *d_grad_;
   cudaStream_t st_;
   std::vector<size_t> off_;
-  std::vector<double> h_theta_, h_grad_, h_obj_;
+  double *h_theta_ = nullptr, *h_grad_ = nullptr, *h_obj_ = nullptr;  // pinned
+  bool ok_ = true;
   std::vector<int> want_;
   std::mutex mu_;
   std::condition_variable cv_;
@@ -912,11 +935,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
     bm[m].obj_out = d_obj + m;
     bm[m].grad_out = d_grad + off[m];
   }
-  pd_eval_opts elo{opts->d, opts->eps, opts->prec}, e64{opts->d, opts->eps, PD_FP64};
-  pd_batch *plo = nullptr, *p64 = nullptr;
   int rc = PD_OK;
-  if (opts->prec != PD_FP64) rc = pd_batch_create(n_maps, bm.data(), &elo, 1, &plo);
-  if (rc == PD_OK) rc = pd_batch_create(n_maps, bm.data(), &e64, 1, &p64);
   std::vector<std::vector<double>> th0(n_maps);
   for (int m = 0; rc == PD_OK && m < n_maps; ++m) {
     th0[m].assign((size_t)maps[m].N * K, 0.0);
@@ -924,53 +943,58 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
         cudaMemcpy(th0[m].data(), theta_io[m], sizeof(double) * th0[m].size(), cudaMemcpyDeviceToHost) != cudaSuccess)
       rc = PD_ECUDA;
   }
-  if (rc) {
-    pd_batch_destroy(plo);
-    pd_batch_destroy(p64);
+  auto release = [&]() {
     cudaFree(d_theta);
     cudaFree(d_grad);
     cudaFree(d_obj);
+  };
+  if (rc) {
+    release();
     return rc;
   }
-  std::vector<int> Ns(n_maps);
-  for (int m = 0; m < n_maps; ++m) Ns[m] = maps[m].N;
-  Coordinator co(n_maps, Ns, K, plo, p64, d_theta, d_obj, d_grad, st);
   std::vector<int> rcs(n_maps, PD_OK);
-  std::vector<std::thread> threads;
-  threads.reserve(n_maps);
-  for (int m = 0; m < n_maps; ++m) {
-    threads.emplace_back([&, m]() {
-      const int N = maps[m].N;
-      BatchedMap ev(&co, m, N, K);
-      FitState fs;
-      pd_fit_opts om = *opts;
-      if (!isnan(maps[m].target_phi)) om.target_phi = maps[m].target_phi;
-      int r = fit_run(ev, th0[m], N, K, om, &fs);
-      // final double-precision evaluation for the report
-      if (r == PD_OK && fs.final_prec != PD_FP64) {
-        std::vector<double> gf;
-        r = ev.eval(fs.cur.x, PD_FP64, &fs.cur.f, &gf);
-        if (r == PD_OK) fs.cur.g = gf;
-      }
-      co.finish();
-      pd_fit_report& rep = reports[m];
-      memset(&rep, 0, sizeof(rep));
-      rep.phi = -fs.cur.f;
-      rep.gnorm = sqrt(dot(fs.cur.g, fs.cur.g));
-      rep.iters = fs.iters;
-      rep.iters_phase1 = fs.iters_phase1;
-      rep.evals = ev.evals;
-      rep.status = fs.status;
-      rcs[m] = r;
-      // gauge-fixed result
-      std::vector<double> th((size_t)N * K, 0.0);
-      for (int q = 0; q < (N - 1) * K; ++q) th[q] = fs.cur.x[q];
-      if (r == PD_OK && cudaMemcpy(theta_io[m], th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice) !=
-                            cudaSuccess)
-        rcs[m] = PD_ECUDA;
-    });
-  }
-  for (auto& t : threads) t.join();
+  {
+    Coordinator co(bm, K, opts->d, opts->eps, d_theta, d_obj, d_grad, st);
+    if (!co.ok()) {
+      release();
+      return PD_ENOMEM;
+    }
+    std::vector<std::thread> threads;
+    threads.reserve(n_maps);
+    for (int m = 0; m < n_maps; ++m) {
+      threads.emplace_back([&, m]() {
+        const int N = maps[m].N;
+        BatchedMap ev(&co, m, N, K);
+        FitState fs;
+        pd_fit_opts om = *opts;
+        if (!isnan(maps[m].target_phi)) om.target_phi = maps[m].target_phi;
+        int r = fit_run(ev, th0[m], N, K, om, &fs);
+        // final double-precision evaluation for the report
+        if (r == PD_OK && fs.final_prec != PD_FP64) {
+          std::vector<double> gf;
+          r = ev.eval(fs.cur.x, PD_FP64, &fs.cur.f, &gf);
+          if (r == PD_OK) fs.cur.g = gf;
+        }
+        co.finish();
+        pd_fit_report& rep = reports[m];
+        memset(&rep, 0, sizeof(rep));
+        rep.phi = -fs.cur.f;
+        rep.gnorm = sqrt(dot(fs.cur.g, fs.cur.g));
+        rep.iters = fs.iters;
+        rep.iters_phase1 = fs.iters_phase1;
+        rep.evals = ev.evals;
+        rep.status = fs.status;
+        rcs[m] = r;
+        // gauge-fixed result
+        std::vector<double> th((size_t)N * K, 0.0);
+        for (int q = 0; q < (N - 1) * K; ++q) th[q] = fs.cur.x[q];
+        if (r == PD_OK && cudaMemcpy(theta_io[m], th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice) !=
+                              cudaSuccess)
+          rcs[m] = PD_ECUDA;
+      });
+    }
+    for (auto& t : threads) t.join();
+  }  // (the coordinator's batch plans are freed here)
   // Err per map (double-precision assignment on the caller's stream)
   int64_t* d_mis = nullptr;
   int32_t* d_lab = nullptr;
@@ -992,11 +1016,7 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
   cudaFree(d_lab);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int m = 0; m < n_maps; ++m) reports[m].seconds = secs;
-  pd_batch_destroy(plo);
-  pd_batch_destroy(p64);
-  cudaFree(d_theta);
-  cudaFree(d_grad);
-  cudaFree(d_obj);
+  release();
   for (int m = 0; m < n_maps; ++m)
     if (rcs[m]) return rcs[m];
   return PD_OK;

@@ -13,6 +13,14 @@
 //           p_i(x) and accumulates (delta_{iG(x)} - p_i(x)) eta(x); per-tile
 //           sums are carried in double per pixel chunk.
 //   reduce: fixed-order double sum over chunks (bitwise reproducible).
+// PD_FP64 runs this structure over the pixel-linear order.  PD_FP32 runs it
+// over 128-pixel tiles (pd_tiles.cuh) with every logit relative to the
+// tile's reference C(t): the centre offset theta'_i . eta(c) - C(t) in
+// float-float, rounded once, plus the remainder theta'_i . (eta(x) -
+// eta(c)) in float from divided differences of the recurrence; pass 2
+// accumulates (delta - p) (eta(x) - eta(c)) and adds the tile's sum of
+// (delta - p) times eta(c) at the end of the tile, so that the float
+// accumulation acts on small numbers.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -2,54 +2,61 @@
 // gradient, PD_BF16 and PD_BF16X3.
 //
 // Both K-long contractions of eqs. (Phi) and (grad) run on the 5th-generation
-// tensor cores with bf16 operands in shared memory and fp32 accumulators in
-// tensor memory (TMEM); the CUDA cores keep only the soft-assignment
-// arithmetic (one ex2 per pixel-grain pair and pass) and the per-pixel
-// features.
+// tensor cores with bf16/fp16 operands in shared memory and fp32
+// accumulators in tensor memory (TMEM); the CUDA cores keep the
+// soft-assignment arithmetic (one ex2 per pixel-grain pair and pass) and the
+// per-pixel features.
 //
-// Pixels are processed in tiles of 128 neighbouring pixels, and every logit
-// is split at the tile centre (see TileMap below).
+// Pixels are processed in tiles of 128 neighbouring pixels (pd_tiles.cuh).
+// Every logit is taken relative to a per-tile reference C(t):
+//   l_i(x) - C(t) = [theta'_i . eta(c) - C(t)] + theta'_i . (eta(x) - eta(c)),
+// c the tile's centre pixel, theta' = -theta log2(e) / eps.  The bracket
+// (the centre offset, one float per tile and grain) is formed once per
+// evaluation by k_tc_tile_setup from float-float parameters and features
+// and rounded once; the tensor cores contract only the small remainder,
+// whose features eta(x) - eta(c) come from divided differences of the
+// Legendre recurrence (no cancellation).  The log-sum-exp is invariant
+// under the per-pixel shift, so log2 S(x) is kept relative to C(t) as well.
 //
 // pass 1  (one CTA per SM, persistent over 128-pixel tiles)
-//   A = features of 128 pixels (rows) x K, written by 128 producer
-//       threads from the in-register Legendre recurrence;
-//   B = all grains' scaled parameters -theta*log2(e)/eps (rows) x K, copied
-//       once per CTA from a prepared global image by a bulk (TMA) copy;
+//   A = eta(x) - eta(c) of 128 pixels (rows) x K, written by 128 producer
+//       threads from the in-register recurrences;
+//   B = all grains' scaled parameters (rows) x K, copied once per CTA from a
+//       prepared global image by a bulk (TMA) copy;
 //   D = A B^T, 128 pixels x 128 grains per MMA group, for the blocks of
-//       grains that the tile's mask keeps (k_tc_tile_masks); an epilogue
-//       warpgroup owns a tile, reads its pixel rows of logits and keeps an
-//       online log-sum-exp; out: log2 S(x) per pixel and per-CTA objective
-//       partials, and one bit per (tile, 128-grain block): whether any
-//       probability of the block on the tile reaches 2^-26.
+//       grains that the tile's mask keeps; an epilogue warpgroup owns a
+//       tile, adds the centre offsets, reads the label logit and keeps an
+//       online log-sum-exp; out: log2 S(x) per pixel, per-CTA objective
+//       partials, and one bit per (tile, 128-grain block): whether the
+//       block holds a probability that can survive in the gradient pass's
+//       fp16 operand, or the label of a pixel of the tile.
 // pass 2  (CTA = 128 grains x a share of the tiles whose bit is set)
-//   D1 = theta_block (128 grains x K) . eta(tile)^T (128 pixels): the
-//       logits transposed, so that a thread owns one grain's row;
-//   the thread forms c = -ex2(l - log2 S(x)) = -p_i(x) for its grain and
-//       writes it as the A operand (grains x pixels, K-major);
-//   D2 += C (128 grains x 128 pixels) . eta(tile) (128 pixels x K): the
-//       probability part of the gradient contraction, accumulated in TMEM
-//       over a chunk of tiles; the chunks add up in double to one partial
-//       per grain and CTA.  The label part sum_{x in G_i} eta(x) comes from
-//       a separate pass over the pixels (k_tc_label_moments).
+//   D1 = theta_block (128 grains x K) . (eta(x) - eta(c))^T (128 pixels):
+//       the logits transposed, so that a thread owns one grain's row;
+//   the thread forms c = delta_{i G(x)} - p_i(x) for its grain, written as
+//       an fp16 A operand (grains x pixels, K-major) in two terms for
+//       PD_BF16X3 (c_hi = fl16(c), c_lo = fl16((c - c_hi) 2^12)), one for
+//       PD_BF16;
+//   D2 += C (128 grains x 128 pixels) . eta(tile) (128 pixels x K, fp16 hi
+//       and lo columns), one TMEM accumulator per term of c, read out every
+//       kP2ChunkTiles tiles and summed in double to one partial per grain
+//       and CTA.  Since c = delta - p is small wherever the fit is good, the
+//       fp32 accumulation acts on small numbers.
 //   A (tile, block) pair whose bit is clear would only add zeros: every
-//   c = -p of it is below 2^-26 and rounds to zero in the fp16 operand, so
-//   leaving it out drops only exact zeros.  To make such pairs
-//   common, the parameter image lists the grains in the Morton order of
-//   their label centroids (k_tc_grain_order), so that a block of 128
-//   grains is a compact region and most tiles lie far from most blocks;
-//   the gradient partials go back to the caller's grain order.
+//   c = -p of it is below 2^-26 and rounds to zero in fp16, and no pixel of
+//   the tile has a label in the block.  To make such pairs common, the
+//   parameter image lists the grains in the Morton order of their label
+//   centroids (k_tc_grain_order), so that a block of 128 grains is a
+//   compact region and most tiles lie far from most blocks; the gradient
+//   partials go back to the caller's grain order.
 //
-// PD_BF16X3 splits every operand into three bf16 terms (hi + mid + lo,
-// about 24 significant bits) and forms the six products whose size is at
-// least 2^-16 of the leading one (hh, hm, mh, hl, mm, lh), which gives
-// float-level logits.  PD_BF16 uses one term for the logits.  The gradient
-// contraction takes c = -p in fp16 (11 significant bits, round to nearest)
-// against the features in fp16, split hi + lo for PD_BF16X3 (one MMA of
-// N = 2 KW per 16 pixels, the two column blocks added at the read-out) and
-// hi only for PD_BF16; its relative error stays near 1e-5 of the gradient,
-// below that of float logits at small eps.  An operand row stores each term once,
-// as KW-column slices side by side; a product is a run of MMAs whose two
-// descriptors start at the slices of its terms.
+// PD_BF16X3 splits every logit operand into three bf16 terms (hi + mid +
+// lo, about 24 significant bits) and forms the six products whose size is
+// at least 2^-16 of the leading one (hh, hm, mh, hl, mm, lh), smallest
+// first, which gives float-level logit remainders.  PD_BF16 uses one term.
+// An operand row stores each term once, as KW-column slices side by side; a
+// product is a run of MMAs whose two descriptors start at the slices of its
+// terms.
 #include "pd_tc_common.cuh"
 
 namespace pd {
@@ -62,10 +69,9 @@ namespace {
 // per block and product); the two epilogue warpgroups take alternate
 // tiles, each all blocks of its tile (so that a pixel's log-sum-exp needs
 // no exchange), through its own two 128-column TMEM buffers.  A block
-// whose logits are all more than 130 below the logit of the label grain of the tile's
-// centre pixel, everywhere in the tile (a bound from the centre logits,
-// see k_tc_centre_logits), would only add exponentials that underflow to
-// zero: it is not visited.
+// whose logits lie, everywhere in the tile, so far below the tile's
+// largest logit that their exponentials underflow to zero (a bound from the
+// centre offsets, see k_tc_tile_setup) is not visited.
 constexpr int kP1Bufs = 4;
 constexpr int kP1Stages = 3;  // pixel-operand stages at most (two tiles in the epilogue, one being written)
 

@@ -339,11 +339,12 @@ __device__ __forceinline__ bool is_consumer(int warp) { return warp < 8; }
 __device__ __forceinline__ bool is_producer(int warp) { return warp >= 8 && warp < kTcMmaWarp; }
 
 // ---------------------------------------------------------------------------
-// Centre logits theta'_i . eta(c_t) of every tile t and grain i, the fp32
-// part of the split logits of both passes (zero for padding grains).  A
-// block takes 256 grains (parameters in registers) and kCentreTiles tiles
-// (centre features in shared memory); the same fma order as a per-grain
-// fp32 dot product.
+// Centre parts theta'_i . eta(c_t) of every tile t and grain i in plain
+// fp32 (zero for padding grains): the Hessian passes take u = v . eta split
+// at the tile centre with these (u is not shift-invariant and of modest
+// size, so it needs no reference).  A block takes 256 grains (parameters in
+// registers) and kCentreTiles tiles (centre features in shared memory); the
+// same fma order as a per-grain fp32 dot product.
 //
 // With bounds (structured grids): the features of a tile's pixels differ
 // from those at its centre pixel by |eta_k(x) - eta_k(c)| <= D_k, where
@@ -830,7 +831,7 @@ k_tc_tile_setup(Geom g, TileMap tm, const float* __restrict__ thH, const float* 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// D_k of k_tc_centre_logits for a structured grid: the largest offset of
+// D_k of the tile bounds for a structured grid: the largest offset of
 // a tile's pixel from its centre pixel is TileShape_a / n_a along axis a.
 template <int DIM, int D>
 TileBound tile_bound(const Geom& g) {
