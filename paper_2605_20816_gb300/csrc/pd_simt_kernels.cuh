@@ -985,7 +985,7 @@ int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* t
     PD_TIMED(st, "scale_theta", k_copy_pad<float><<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(c.v, N, K, KP, vS));
   if (!(c.plan && c.plan->features))
     PD_TIMED(st, "centre_features",
-             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ec)));
+             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), kFeatThreads, 0, st>>>(c.g, tm, ec)));
   PD_TIMED(st, "tile_refs",
            (k_tile_refs<K><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(thH, N, n_tiles, ec, ref)));
   const dim3 grid2(nch, gtiles);

@@ -283,8 +283,10 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
                        !mbar_wait_warp(&bar_off_free[s], (uint32_t)((use - 1) & 1), &abort_flag, status)))
         break;
       if (p0 == 0) {
-        // the tile's centre logits of this launch's grains, by one bulk copy
-        // that the stage's barrier also waits for, and the blocks to visit
+        // the tile's centre offsets of this launch's grains, by one bulk
+        // copy that the stage's barrier also waits for, and the blocks to
+        // visit (one copy per visited block instead moves fewer bytes but
+        // made the pass slower: the copies are issued one after another)
         sMask[s] = maskc;
         fence_proxy_async();
         mbar_expect_tx(&bar_a_full[s], (uint32_t)Ng * 4);
@@ -766,16 +768,21 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
-          // l - log2 S = r + (off - lv), two pixels per packed fp32 add
+          // l - log2 S = r + (off - lv); two pixels per packed fp32
+          // operation throughout (each rounds as its scalar form would)
           const float2 t = __fadd2_rn(make_float2(off, off), make_float2(-lv[u], -lv[u + 1]));
           const float2 x = __fadd2_rn(make_float2(__uint_as_float(r[q8 + u]), __uint_as_float(r[q8 + u + 1])), t);
-          const float c0 = (lg[u] == gi ? 1.f : 0.f) - Arith<float>::ex(x.x);
-          const float c1 = (lg[u + 1] == gi ? 1.f : 0.f) - Arith<float>::ex(x.y);
-          const __half2 h = __floats2half2_rn(c0, c1);
+          const float2 pe = make_float2(Arith<float>::ex(x.x), Arith<float>::ex(x.y));
+          // c = delta - p
+          const float2 c = __ffma2_rn(pe, make_float2(-1.f, -1.f),
+                                      make_float2(lg[u] == gi ? 1.f : 0.f, lg[u + 1] == gi ? 1.f : 0.f));
+          const __half2 h = __floats2half2_rn(c.x, c.y);
           hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
           if (CT == 2) {
-            const float2 hf = __half22float2(h);
-            const __half2 l2 = __floats2half2_rn((c0 - hf.x) * kLoScale, (c1 - hf.y) * kLoScale);
+            // c - c_hi is exact in fp32, and the scaling by 2^12 too
+            const float2 dlo = __ffma2_rn(__half22float2(h), make_float2(-1.f, -1.f), c);
+            const float2 slo = __fmul2_rn(dlo, make_float2(kLoScale, kLoScale));
+            const __half2 l2 = __floats2half2_rn(slo.x, slo.y);
             lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
           }
         }
@@ -1092,19 +1099,16 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   }
   const double scale = Arith<float>::theta_scale(c.eps);
   {
-    const int64_t n = (int64_t)N * KP;
-    PD_TIMED(st, "theta_ff",
-             k_theta_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, K, KP, scale, thH, thL));
-  }
-  {
+    // the operand image, the transposed copy and the float-float parameters
     const int64_t n = (int64_t)Npad * KW;
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, Npad, K, KW, scale,
-                                                                                nullptr, perm, img, th32t));
+                                                                                nullptr, perm, img, th32t, thH, thL,
+                                                                                KP));
   }
   if (!have_features)
     PD_TIMED(st, "centre_features",
-             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
+             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), kFeatThreads, 0, st>>>(c.g, tm, ecg)));
   PD_TIMED(st, "tc_tile_setup",
            (k_tc_tile_setup<DIM, D><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(
                c.g, tm, thH, thL, N, Npad, perm, ecg, offg, tb, bounds ? 1 : 0, masks)));

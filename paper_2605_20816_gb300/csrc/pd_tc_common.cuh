@@ -258,13 +258,15 @@ __device__ __forceinline__ void store_eta_row(uint8_t* base, int r, const float*
 // Parameter images: rows = grains (in the order perm gives, when given;
 // padded to Npad with zero rows), K-major no-swizzle, one slice of KW
 // columns per term; plus a transposed float copy (K x Npad, in the
-// caller's grain order) used for the centre logits and the label logit of
-// the objective.
+// caller's grain order) used for the label logit of the objective, and
+// (thH != nullptr) the float-float parameters [N][KP] in the caller's order
+// (as k_theta_ff writes them) for the centre offsets.
 // ---------------------------------------------------------------------------
 template <int KS>
 __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Npad, int K, int KW, double scale,
                                  const double* __restrict__ dscale, const int* __restrict__ perm,
-                                 uint8_t* __restrict__ img, float* __restrict__ th32t) {
+                                 uint8_t* __restrict__ img, float* __restrict__ th32t, float* __restrict__ thH,
+                                 float* __restrict__ thL, int KP) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (row, k) pairs
   if (q >= (int64_t)Npad * KW) return;
   const int r = (int)(q / KW), k = (int)(q % KW);
@@ -280,13 +282,18 @@ __global__ void k_tc_theta_image(const double* __restrict__ theta, int N, int Np
   for (int t = 0; t < n_terms(KS); ++t) *reinterpret_cast<uint16_t*>(img + kmaj(r, t * KW + k, KT)) = parts[t];
   // transposed float copy in the caller's grain order, zero rows beyond N
   if (k < K) th32t[(int64_t)k * Npad + (src >= 0 ? src : r)] = (float)t;
+  if (thH && src >= 0 && k < KP) {
+    const float h32 = (float)t;
+    thH[(int64_t)src * KP + k] = h32;
+    thL[(int64_t)src * KP + k] = (float)(t - (double)h32);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Pixel tiles (pd_tiles.cuh).  The logits of a tile's pixels are formed
 // relative to the tile's reference logit C(t): the centre part
 // theta'_i . eta(c) - C(t) per grain and tile from float-float arithmetic
-// (k_tc_centre_offsets), the small remainder theta'_i . (eta(x) - eta(c)) on
+// (k_tc_tile_setup), the small remainder theta'_i . (eta(x) - eta(c)) on
 // the tensor cores, whose fp32 accumulation truncates (its biased error must
 // act on small numbers).
 // ---------------------------------------------------------------------------
@@ -573,9 +580,12 @@ k_tc_grain_order(const unsigned long long* __restrict__ lmom, int N, int K, int 
     uint32_t code = 0xffffffffu;
     if (cnt > 0) {
       code = 0;
+      // (a 10-bit cell per axis: float division is ample, and the
+      // double-precision one cost most of this kernel)
+      const float inv = 1.f / (float)cnt;
       for (int a = 0; a < DIM; ++a) {
-        const double c = (double)(long long)lmom[(int64_t)i * K + 1 + a] / (double)cnt;  // in [-1, 1]
-        int v = (int)((c + 1.0) * 512.0);
+        const float c = (float)(long long)lmom[(int64_t)i * K + 1 + a] * inv;  // in [-1, 1]
+        int v = (int)((c + 1.f) * 512.f);
         v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
         code |= spread_bits((uint32_t)v, DIM) << a;
       }

@@ -750,23 +750,18 @@ int eval_tc_hvp_dd(const EvalCall& c, cudaStream_t st) {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     PD_TIMED(st, "tc_theta_image",
              k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.theta, N, Npad, K, KW, Arith<float>::theta_scale(c.eps),
-                                                          nullptr, perm, img, th32t));
+                                                          nullptr, perm, img, th32t, thH, thL, KP));
     PD_TIMED(st, "tc_v_image",
-             k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.v, N, Npad, K, KW, 1.0, vsc + 1, perm, vimg, v32t));
+             k_tc_theta_image<KS><<<blocks, 256, 0, st>>>(c.v, N, Npad, K, KW, 1.0, vsc + 1, perm, vimg, v32t,
+                                                          nullptr, nullptr, 0));
   }
   const dim3 gridc((unsigned)((Npad + 255) / 256),
                    (unsigned)std::min<int64_t>((n_tiles + kCentreTiles - 1) / kCentreTiles, 4096));
-  {
-    const int64_t n = (int64_t)N * KP;
-    PD_TIMED(st, "theta_ff",
-             k_theta_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.theta, N, K, KP,
-                                                                      Arith<float>::theta_scale(c.eps), thH, thL));
-  }
   // logits relative to the tiles' reference logits; u (not shift-invariant,
   // and of modest size) from plain fp32 centre parts
   if (!have_features)
     PD_TIMED(st, "centre_features",
-             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), 256, 0, st>>>(c.g, tm, ecg)));
+             (k_centre_features<DIM, D><<<centre_feature_blocks(n_tiles), kFeatThreads, 0, st>>>(c.g, tm, ecg)));
   PD_TIMED(st, "tc_tile_setup",
            (k_tc_tile_setup<DIM, D><<<tile_centre_blocks(n_tiles), kRefThreads, 0, st>>>(
                c.g, tm, thH, thL, N, Npad, perm, ecg, offg, tb, bounds ? 1 : 0, masks)));

@@ -320,9 +320,11 @@ __device__ __forceinline__ float unord_f32(uint32_t o) {
 // The centre features eta(c_t) of every tile as float-float pairs, ec
 // [tiles][K]: one thread per tile runs the Legendre recurrence of each axis
 // in double (FP64 is slow on this part: once per axis, not per feature)
-// and forms the products.  They depend on the pixel set only.
+// and forms the products.  They depend on the pixel set only.  Small blocks
+// (kFeatThreads) spread the double-precision work over all SMs.
+constexpr int kFeatThreads = 32;
 template <int DIM, int D>
-__global__ void __launch_bounds__(256) k_centre_features(Geom g, TileMap tm, float2* __restrict__ ec) {
+__global__ void __launch_bounds__(kFeatThreads) k_centre_features(Geom g, TileMap tm, float2* __restrict__ ec) {
   constexpr int K = basis_K(DIM, D);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tm.n_tiles) return;
@@ -344,7 +346,9 @@ __global__ void __launch_bounds__(256) k_centre_features(Geom g, TileMap tm, flo
   }
 }
 
-inline unsigned centre_feature_blocks(int64_t n_tiles) { return (unsigned)((n_tiles + 255) / 256); }
+inline unsigned centre_feature_blocks(int64_t n_tiles) {
+  return (unsigned)((n_tiles + kFeatThreads - 1) / kFeatThreads);
+}
 
 // The centre features of tiles t0 .. t0+nt-1 from ec into shared memory:
 // float-float pairs sec[q][k] and hi parts sech[q][k] (rows padded to a
