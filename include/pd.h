@@ -163,8 +163,12 @@ int pd_hvp(const pd_grid* grid, const int32_t* labels, int N,
  * evaluation leaves in that scratch the Legendre features of every tile
  * centre (Omega only) and, for the tensor-core precisions, the grain order
  * (Morton order of the label centroids, G only), which later evaluations
- * reuse.  Plan evaluations allocate nothing and return results bitwise equal
- * to pd_objective_grad / pd_hvp with the same arguments.
+ * reuse.  Plan evaluations take no scratch allocation and return results
+ * bitwise equal to pd_objective_grad / pd_hvp with the same arguments.
+ * Calls that repeat the previous call's arguments (theta, v and output
+ * pointers, eps), as the evaluations of a fit do, replay a CUDA graph of
+ * the evaluation recorded on the second such call (kept until
+ * pd_plan_destroy); tracing (pd_prof_enable) runs every call directly.
  *
  * pd_plan_create: grid, labels, N, d and prec as for pd_objective_grad
  * (N >= 2, P >= 1); flags = 0, or PD_PLAN_HVP to also reserve the scratch of

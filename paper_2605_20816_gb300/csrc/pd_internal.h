@@ -121,6 +121,7 @@ class ProfScope {
   cudaStream_t st_;
   int idx_;
 };
+bool prof_enabled();  // pd_prof_enable is on
 #define PD_TIMED(st, name, ...) \
   do {                          \
     ::pd::ProfScope pd_ps_(st, name); \
@@ -147,11 +148,23 @@ void noalloc_forget_device();
 // A plan of evaluations on one pixel set and label map (pd_plan.cu): one
 // device allocation holding the arena of the objective/gradient and, when
 // asked for, the arena of the Hessian-vector product.
+// The evaluation of one kind recorded as a CUDA graph, with the arguments
+// it was recorded for.
+struct PlanGraph {
+  cudaGraphExec_t exec = nullptr;
+  const double *theta = nullptr, *v = nullptr;
+  double *obj = nullptr, *grad = nullptr, *hv = nullptr;
+  double eps = 0.0;
+  bool seen = false;  // the arguments were used by the last direct call
+};
 struct PlanCore {
   Geom g{};
   int dim = 0, d = 0, N = 0, prec = 0;
   const int32_t* labels = nullptr;
   PlanState eval, hvp;
+  PlanGraph geval, ghvp;
+  cudaStream_t cap = nullptr;  // capture stream (created on first use)
+  bool graphs = true;          // false once a capture failed
   bool with_hvp = false;
   char* mem = nullptr;
   size_t bytes = 0;

@@ -9,6 +9,14 @@
 // A sizing pass runs the evaluation's allocation sequence without a buffer
 // and records the bytes it needs; it returns before any launch, so its
 // pointer arguments are never read.
+//
+// Repeated calls with the same arguments (the same parameter, direction and
+// output pointers and the same eps, as in every evaluation of a fit) replay
+// a CUDA graph of the evaluation: the first call with new arguments runs
+// directly (and leaves the cached data), the second records the launches
+// on a private stream as a graph, and it and every later call launch that
+// graph on the caller's stream (one launch instead of about ten).  Tracing
+// (pd_prof_enable) runs every call directly.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <new>
@@ -67,16 +75,78 @@ int plan_init(PlanCore* p, const Geom& g, int dim, const int32_t* labels, int N,
   return PD_OK;
 }
 
+namespace {
+
+bool same_args(const PlanGraph& g, const double* theta, const double* v, double eps, double* obj, double* grad,
+               double* hv) {
+  return g.theta == theta && g.v == v && g.eps == eps && g.obj == obj && g.grad == grad && g.hv == hv;
+}
+
+// One evaluation of kind ps (graph gr): directly, or through the graph.
+int run_cached(PlanCore* p, PlanState* ps, PlanGraph* gr, const double* theta, const double* v, double eps,
+               double* obj, double* grad, double* hv, cudaStream_t st) {
+  // (a call recorded into the caller's own graph, as the tensor-core batch
+  // does, runs its launches directly into that graph)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return run(p, ps, theta, v, eps, obj, grad, hv, st);
+  const bool same = same_args(*gr, theta, v, eps, obj, grad, hv);
+  if (!p->graphs || prof_enabled() || !same || (!gr->exec && !gr->seen)) {
+    if (!same) {
+      gr->theta = theta, gr->v = v, gr->eps = eps, gr->obj = obj, gr->grad = grad, gr->hv = hv;
+      if (gr->exec) cudaGraphExecDestroy(gr->exec);
+      gr->exec = nullptr;
+    }
+    gr->seen = true;
+    return run(p, ps, theta, v, eps, obj, grad, hv, st);
+  }
+  if (!gr->exec) {
+    // record the launches of this call (no work runs on the capture stream)
+    if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      p->graphs = false;
+      return run(p, ps, theta, v, eps, obj, grad, hv, st);
+    }
+    cudaGraph_t graph = nullptr;
+    int rc = PD_OK;
+    if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PD_ECUDA;
+    if (rc == PD_OK) {
+      rc = run(p, ps, theta, v, eps, obj, grad, hv, p->cap);
+      if (cudaStreamEndCapture(p->cap, &graph) != cudaSuccess && rc == PD_OK) rc = PD_ECUDA;
+    }
+    if (rc == PD_OK && cudaGraphInstantiate(&gr->exec, graph, 0) != cudaSuccess) {
+      gr->exec = nullptr;
+      rc = PD_ECUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != PD_OK) {
+      // a capture that failed leaves nothing behind: run directly from now on
+      cudaGetLastError();
+      p->graphs = false;
+      return run(p, ps, theta, v, eps, obj, grad, hv, st);
+    }
+  }
+  return cudaGraphLaunch(gr->exec, st) == cudaSuccess ? PD_OK : PD_ECUDA;
+}
+
+}  // namespace
+
 int plan_eval(PlanCore* p, const double* theta, double eps, double* obj, double* grad, cudaStream_t st) {
-  return run(p, &p->eval, theta, nullptr, eps, obj, grad, nullptr, st);
+  return run_cached(p, &p->eval, &p->geval, theta, nullptr, eps, obj, grad, nullptr, st);
 }
 
 int plan_hvp(PlanCore* p, const double* theta, const double* v, double eps, double* hv, cudaStream_t st) {
   if (!p->with_hvp) return PD_EINVAL;
-  return run(p, &p->hvp, theta, v, eps, nullptr, nullptr, hv, st);
+  return run_cached(p, &p->hvp, &p->ghvp, theta, v, eps, nullptr, nullptr, hv, st);
 }
 
 void plan_free(PlanCore* p) {
+  if (p->geval.exec) cudaGraphExecDestroy(p->geval.exec);
+  if (p->ghvp.exec) cudaGraphExecDestroy(p->ghvp.exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
   if (p->mem) cudaFree(p->mem);
   *p = PlanCore{};
 }

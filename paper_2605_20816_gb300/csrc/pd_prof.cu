@@ -31,9 +31,21 @@ void clear_locked() {
 
 }  // namespace
 
+bool prof_enabled() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
+
 ProfScope::ProfScope(cudaStream_t st, const char* name) : st_(st), idx_(-1) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return;
+  // (launches recorded into a graph are not traced: their events would
+  // belong to the graph, not to a stream)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
   Rec r{name, nullptr, nullptr};
   if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
     cudaGetLastError();

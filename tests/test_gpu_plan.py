@@ -104,3 +104,28 @@ def test_plan_argument_errors():
     with pytest.raises(pd.PdError) as e:
         pd.Plan(grid, lab, N, 9)                             # above the 2-D maximum degree
     assert e.value.code == pd.PD_ENOTSUP
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_plan_graph_replay_follows_theta(prec):
+    # the calls of a fit: the same buffers every time, theta rewritten in
+    # place; from the second call on the plan replays a recorded graph,
+    # which must read the current theta and v
+    grid, lab, N, th0, v, K = _setup((200, 190), 60, 4, 17)
+    plan = pd.Plan(grid, lab, N, 4, prec=prec, hvp=True)
+    th = th0.clone()
+    obj = torch.empty((), dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(th)
+    hv = torch.empty_like(th)
+    vv = v.clone()
+    for rep in range(4):
+        th.copy_(th0 * (1.0 + 0.05 * rep))
+        vv.copy_(v * (1.0 - 0.1 * rep))
+        want_o, want_g = pd.pd_objective_grad(grid, lab, N, th, 4, 1e-2, prec=prec)
+        want_h = pd.pd_hvp(grid, lab, N, th, vv, 4, 1e-2, prec=prec)
+        plan.objective_grad(th, 1e-2, obj_out=obj, grad_out=grad)
+        plan.hvp(th, vv, 1e-2, out=hv)
+        torch.cuda.synchronize()
+        assert _same(obj, want_o) and _same(grad, want_g), rep
+        assert _same(hv, want_h), rep
+    plan.close()
