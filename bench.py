@@ -346,24 +346,41 @@ def time_to_fit(pd, grid, lab, N):
     """Time to reach the FP64 plain fit's objective: Phi_ref is Phi after
     1000 FP64 L-BFGS iterations from theta = 0 (the paper's budget, Sec.
     5.2); a form has reached it when Phi >= Phi_ref - 1e-8 |Phi_ref|.  The
-    plain FP32 form and the BF16X3 (tensor-core) form each run a first phase
-    of up to 3000 iterations that leaves when its relative gain per
-    iteration drops below 1e-7, then FP64 refinement; a target met in the
-    first phase must hold in FP64."""
+    plain FP32 form and the BF16X3 (tensor-core) forms, plain and
+    eps-annealed (ANNEAL), each run a first phase of up to 3000 iterations
+    that leaves when its relative gain per iteration drops below 1e-7, then
+    FP64 refinement; a target met in the first phase must hold in FP64."""
+    warm_up_fits(pd, grid, lab, N)
     t = time.perf_counter()
     _, ref = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=1000, prec=pd.PD_FP64)
     rows = {"fp64_plain": {"seconds": time.perf_counter() - t, "iters": ref["iters"], "evals": ref["evals"],
                            "phi": ref["phi"]}}
     target = ref["phi"] - 1e-8 * abs(ref["phi"])
-    for name, prec in (("fp32_then_fp64", pd.PD_FP32), ("bf16x3_then_fp64", pd.PD_BF16X3)):
+    for name, prec, kw in (("fp32_then_fp64", pd.PD_FP32, {}), ("bf16x3_then_fp64", pd.PD_BF16X3, {}),
+                           ("anneal_bf16x3_then_fp64", pd.PD_BF16X3, ANNEAL)):
         t = time.perf_counter()
         _, rep = pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=3000, prec=prec, refine_iter=1000, target_phi=target,
-                           switch_rtol=1e-7)
+                           switch_rtol=1e-7, **kw)
         rows[name] = {"seconds": time.perf_counter() - t, "iters": rep["iters"], "iters_phase1": rep["iters_phase1"],
-                      "evals": rep["evals"], "phi": rep["phi"], "reached": rep["phi"] >= target}
-    ok = rows["fp32_then_fp64"]["reached"] and rows["bf16x3_then_fp64"]["reached"]
-    return {"phi_ref": ref["phi"], "target": target, "runs": rows,
-            "multiple_vs_fp32": rows["fp32_then_fp64"]["seconds"] / rows["bf16x3_then_fp64"]["seconds"] if ok else None}
+                      "evals": rep["evals"], "phi": rep["phi"], "reached": rep["phi"] >= target,
+                      "stages": rep["stages"]}
+    best = min(("bf16x3_then_fp64", "anneal_bf16x3_then_fp64"),
+               key=lambda k: rows[k]["seconds"] if rows[k]["reached"] else float("inf"))
+    ok = rows["fp32_then_fp64"]["reached"] and rows[best]["reached"]
+    return {"phi_ref": ref["phi"], "target": target, "runs": rows, "schedule": best,
+            "anneal": "eps0 = 10 eps, factor 0.25, 100 iterations per stage, then the normal schedule at eps",
+            "multiple_vs_fp32": rows["fp32_then_fp64"]["seconds"] / rows[best]["seconds"] if ok else None}
+
+
+# eps-annealing of the fit schedules (stages 1e-2, 2.5e-3, then eps = 1e-3)
+ANNEAL = dict(anneal_eps0=1e-2, anneal_factor=0.25, anneal_iter=100)
+
+
+def warm_up_fits(pd, grid, lab, N):
+    """One short fit per precision before any fit is timed, so that the
+    kernels' first-use cost (module loading) is not counted in a fit."""
+    for prec in (pd.PD_FP64, pd.PD_FP32, pd.PD_BF16X3):
+        pd.pd_fit(grid, lab, N, DEG, EPS, max_iter=2, prec=prec)
 
 
 def run_ours(args):
@@ -648,8 +665,8 @@ def run_fit(args):
     """Time to reach the FP64 plain fit's objective (<= 1e-8 relative).
 
     Config 2 (1024^2, N = 485, degree 4): the plain FP32 form against the
-    tensor-core forms (BF16X3 first phase, with and without the learned warm
-    start), each followed by FP64 refinement.  Config 5 (512^2, N = 300,
+    tensor-core forms (BF16X3 first phase, plain, eps-annealed, and from the
+    learned warm start), each followed by FP64 refinement.  Config 5 (512^2, N = 300,
     degree 4, a few seeded maps): the same per map, and the batched,
     warm-started BF16X3 + FP64 form fitting all maps at once against the
     plain FP32 form fitting them one by one.  A first phase may run up to
@@ -662,11 +679,11 @@ def run_fit(args):
     from paper_2605_20816_gb300 import pd, warmstart
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
 
-    def fit(grid, lab, N, prec, target, theta0=None):
+    def fit(grid, lab, N, prec, target, theta0=None, anneal=False):
         init = pd.PD_INIT_ZERO if theta0 is None else pd.PD_INIT_GIVEN
         t = time.perf_counter()
         _, rep = pd.pd_fit(grid, lab, N, DEG, EPS, theta=theta0, init=init, max_iter=3000, prec=prec,
-                           refine_iter=1000, target_phi=target, switch_rtol=1e-7)
+                           refine_iter=1000, target_phi=target, switch_rtol=1e-7, **(ANNEAL if anneal else {}))
         return {"seconds": time.perf_counter() - t, "iters": rep["iters"], "iters_phase1": rep["iters_phase1"],
                 "evals": rep["evals"], "phi": rep["phi"], "reached": rep["phi"] >= target}
 
@@ -694,15 +711,17 @@ def run_fit(args):
     # config 2
     grid, lab_np, N, _ = make_workload_gpu(pd, torch)
     lab = torch.from_numpy(lab_np).cuda()
+    warm_up_fits(pd, grid, lab, N)
     ref, t_ref = reference(grid, lab, N)
     target = ref["phi"] - 1e-8 * abs(ref["phi"])
     rows = {"fp64_plain": {"seconds": t_ref, "iters": ref["iters"], "evals": ref["evals"], "phi": ref["phi"]},
             "fp32_then_fp64": fit(grid, lab, N, pd.PD_FP32, target),
-            "bf16x3_then_fp64": fit(grid, lab, N, pd.PD_BF16X3, target)}
+            "bf16x3_then_fp64": fit(grid, lab, N, pd.PD_BF16X3, target),
+            "anneal_bf16x3_then_fp64": fit(grid, lab, N, pd.PD_BF16X3, target, anneal=True)}
     th0, t_pred = warm(grid, lab, N)
     rows["warm_bf16x3_then_fp64"] = fit(grid, lab, N, pd.PD_BF16X3, target, th0)
     rows["warm_bf16x3_then_fp64"]["seconds"] += t_pred
-    best = min(("bf16x3_then_fp64", "warm_bf16x3_then_fp64"),
+    best = min(("bf16x3_then_fp64", "anneal_bf16x3_then_fp64", "warm_bf16x3_then_fp64"),
                key=lambda k: rows[k]["seconds"] if rows[k]["reached"] else float("inf"))
 
     # config 5: per map, then batched
@@ -713,7 +732,8 @@ def run_fit(args):
         tg = r5["phi"] - 1e-8 * abs(r5["phi"])
         row = {"grains": n5, "fp64_plain_seconds": t_r5, "phi_ref": r5["phi"],
                "fp32_then_fp64": fit(g5, l5, n5, pd.PD_FP32, tg),
-               "bf16x3_then_fp64": fit(g5, l5, n5, pd.PD_BF16X3, tg)}
+               "bf16x3_then_fp64": fit(g5, l5, n5, pd.PD_BF16X3, tg),
+               "anneal_bf16x3_then_fp64": fit(g5, l5, n5, pd.PD_BF16X3, tg, anneal=True)}
         w0, t_w = warm(g5, l5, n5)
         row["warm_bf16x3_then_fp64"] = fit(g5, l5, n5, pd.PD_BF16X3, tg, w0)
         row["warm_bf16x3_then_fp64"]["seconds"] += t_w
@@ -722,14 +742,15 @@ def run_fit(args):
         targets5.append(tg)
     plain_total = sum(r["fp32_then_fp64"]["seconds"] for r in per_map)
     batched = {"plain_fp32_then_fp64_seconds": plain_total}
-    for name, use_warm in (("cold", False), ("warm", True)):
+    for name, use_warm, anneal in (("cold", False, False), ("warm", True, False), ("anneal", False, True)):
         t = time.perf_counter()
         if use_warm:
             thetas = [warm(g5, l5, n5)[0] for g5, l5, n5 in maps5]
         else:
             thetas = [torch.zeros((n5, pd.pd_K(2, DEG)), dtype=torch.float64, device="cuda") for _, _, n5 in maps5]
         reps = pd.pd_fit_batched(maps5, thetas, DEG, EPS, init=pd.PD_INIT_GIVEN, max_iter=3000, prec=pd.PD_BF16X3,
-                                 refine_iter=1000, switch_rtol=1e-7, targets=targets5)
+                                 refine_iter=1000, switch_rtol=1e-7, targets=targets5,
+                                 **(ANNEAL if anneal else {}))
         t_b = time.perf_counter() - t
         batched[name] = {"seconds": t_b, "reached": all(r["phi"] >= tg for r, tg in zip(reps, targets5)),
                          "iters": [r["iters"] for r in reps], "multiple_vs_plain_fp32": plain_total / t_b}

@@ -390,7 +390,9 @@ void pd_batch_destroy(pd_batch* batch);
 
 /* Synchronous: the ascent scheme of pd_fit (L-BFGS only; a first phase in
  * any precision with optional FP64 refinement; init PD_INIT_ZERO or
- * PD_INIT_GIVEN, e.g. a learned warm start) for every map at once.  Each map runs its own optimiser
+ * PD_INIT_GIVEN, e.g. a learned warm start; eps-annealing as in pd_fit, but
+ * no Err-aligned stopping: err_stop != 0 is PD_ENOTSUP) for every map at
+ * once.  Each map runs its own optimiser
  * on a host thread; their objective/gradient requests are served together,
  * one graph replay per round for all maps that are waiting.  theta_io[m]:
  * device double[N_m][K], in (PD_INIT_GIVEN) and out (gauge-fixed).

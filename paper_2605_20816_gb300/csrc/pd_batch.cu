@@ -777,10 +777,10 @@ class Coordinator {
       ok_ = false;
     }
     want_.assign(n_, -1);
+    want_eps_.assign(n_, 0.0);
   }
   ~Coordinator() {
-    for (pd_batch* b : plans_)
-      if (b) pd_batch_destroy(b);
+    for (auto& kv : plans_) pd_batch_destroy(kv.second);
     if (h_theta_) cudaFreeHost(h_theta_);
     if (h_grad_) cudaFreeHost(h_grad_);
     if (h_obj_) cudaFreeHost(h_obj_);
@@ -789,10 +789,11 @@ class Coordinator {
   int64_t rounds = 0;
 
   // called from map m's thread; theta/grad are full [N][K] blocks
-  int eval(int m, int prec, const double* theta, double* phi, double* grad) {
+  int eval(int m, int prec, double eps, const double* theta, double* phi, double* grad) {
     std::unique_lock<std::mutex> lk(mu_);
     memcpy(&h_theta_[off_[m]], theta, sizeof(double) * maps_[m].N * K_);
     want_[m] = prec;
+    want_eps_[m] = eps;
     ++waiting_;
     const int64_t my_round = round_;
     if (waiting_ == running_) {
@@ -812,14 +813,15 @@ class Coordinator {
   }
 
  private:
-  // the batch plan of a precision, built on first use
-  int plan(int prec, pd_batch** out) {
-    if (!plans_[prec]) {
-      pd_eval_opts eo{d_, eps_, prec};
-      const int rc = pd_batch_create(n_, maps_.data(), &eo, n_ >= kTuneMaps ? 1 : 0, &plans_[prec]);
+  // the batch plan of a precision and eps, built on first use
+  int plan(int prec, double eps, pd_batch** out) {
+    pd_batch*& b = plans_[std::make_pair(prec, eps)];
+    if (!b) {
+      pd_eval_opts eo{d_, eps, prec};
+      const int rc = pd_batch_create(n_, maps_.data(), &eo, n_ >= kTuneMaps ? 1 : 0, &b);
       if (rc) return rc;
     }
-    *out = plans_[prec];
+    *out = b;
     return PD_OK;
   }
 
@@ -828,16 +830,17 @@ class Coordinator {
     int rc = PD_OK;
     if (cudaMemcpyAsync(d_theta_, h_theta_, sizeof(double) * off_[n_], cudaMemcpyHostToDevice, st_) != cudaSuccess)
       rc = PD_ECUDA;
-    // one replay per precision that some waiting map asked for
-    for (int prec = PD_FP64; rc == PD_OK && prec <= PD_BF16X3; ++prec) {
-      bool any = false;
-      for (int m = 0; m < n_; ++m) {
-        act[m] = want_[m] == prec;
-        any = any || act[m];
-      }
-      if (!any) continue;
+    // one replay per (precision, eps) that some waiting map asked for (maps
+    // in different annealing stages ask for different eps)
+    std::vector<std::pair<int, double>> kinds;
+    for (int m = 0; m < n_; ++m)
+      if (want_[m] >= 0 && std::find(kinds.begin(), kinds.end(), std::make_pair(want_[m], want_eps_[m])) == kinds.end())
+        kinds.push_back(std::make_pair(want_[m], want_eps_[m]));
+    for (const auto& kd : kinds) {
+      if (rc != PD_OK) break;
+      for (int m = 0; m < n_; ++m) act[m] = want_[m] == kd.first && want_eps_[m] == kd.second;
       pd_batch* b = nullptr;
-      rc = plan(prec, &b);
+      rc = plan(kd.first, kd.second, &b);
       if (rc == PD_OK) rc = pd_batch_set_active(b, act.data(), st_);
       if (rc == PD_OK) rc = pd_batch_eval(b, st_);
     }
@@ -857,7 +860,8 @@ class Coordinator {
   int n_, K_, d_;
   double eps_;
   std::vector<pd_map> maps_;
-  pd_batch* plans_[PD_BF16X3 + 1] = {};
+  std::map<std::pair<int, double>, pd_batch*> plans_;
+  std::vector<double> want_eps_;
   double *d_theta_, *d_obj_, *d_grad_;
   cudaStream_t st_;
   std::vector<size_t> off_;
@@ -874,13 +878,15 @@ class Coordinator {
 // Evaluator of one map that goes through the coordinator.
 class BatchedMap : public Evaluator {
  public:
-  BatchedMap(Coordinator* co, int m, int N, int K) : co_(co), m_(m), N_(N), K_(K), th_((size_t)N * K), gr_((size_t)N * K) {}
+  BatchedMap(Coordinator* co, int m, int N, int K, double eps)
+      : co_(co), m_(m), N_(N), K_(K), eps_(eps), th_((size_t)N * K), gr_((size_t)N * K) {}
   int n_free() const override { return (N_ - 1) * K_; }
+  void set_eps(double e) { eps_ = e; }
   int eval(const Vec& x, int prec, double* f, Vec* gf) override {
     for (int q = 0; q < n_free(); ++q) th_[q] = x[q];
     for (int k = 0; k < K_; ++k) th_[(size_t)(N_ - 1) * K_ + k] = 0.0;
     double phi = 0.0;
-    const int rc = co_->eval(m_, prec, th_.data(), &phi, gr_.data());
+    const int rc = co_->eval(m_, prec, eps_, th_.data(), &phi, gr_.data());
     if (rc) return rc;
     ++evals;
     *f = -phi;
@@ -895,6 +901,7 @@ class BatchedMap : public Evaluator {
  private:
   Coordinator* co_;
   int m_, N_, K_;
+  double eps_;
   std::vector<double> th_, gr_;
 };
 
@@ -909,7 +916,11 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
   if (opts->method != PD_METHOD_LBFGS || opts->lbfgs_m < 1) return PD_ENOTSUP;
   if (opts->prec < PD_FP64 || opts->prec > PD_BF16X3) return PD_EINVAL;
   if (opts->init != PD_INIT_ZERO && opts->init != PD_INIT_GIVEN) return PD_ENOTSUP;
-  if (opts->anneal_eps0 > opts->eps) return PD_ENOTSUP;  // annealing: pd_fit only
+  const bool anneal = opts->anneal_eps0 > opts->eps;
+  if (anneal && (!isfinite(opts->anneal_eps0) || !(opts->anneal_factor > 0.0 && opts->anneal_factor < 1.0) ||
+                 opts->anneal_iter < 1))
+    return PD_EINVAL;
+  if (opts->err_stop) return PD_ENOTSUP;  // Err-aligned stopping: pd_fit only
   cudaStream_t st = (cudaStream_t)stream;
   const int K = basis_K(2, opts->d);
   for (int m = 0; m < n_maps; ++m) {
@@ -964,11 +975,39 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
     for (int m = 0; m < n_maps; ++m) {
       threads.emplace_back([&, m]() {
         const int N = maps[m].N;
-        BatchedMap ev(&co, m, N, K);
+        BatchedMap ev(&co, m, N, K, opts->eps);
         FitState fs;
         pd_fit_opts om = *opts;
         if (!isnan(maps[m].target_phi)) om.target_phi = maps[m].target_phi;
-        int r = fit_run(ev, th0[m], N, K, om, &fs);
+        // the stages of eps-annealing, as in pd_fit: each warm-started from
+        // the last, the last at eps with the full schedule
+        std::vector<double> ths = th0[m];
+        double eps_k = anneal ? opts->anneal_eps0 : opts->eps;
+        int r = PD_OK, stages = 0, iters = 0, iters1 = 0;
+        for (;;) {
+          const bool last = eps_k <= opts->eps;
+          if (last) eps_k = opts->eps;
+          ev.set_eps(eps_k);
+          pd_fit_opts so = om;
+          so.eps = eps_k;
+          if (!last) {
+            so.max_iter = opts->anneal_iter;
+            so.refine_iter = 0;
+            so.target_phi = -INFINITY;
+            so.switch_rtol = 0.0;
+          }
+          r = fit_run(ev, ths, N, K, so, &fs);
+          if (r) break;
+          ++stages;
+          iters += fs.iters;
+          iters1 += last ? fs.iters_phase1 : fs.iters;
+          for (size_t q = 0; q < fs.cur.x.size(); ++q) ths[q] = fs.cur.x[q];
+          for (int k = 0; k < K; ++k) ths[(size_t)(N - 1) * K + k] = 0.0;
+          if (last) break;
+          eps_k *= opts->anneal_factor;
+        }
+        fs.iters = iters;
+        fs.iters_phase1 = iters1;
         // final double-precision evaluation for the report
         if (r == PD_OK && fs.final_prec != PD_FP64) {
           std::vector<double> gf;
@@ -984,6 +1023,8 @@ extern "C" int pd_fit_batched(int n_maps, const pd_map* maps, double* const* the
         rep.iters_phase1 = fs.iters_phase1;
         rep.evals = ev.evals;
         rep.status = fs.status;
+        rep.eps_final = eps_k;
+        rep.stages = stages;
         rcs[m] = r;
         // gauge-fixed result
         std::vector<double> th((size_t)N * K, 0.0);

@@ -417,7 +417,8 @@ class Batch:
 
 def pd_fit_batched(maps, thetas, d: int, eps: float, init: int = PD_INIT_ZERO, max_iter: int = 1000,
                    lbfgs_m: int = 10, prec: int = PD_FP64, refine_iter: int = 0, gtol: float = 0.0,
-                   target_phi: float = -math.inf, switch_rtol: float = 0.0, targets=None):
+                   target_phi: float = -math.inf, switch_rtol: float = 0.0, targets=None,
+                   anneal_eps0: float = 0.0, anneal_factor: float = 0.5, anneal_iter: int = 100):
     """maps = [(grid, labels, N)], thetas = [CUDA float64 [N, K]] (in/out),
     targets = per-map objective targets (None: target_phi for all).
     Returns the list of per-map report dicts."""
@@ -426,7 +427,7 @@ def pd_fit_batched(maps, thetas, d: int, eps: float, init: int = PD_INIT_ZERO, m
     arr = (pd_map * n)(*[_map(g, lab, N, target_phi=t) for (g, lab, N), t in zip(maps, tg)])
     ths = (C.c_void_p * n)(*[t.data_ptr() for t in thetas])
     opts = pd_fit_opts(d, float(eps), init, PD_METHOD_LBFGS, max_iter, lbfgs_m, 50, prec, refine_iter, gtol,
-                       target_phi, switch_rtol)
+                       target_phi, switch_rtol, float(anneal_eps0), float(anneal_factor), int(anneal_iter), 0)
     reps = (pd_fit_report * n)()
     _check(lib().pd_fit_batched(n, arr, ths, C.byref(opts), reps, _stream()), "pd_fit_batched")
     return [r.as_dict() for r in reps]

@@ -161,3 +161,10 @@ def test_fit_batched_reaches_single_map_optima():
                               refine_iter=600, switch_rtol=1e-7, gtol=1e-12)
     for r, s in zip(reps3, single):
         assert abs(r["phi"] - s["phi"]) <= 1e-8 * abs(s["phi"]), (r, s)
+    # with eps-annealing (0.2, 0.1, then eps = 0.05): the same optima
+    thetas4 = [torch.zeros_like(t) for t in thetas]
+    reps4 = pd.pd_fit_batched(maps, thetas4, d, eps, max_iter=300, prec=pd.PD_BF16X3, refine_iter=600,
+                              switch_rtol=1e-7, gtol=1e-12, anneal_eps0=0.2, anneal_factor=0.5, anneal_iter=30)
+    for r, s in zip(reps4, single):
+        assert r["stages"] == 3 and r["eps_final"] == eps, r
+        assert abs(r["phi"] - s["phi"]) <= 1e-8 * abs(s["phi"]), (r, s)
