@@ -51,7 +51,7 @@ WORKLOAD = ("2D 1024x1024, N=500 degree-4 polynomial diagram, 2% boundary noise,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"],
@@ -144,7 +144,7 @@ class ClockSampler:
                 continue
         if not rows:
             return None
-        sel = [r for r in rows if self.t0 and self.t1 and self.t0 - 0.2 <= r[0] <= self.t1 + 0.2] or rows
+        sel = [r for r in rows if self.t0 and self.t1 and self.t0 - 0.05 <= r[0] <= self.t1 + 0.05] or rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[q] for r in sel for q in range(4) if r[3][q].lower().startswith("active")})
         return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
