@@ -146,10 +146,19 @@ int pd_objective_grad(const pd_grid* grid, const int32_t* labels, int N,
 
 /* Hessian-vector product from eq. (hess):
  *   (H v)_i = -(1/(eps^2 P)) sum_x p_i(x) (u_i(x) - sum_k p_k(x) u_k(x)) eta(x),
- * u_i(x) = v_i . eta(x).  v, hv_out: device double[N][K].  labels are not
- * used by the Hessian but keep the call shape of pd_objective_grad (may be
- * NULL).  prec: any; the tensor-core precisions scale v by a power of two
- * internally (their fp16 operands need |v| <= 1) and undo it exactly. */
+ * u_i(x) = v_i . eta(x).  v, hv_out: device double[N][K].  labels do not
+ * enter the Hessian (the call keeps the shape of pd_objective_grad); they
+ * may be NULL (the tensor-core precisions take them as a hint for the
+ * grain order of their pair skipping).  u_i - ubar of the grain that holds
+ * nearly all of a pixel's probability is a small difference of two large
+ * terms: PD_FP32 forms it from sums that leave each pixel's arg-max grain
+ * out, so that it keeps its relative accuracy where p is close to 1; the
+ * tensor-core precisions form the plain difference, whose error is about
+ * 2^-24 |u| at such pixels (negligible beside the grain boundaries'
+ * terms, except on maps where nearly every pixel has p within 1e-4 of 1).
+ * prec: any;
+ * the tensor-core precisions scale v by a power of two internally (their
+ * fp16 operands need |v| <= 1) and undo it exactly. */
 int pd_hvp(const pd_grid* grid, const int32_t* labels, int N,
            const double* theta, const double* v, const pd_eval_opts* opts,
            double* hv_out, void* stream);

@@ -48,6 +48,7 @@ struct BatchMapDev {
   float2* ec;        // FP32: centre features [tiles][K]
   float2* ref;       // FP32: reference logits [tiles]
   void* lse;
+  float* q;          // FP32: 1 - p_G per pixel
   double* objp;
   double* part;
   double* obj_out;
@@ -132,7 +133,8 @@ k_batch_pass1(const BatchMapDev* __restrict__ maps, const int2* __restrict__ ite
     const BatchMapDev& mp = maps[w.x];
     if constexpr (std::is_same<T, float>::value)
       pass1_tiles_block<2, D, false>(mp.g, mp.tm, mp.labels, mp.N, static_cast<const float*>(mp.thS), mp.thL,
-                                     nullptr, mp.ec, mp.ref, static_cast<float*>(mp.lse), nullptr, mp.objp + w.y, w.y);
+                                     nullptr, mp.ec, mp.ref, static_cast<float*>(mp.lse), mp.q, nullptr, nullptr,
+                                     nullptr, mp.objp + w.y, w.y);
     else
       pass1_block<T, 2, D, 2, false>(mp.g, mp.labels, mp.N, static_cast<const T*>(mp.thS), nullptr,
                                      static_cast<T*>(mp.lse), nullptr, mp.objp + w.y, w.y);
@@ -153,8 +155,8 @@ k_batch_pass2(const BatchMapDev* __restrict__ maps, const int2* __restrict__ ite
     const int gtiles = (mp.N + kGradThreads - 1) / kGradThreads;
     if constexpr (std::is_same<T, float>::value)
       pass2_tiles_block<2, D, false>(mp.g, mp.tm, mp.labels, mp.N, static_cast<const float*>(mp.thS), mp.thL,
-                                     nullptr, mp.ec, mp.ref, static_cast<const float*>(mp.lse), nullptr, mp.ppc,
-                                     mp.part, w.y / gtiles, w.y % gtiles);
+                                     nullptr, mp.ec, mp.ref, static_cast<const float*>(mp.lse), mp.q, nullptr,
+                                     nullptr, nullptr, mp.ppc, mp.part, w.y / gtiles, w.y % gtiles);
     else
       pass2_block<T, 2, D, false>(mp.g, mp.labels, mp.N, static_cast<const T*>(mp.thS), nullptr,
                                   static_cast<const T*>(mp.lse), nullptr, mp.ppc, mp.part, w.y / gtiles,
@@ -341,7 +343,7 @@ int build_plan(pd_batch* b, const Tune& tu) {
     return o;
   };
   std::vector<size_t> o_th(b->n_maps), o_lse(b->n_maps), o_objp(b->n_maps), o_part(b->n_maps);
-  std::vector<size_t> o_thl(b->n_maps, 0), o_ec(b->n_maps, 0), o_ref(b->n_maps, 0);
+  std::vector<size_t> o_thl(b->n_maps, 0), o_ec(b->n_maps, 0), o_ref(b->n_maps, 0), o_q(b->n_maps, 0);
   b->hmaps.assign(b->n_maps, BatchMapDev{});
   std::vector<int2> items1, items2;
   for (int m = 0; m < b->n_maps; ++m) {
@@ -364,6 +366,7 @@ int build_plan(pd_batch* b, const Tune& tu) {
       o_thl[m] = take(4 * (size_t)mp.N * b->KP);
       o_ec[m] = take(sizeof(float2) * (size_t)h.tm.n_tiles * b->K);
       o_ref[m] = take(sizeof(float2) * (size_t)h.tm.n_tiles);
+      o_q[m] = take(4 * (size_t)P);
     } else {
       h.blocks1 = (int)((P + kLseThreads * 2 - 1) / (kLseThreads * 2));
       const int64_t tiles = (P + kPixTile - 1) / kPixTile;
@@ -398,6 +401,7 @@ int build_plan(pd_batch* b, const Tune& tu) {
       h.thL = reinterpret_cast<float*>(base + o_thl[m]);
       h.ec = reinterpret_cast<float2*>(base + o_ec[m]);
       h.ref = reinterpret_cast<float2*>(base + o_ref[m]);
+      h.q = reinterpret_cast<float*>(base + o_q[m]);
     }
     h.objp = reinterpret_cast<double*>(base + o_objp[m]);
     h.part = b->maps[m].grad_out ? reinterpret_cast<double*>(base + o_part[m]) : nullptr;

@@ -140,6 +140,35 @@ struct Arith<float> {
   static double theta_scale(double eps) { return -1.4426950408889634073599246810018921 / eps; }
 };
 
+// The log-sum-exp of a pixel whose label term is kept apart (log2 units):
+// m the running max (m >= lG), s the sum of 2^(l_k - m) over the grains
+// other than the label G, lG the label's logit.  With rho = s 2^(m - lG),
+// p_G = 1 / (1 + rho), so
+//   log2 S = lG + log2(1 + rho),  1 - p_G = rho / (1 + rho),
+//   log p_G = -log(1 + rho),
+// none of which cancels when p_G is close to 1 (rho small).  Below
+// p_G = 2^-100 nothing cancels and S is taken directly.  A NaN lG (a label
+// outside 0..N-1) gives log2 S from s and a NaN log p_G.
+struct LabelLse {
+  float lse, q;
+  double logp;
+};
+__device__ __forceinline__ LabelLse label_lse(float m, float s, float lG) {
+  LabelLse r;
+  if (lG - m >= -100.f) {
+    const float rho = __fdividef(s, Arith<float>::ex(lG - m));
+    const float l1 = log1pf(rho);
+    r.lse = fmaf(l1, 1.44269504088896341f, lG);
+    r.q = __fdividef(rho, 1.f + rho);
+    r.logp = -(double)l1;
+  } else {
+    r.lse = m + log2f(s);
+    r.q = 1.f;
+    r.logp = (double)(lG - r.lse) * Arith<float>::to_nat;
+  }
+  return r;
+}
+
 // Row stride of the scaled parameter copy: K padded to a 16-byte multiple.
 template <typename T>
 __host__ __device__ constexpr int padded_K(int K) {

@@ -74,7 +74,7 @@ int noalloc_eval_dd(const EvalCall& c, cudaStream_t st, char* base) {
     const size_t fixed = 2 * FixedArena::round_up(sizeof(float) * (size_t)N * KP) +
                          FixedArena::round_up(sizeof(float2) * (size_t)n_tiles * K) +
                          FixedArena::round_up(sizeof(float2) * (size_t)n_tiles) +
-                         FixedArena::round_up(sizeof(float) * (size_t)P) +
+                         (want_grad ? 2 : 1) * FixedArena::round_up(sizeof(float) * (size_t)P) +
                          FixedArena::round_up(sizeof(double) * (size_t)blocks1) + 256;
     if (fixed > (size_t)PD_NOALLOC_SCRATCH_BYTES) return PD_ESCRATCH;
     int64_t tpc = tiles_per_chunk(n_tiles, gtiles, device_sm_count());
@@ -92,10 +92,12 @@ int noalloc_eval_dd(const EvalCall& c, cudaStream_t st, char* base) {
     float2* ec = fx.take<float2>((size_t)n_tiles * K);
     float2* ref = fx.take<float2>((size_t)n_tiles);
     float* lse = fx.take<float>((size_t)P);
+    float* qv = want_grad ? fx.take<float>((size_t)P) : nullptr;
     double* objp = fx.take<double>((size_t)blocks1);
     double* part = want_grad ? fx.take<double>((size_t)nch * N * K) : nullptr;
-    if (!thH || !thL || !ec || !ref || !lse || !objp || (want_grad && !part)) return PD_ESCRATCH;
-    return launch_simt_tiles<DIM, D>(c, tm, thH, thL, nullptr, ec, ref, lse, nullptr, objp, part, tpc, st);
+    if (!thH || !thL || !ec || !ref || !lse || !objp || (want_grad && (!part || !qv))) return PD_ESCRATCH;
+    return launch_simt_tiles<DIM, D>(c, tm, thH, thL, nullptr, ec, ref, lse, qv, nullptr, nullptr, objp, part, tpc,
+                                     st);
   } else {
     constexpr int ppt = 2;
     const int blocks1 = (int)((P + kLseThreads * ppt - 1) / (kLseThreads * ppt));

@@ -380,8 +380,9 @@ __device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& 
                                                   int N, const float* __restrict__ thH, const float* __restrict__ thL,
                                                   const float* __restrict__ vS, const float2* __restrict__ ecg,
                                                   const float2* __restrict__ refg, float* __restrict__ lse_out,
-                                                  float* __restrict__ ubar_out, double* __restrict__ obj_slot,
-                                                  int64_t blk) {
+                                                  float* __restrict__ q_out, float* __restrict__ ubar_out,
+                                                  float* __restrict__ dm_out, int* __restrict__ mx_out,
+                                                  double* __restrict__ obj_slot, int64_t blk) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KP = padded_K<float>(K);
   constexpr int GT = HVP ? 64 : 128;  // grains per shared chunk
@@ -405,7 +406,15 @@ __device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& 
   }
   float de[2][K], eta[HVP ? 2 : 1][K];
   int64_t jq[2];
-  float m[2], s[2], tu[2];
+  // m: running max; s: the sum of 2^(l - m) over the grains other than the
+  // pixel's label G (gradient) -- the label's term is added at the end, so
+  // that 1 - p_G = s / (s + 2^(lG - m)) and log p_G carry no cancellation
+  // when p_G is close to 1 (a well-fitted pixel).  For the HVP the grain
+  // kept apart is the arg-max M (index mx, u_M = uM): s and tu sum 2^(l - m)
+  // and 2^(l - m) u over the others, so that u_M - ubar = (uM s - tu) /
+  // (1 + s) keeps its relative accuracy when p_M is close to 1.
+  float m[2], s[2], tu[2], uM[2];
+  int Gq[2], mx[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int64_t t = t0 + hq + 2 * q;
@@ -421,6 +430,9 @@ __device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& 
     m[q] = -INFINITY;
     s[q] = 0.f;
     tu[q] = 0.f;
+    uM[q] = 0.f;
+    mx[q] = -1;
+    Gq[q] = !HVP && jq[q] >= 0 ? labels[jq[q]] : -1;
   }
 
   for (int g0 = 0; g0 < N; g0 += GT) {
@@ -466,17 +478,58 @@ __device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& 
         float cm = l[q][0];
 #pragma unroll
         for (int c = 1; c < kChunk; ++c) cm = fmaxf(cm, l[q][c]);
+        if (HVP) {
+          if (cm > m[q]) {
+            // the max moves into this chunk: the old max's term joins the
+            // sums, the first grain attaining cm is kept apart
+            const float rr = Arith<float>::ex(m[q] - cm);
+            float add = rr, addu = uM[q] * rr;
+            bool found = false;
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+              const float e = Arith<float>::ex(l[q][c] - cm);
+              const bool hit = !found && l[q][c] == cm;
+              found = found || hit;
+              if (hit) {
+                uM[q] = u[q][c];
+                mx[q] = g0 + i + c;
+              } else {
+                add += e;
+                addu = fmaf(e, u[q][c], addu);
+              }
+            }
+            s[q] = fmaf(s[q], rr, add);
+            tu[q] = fmaf(tu[q], rr, addu);
+            m[q] = cm;
+          } else {
+            float add = 0.f, addu = 0.f;
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+              const float e = Arith<float>::ex(l[q][c] - m[q]);
+              add += e;
+              addu = fmaf(e, u[q][c], addu);
+            }
+            s[q] += add;
+            tu[q] += addu;
+          }
+          continue;
+        }
         const float mn = fmaxf(m[q], cm);
         const float rr = Arith<float>::ex(m[q] - mn);
-        float add = 0.f, addu = 0.f;
+        float add = 0.f;
+        const int lc = Gq[q] - (g0 + i);
+        if ((unsigned)lc < (unsigned)kChunk) {
+          // the chunk of the label: its term kept apart
 #pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-          const float e = Arith<float>::ex(l[q][c] - mn);
-          add += e;
-          if (HVP) addu = fmaf(e, u[q][c], addu);
+          for (int c = 0; c < kChunk; ++c) {
+            const float e = Arith<float>::ex(l[q][c] - mn);
+            add += c == lc ? 0.f : e;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < kChunk; ++c) add += Arith<float>::ex(l[q][c] - mn);
         }
         s[q] = fmaf(s[q], rr, add);
-        if (HVP) tu[q] = fmaf(tu[q], rr, addu);
         m[q] = mn;
       }
     }
@@ -484,11 +537,26 @@ __device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& 
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const float l = soff[hq + 2 * q][i] + dot_k<K>(sth + i * KP, de[q]);
+        if (HVP) {
+          const float uu = dot_k<K>(sv + i * KP, eta[q]);
+          if (l > m[q]) {  // a new max: the old one's term joins the sums
+            const float rr = Arith<float>::ex(m[q] - l);
+            s[q] = fmaf(s[q], rr, rr);
+            tu[q] = fmaf(tu[q], rr, uM[q] * rr);
+            uM[q] = uu;
+            mx[q] = g0 + i;
+            m[q] = l;
+          } else {
+            const float e = Arith<float>::ex(l - m[q]);
+            s[q] += e;
+            tu[q] = fmaf(e, uu, tu[q]);
+          }
+          continue;
+        }
         const float mn = fmaxf(m[q], l);
         const float rr = Arith<float>::ex(m[q] - mn);
-        const float e = Arith<float>::ex(l - mn);
+        const float e = g0 + i == Gq[q] ? 0.f : Arith<float>::ex(l - mn);
         s[q] = fmaf(s[q], rr, e);
-        if (HVP) tu[q] = fmaf(tu[q], rr, e * dot_k<K>(sv + i * KP, eta[q]));
         m[q] = mn;
       }
     }
@@ -499,25 +567,32 @@ __device__ __forceinline__ void pass1_tiles_block(const Geom& g, const TileMap& 
   for (int q = 0; q < 2; ++q) {
     const int64_t j = jq[q];
     if (j < 0) continue;
-    const float lse = m[q] + lse_log2(s[q]);
-    if (lse_out) lse_out[j] = lse;
-    if (HVP) ubar_out[j] = tu[q] / s[q];
-    if (!HVP && obj_slot) {
-      const int G = labels[j];
-      if ((unsigned)G < (unsigned)N) {
-        float h[K], l[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          h[k] = thH[(int64_t)G * KP + k];
-          l[k] = thL[(int64_t)G * KP + k];
-        }
-        const int lt = hq + 2 * q;
-        const float lG = centre_offset<K>(h, l, sec[lt], sref[lt]) + dot_k<K>(h, de[q]);
-        racc += (double)(lG - lse) * Arith<float>::to_nat;
-      } else {
-        racc = NAN;  // a label outside 0..N-1 poisons the objective
-      }
+    if (HVP) {
+      // S = 1 + s (the max's own term is 1)
+      const float S = 1.f + s[q];
+      if (lse_out) lse_out[j] = m[q] + lse_log2(S);
+      ubar_out[j] = (uM[q] + tu[q]) / S;
+      dm_out[j] = fmaf(uM[q], s[q], -tu[q]) / S;  // u_M - ubar
+      mx_out[j] = mx[q];
+      continue;
     }
+    const int G = Gq[q];
+    const bool lab_ok = (unsigned)G < (unsigned)N;
+    float lG = NAN;  // the label logit, formed as in the loop
+    if (lab_ok) {
+      float h[K], l[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        h[k] = thH[(int64_t)G * KP + k];
+        l[k] = thL[(int64_t)G * KP + k];
+      }
+      const int lt = hq + 2 * q;
+      lG = centre_offset<K>(h, l, sec[lt], sref[lt]) + dot_k<K>(h, de[q]);
+    }
+    const LabelLse rl = label_lse(m[q], s[q], lG);
+    if (lse_out) lse_out[j] = rl.lse;
+    if (q_out) q_out[j] = rl.q;
+    if (obj_slot) racc = lab_ok ? racc + rl.logp : NAN;  // a label outside 0..N-1 poisons the objective
   }
   if (!HVP && obj_slot) {
     const double bs = block_sum_fixed(racc, sred);
@@ -529,9 +604,23 @@ template <int DIM, int D, bool HVP>
 __global__ void __launch_bounds__(kLseThreads)
 k_pass1_tiles(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const float* __restrict__ thH,
               const float* __restrict__ thL, const float* __restrict__ vS, const float2* __restrict__ ecg,
-              const float2* __restrict__ refg, float* __restrict__ lse_out, float* __restrict__ ubar_out,
+              const float2* __restrict__ refg, float* __restrict__ lse_out, float* __restrict__ q_out,
+              float* __restrict__ ubar_out, float* __restrict__ dm_out, int* __restrict__ mx_out,
               double* __restrict__ obj_part) {
-  pass1_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse_out, ubar_out,
+  pass1_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse_out, q_out, ubar_out, dm_out, mx_out,
+                                 obj_part ? obj_part + blockIdx.x : nullptr, blockIdx.x);
+}
+
+// The same for the longest feature vectors (K > 28), held to two blocks
+// per SM: left free, the compiler gives them one.
+template <int DIM, int D, bool HVP>
+__global__ void __launch_bounds__(kLseThreads, 2)
+k_pass1_tiles_2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const float* __restrict__ thH,
+                const float* __restrict__ thL, const float* __restrict__ vS, const float2* __restrict__ ecg,
+                const float2* __restrict__ refg, float* __restrict__ lse_out, float* __restrict__ q_out,
+                float* __restrict__ ubar_out, float* __restrict__ dm_out, int* __restrict__ mx_out,
+                double* __restrict__ obj_part) {
+  pass1_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse_out, q_out, ubar_out, dm_out, mx_out,
                                  obj_part ? obj_part + blockIdx.x : nullptr, blockIdx.x);
 }
 
@@ -553,15 +642,18 @@ __device__ __forceinline__ void pass2_tiles_block(const Geom& g, const TileMap& 
                                                   int N, const float* __restrict__ thH, const float* __restrict__ thL,
                                                   const float* __restrict__ vS, const float2* __restrict__ ecg,
                                                   const float2* __restrict__ refg, const float* __restrict__ lse,
-                                                  const float* __restrict__ ubar, int64_t tpc,
-                                                  double* __restrict__ part, int64_t chunk, int gtile) {
+                                                  const float* __restrict__ qin, const float* __restrict__ ubar,
+                                                  const float* __restrict__ dmin, const int* __restrict__ mxin,
+                                                  int64_t tpc, double* __restrict__ part, int64_t chunk, int gtile) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KP = padded_K<float>(K);
   constexpr int RS = p2_stride<KP>();
   __shared__ __align__(16) float sde[kTilePix * RS];
-  __shared__ float slse[kTilePix];
-  __shared__ float subar[HVP ? kTilePix : 1];
-  __shared__ int slab[kTilePix];
+  // per pixel: for the HVP one 16-byte word (log2 S, u_M - ubar, the
+  // arg-max grain M, ubar); for the gradient log2 S, 1 - p_G and the label
+  __shared__ float4 spx[HVP ? kTilePix : 1];
+  __shared__ float slse[HVP ? 1 : kTilePix], sqv[HVP ? 1 : kTilePix];
+  __shared__ int slab[HVP ? 1 : kTilePix];
   __shared__ float2 sec[K];
   __shared__ float2 sref;
   __shared__ double sacc[K * kGradThreads];
@@ -593,9 +685,14 @@ __device__ __forceinline__ void pass2_tiles_block(const Geom& g, const TileMap& 
 #pragma unroll
       for (int k = 0; k < KP; k += 4)
         *reinterpret_cast<float4*>(sde + threadIdx.x * RS + k) = make_float4(dd[k], dd[k + 1], dd[k + 2], dd[k + 3]);
-      slse[threadIdx.x] = j >= 0 ? lse[j] : INFINITY;
-      if (HVP) subar[threadIdx.x] = j >= 0 ? ubar[j] : 0.f;
-      else slab[threadIdx.x] = j >= 0 ? labels[j] : -1;
+      if (HVP)
+        spx[threadIdx.x] = j >= 0 ? make_float4(lse[j], dmin[j], __int_as_float(mxin[j]), ubar[j])
+                                  : make_float4(INFINITY, 0.f, __int_as_float(-1), 0.f);
+      else {
+        slse[threadIdx.x] = j >= 0 ? lse[j] : INFINITY;
+        sqv[threadIdx.x] = j >= 0 ? qin[j] : 0.f;
+        slab[threadIdx.x] = j >= 0 ? labels[j] : -1;
+      }
       if (threadIdx.x < K) sec[threadIdx.x] = ecg[t * K + threadIdx.x];
       if (threadIdx.x == 0) sref = refg[t];
     }
@@ -610,13 +707,18 @@ __device__ __forceinline__ void pass2_tiles_block(const Geom& g, const TileMap& 
     }
     float cs = 0.f;  // sum of c over the tile
     auto coef = [&](int q, float l, const float* de) -> float {
-      const float p = Arith<float>::ex(l - slse[q]);
       float cc;
       if (HVP) {
+        const float4 px = spx[q];
+        const float p = Arith<float>::ex(l - px.x);
+        const bool own = __float_as_int(px.z) == i;
+        // the arg-max grain's u_M - ubar from pass 1 (no cancellation near p_M = 1)
         const float u = uc + dot_k<K>(vv, de);
-        cc = p * (u - subar[q]);
+        cc = p * (own ? px.y : u - px.w);
       } else {
-        cc = (slab[q] == i ? 1.f : 0.f) - p;
+        // the label's c = 1 - p_G from pass 1 (no cancellation near p_G = 1)
+        const float p = Arith<float>::ex(l - slse[q]);
+        cc = slab[q] == i ? sqv[q] : -p;
       }
       return vi ? cc : 0.f;
     };
@@ -671,10 +773,11 @@ template <int DIM, int D, bool HVP>
 __global__ void __launch_bounds__(kGradThreads)
 k_pass2_tiles(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const float* __restrict__ thH,
               const float* __restrict__ thL, const float* __restrict__ vS, const float2* __restrict__ ecg,
-              const float2* __restrict__ refg, const float* __restrict__ lse, const float* __restrict__ ubar,
+              const float2* __restrict__ refg, const float* __restrict__ lse, const float* __restrict__ qin,
+              const float* __restrict__ ubar, const float* __restrict__ dmin, const int* __restrict__ mxin,
               int64_t tpc, double* __restrict__ part) {
-  pass2_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse, ubar, tpc, part, blockIdx.x,
-                                 blockIdx.y);
+  pass2_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse, qin, ubar, dmin, mxin, tpc, part,
+                                 blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -960,13 +1063,15 @@ inline int chunks_for(int64_t P, int grain_tiles, int sms) {
 
 // Launches of one FP32 tile evaluation into caller-provided scratch:
 // parameters thH/thL/vS [N][KP], centre features ec [tiles][K], reference
-// logits ref [tiles], lse and ubar [P], objective partials objp [tiles /
-// kT1Tiles], gradient partials part [chunks][N][K].  Shared by the
-// allocating and the allocation-free entry points.
+// logits ref [tiles], lse [P], qv [P] (1 - p_G of the label, or u_M -
+// ubar of the arg-max grain for the HVP), ubar and mx (the arg-max grain)
+// [P], objective partials objp [tiles / kT1Tiles], gradient partials part
+// [chunks][N][K].  Shared by the allocating and the allocation-free entry
+// points.
 template <int DIM, int D>
 int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* thL, float* vS, float2* ec,
-                      float2* ref, float* lse, float* ubar, double* objp, double* part, int64_t tpc,
-                      cudaStream_t st) {
+                      float2* ref, float* lse, float* qv, float* ubar, int* mx, double* objp, double* part,
+                      int64_t tpc, cudaStream_t st) {
   constexpr int K = basis_K(DIM, D);
   constexpr int KP = padded_K<float>(K);
   const int N = c.N;
@@ -992,18 +1097,22 @@ int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* t
   if (hvp) {
     PD_TIMED(st, "simt_hvp_pass1",
              (k_pass1_tiles<DIM, D, true><<<(unsigned)blocks1, kLseThreads, 0, st>>>(
-                 c.g, tm, c.labels, N, thH, thL, vS, ec, ref, lse, ubar, nullptr)));
+                 c.g, tm, c.labels, N, thH, thL, vS, ec, ref, lse, nullptr, ubar, qv, mx, nullptr)));
     PD_TIMED(st, "simt_hvp_pass2",
              (k_pass2_tiles<DIM, D, true><<<grid2, kGradThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, vS, ec, ref,
-                                                                         lse, ubar, tpc, part)));
+                                                                         lse, nullptr, ubar, qv, mx, tpc, part)));
   } else {
+    auto k1 = k_pass1_tiles<DIM, D, false>;
+    if constexpr (K > 28) k1 = k_pass1_tiles_2<DIM, D, false>;
     PD_TIMED(st, "simt_lse_pass1",
-             (k_pass1_tiles<DIM, D, false><<<(unsigned)blocks1, kLseThreads, 0, st>>>(
-                 c.g, tm, c.labels, N, thH, thL, nullptr, ec, ref, lse, nullptr, objp)));
+             (k1<<<(unsigned)blocks1, kLseThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, nullptr, ec, ref, lse,
+                                                             want_grad ? qv : nullptr, nullptr, nullptr, nullptr,
+                                                             objp)));
     if (want_grad)
       PD_TIMED(st, "simt_grad_pass2",
                (k_pass2_tiles<DIM, D, false><<<grid2, kGradThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, nullptr,
-                                                                            ec, ref, lse, nullptr, tpc, part)));
+                                                                            ec, ref, lse, qv, nullptr, nullptr,
+                                                                            nullptr, tpc, part)));
   }
   if (c.obj && !hvp)
     PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, (int)blocks1, 1.0 / (double)P, c.obj));
@@ -1053,7 +1162,9 @@ int eval_simt_tiles(const EvalCall& c, cudaStream_t st) {
   float2* ec = sc.get<float2>((size_t)n_tiles * K);
   float2* ref = sc.get<float2>((size_t)n_tiles);
   float* lse = (want_grad || hvp || all) ? sc.get<float>((size_t)P) : nullptr;
+  float* qv = (want_grad || hvp || all) ? sc.get<float>((size_t)P) : nullptr;  // 1 - p_G, or u_M - ubar
   float* ubar = hvp ? sc.get<float>((size_t)P) : nullptr;
+  int* mx = hvp ? sc.get<int>((size_t)P) : nullptr;  // the arg-max grain of each pixel (HVP)
   double* objp = (!hvp && (c.obj || all)) ? sc.get<double>((size_t)blocks1) : nullptr;
   double* part = (want_grad || hvp || all) ? sc.get<double>((size_t)nch * N * K) : nullptr;
   if (!sc.ok()) return PD_ENOMEM;
@@ -1062,7 +1173,7 @@ int eval_simt_tiles(const EvalCall& c, cudaStream_t st) {
     return PD_OK;
   }
   if (!c.obj) objp = nullptr;
-  return launch_simt_tiles<DIM, D>(c, tm, thH, thL, vS, ec, ref, lse, ubar, objp, part, tpc, st);
+  return launch_simt_tiles<DIM, D>(c, tm, thH, thL, vS, ec, ref, lse, qv, ubar, mx, objp, part, tpc, st);
 }
 
 template <typename T, int DIM, int D>

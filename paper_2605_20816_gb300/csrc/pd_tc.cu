@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kP1Threads, 1)
 k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, int g0, int Ng, int n_stages,
            const uint8_t* __restrict__ img, const float* __restrict__ th32t, int th_resident,
            const float* __restrict__ offg, const int* __restrict__ rank, float* __restrict__ lse_out,
-           double* __restrict__ obj_part,
+           float* __restrict__ q_out, double* __restrict__ obj_part,
            float2* __restrict__ ms_out, float* __restrict__ lg_out, const unsigned long long* __restrict__ masks,
            uint32_t* __restrict__ need_bits, int64_t n_words, int* __restrict__ status) {
   constexpr int K = basis_K(DIM, D);
@@ -330,8 +330,12 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     // them valid); the running max starts at the label logit (a lower bound
     // of the max, usually the max itself), so most chunks of far-away grains
     // lie more than 127 below it: their exponentials underflow to exactly
-    // zero in ex2.approx.ftz and the whole chunk is skipped
-    auto chunk = [&](const uint32_t(&r)[32], const float* off, int nv, float& m, float& ssum) -> float {
+    // zero in ex2.approx.ftz and the whole chunk is skipped.  The label's
+    // own column (li, when in 0..31) is left out: ssum sums the other
+    // grains only, and the label's term, from the producers' label logit,
+    // joins at the end, so that 1 - p_G and log p_G carry no cancellation
+    // when p_G is close to 1
+    auto chunk = [&](const uint32_t(&r)[32], const float* off, int nv, int li, float& m, float& ssum) -> float {
       if (nv <= 0) return -INFINITY;
       float v[32];
       const float4* off4 = reinterpret_cast<const float4*>(off);  // 16-byte aligned: cbase is a multiple of 32
@@ -355,6 +359,13 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           v[q + 1] = q + 1 < nv ? __uint_as_float(r[q + 1]) + o.y : -INFINITY;
           v[q + 2] = q + 2 < nv ? __uint_as_float(r[q + 2]) + o.z : -INFINITY;
           v[q + 3] = q + 3 < nv ? __uint_as_float(r[q + 3]) + o.w : -INFINITY;
+        }
+      }
+      {
+        const uint32_t lm = (unsigned)li < 32u ? 1u << li : 0u;
+        if (__any_sync(0xffffffffu, lm != 0u)) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = (lm >> q) & 1u ? -INFINITY : v[q];
         }
       }
       const float cm = tree_max32(v);
@@ -397,19 +408,20 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         const int cbase = q * 128;
         const float* off = sOff + s * Ng + cbase;
         const int nrem = N - g0 - cbase;  // valid grains from this chunk on
+        const int lb = sLRow[s * 128 + row] - g0 - cbase;  // the label's column in the block (when in 0..127)
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 32, RB);
-        float bm = chunk(RA, off, nrem, m, ssum);
+        float bm = chunk(RA, off, nrem, lb, m, ssum);
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 64, RA);
-        bm = fmaxf(bm, chunk(RB, off + 32, nrem - 32, m, ssum));
+        bm = fmaxf(bm, chunk(RB, off + 32, nrem - 32, lb - 32, m, ssum));
         tmem_wait_ld();
         tmem_ld32(tmem + lane_base + col + 96, RB);
-        bm = fmaxf(bm, chunk(RA, off + 64, nrem - 64, m, ssum));
+        bm = fmaxf(bm, chunk(RA, off + 64, nrem - 64, lb - 64, m, ssum));
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&bar_d_empty[b]);  // the logits are in registers: release the TMEM buffer
-        bm = fmaxf(bm, chunk(RB, off + 96, nrem - 96, m, ssum));
+        bm = fmaxf(bm, chunk(RB, off + 96, nrem - 96, lb - 96, m, ssum));
         // the largest logit of this pixel in the block
         sBm[s * Ng + q * 128 + row] = bm;
       }
@@ -423,10 +435,12 @@ k_tc_pass1(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           // group's part, and the label logit (one term of the full sum)
           lse = fmaxf(m + Arith<float>::lg(ssum), sLG[s * 128 + row]);
         } else {
-          // the accurate logarithm: S is 1 plus small terms at most pixels
-          lse = m + log2f(ssum);
-          lse_out[j] = lse;
-          racc += (double)(sLGv[s * 128 + row] - lse) * Arith<float>::to_nat;
+          // the label's term joins (a NaN label logit: a label outside 0..N-1)
+          const LabelLse r = label_lse(m, ssum, sLGv[s * 128 + row]);
+          lse = r.lse;
+          lse_out[j] = r.lse;
+          q_out[j] = r.q;
+          racc += r.logp;
         }
       }
       if (need_bits) {
@@ -533,9 +547,9 @@ __device__ __forceinline__ P2Share p2_share(const int* counts, int64_t n_tiles, 
 template <int DIM, int D, int KS, int NB, int NA>
 __global__ void __launch_bounds__(kP2ThreadsG, 1)
 k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Npad, const uint8_t* __restrict__ img,
-           const float* __restrict__ offg, const float* __restrict__ lse, const int* __restrict__ kept,
-           const int* __restrict__ n_kept_gb, int nb, const int* __restrict__ perm, double* __restrict__ part,
-           int* __restrict__ status) {
+           const float* __restrict__ offg, const float* __restrict__ lse, const float* __restrict__ qin,
+           const int* __restrict__ kept, const int* __restrict__ n_kept_gb, int nb, const int* __restrict__ perm,
+           double* __restrict__ part, int* __restrict__ status) {
   using L = Pass2Layout<DIM, D, KS>;
   constexpr int K = L::K, KW = L::KW, KT = L::KT, ET = L::ET, N2 = L::N2, CT = L::CT, LB = L::LB;
   constexpr uint32_t IDESC1 = idesc_bf16(128, kTcPixTile);
@@ -552,6 +566,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
   float* sLse = reinterpret_cast<float*>(sA2 + NA * L::kA2Bytes);  // [NB][128] log2 S of the pixels
   float* sOffP = sLse + NB * kTcPixTile;                           // [NB][128] centre logits of the block
   int* sLab = reinterpret_cast<int*>(sOffP + NB * 128);            // [NB][128] labels of the pixels
+  float* sNq = reinterpret_cast<float*>(sLab + NB * kTcPixTile);  // [NB][128] -(1 - p_G) of the pixels
   __shared__ __align__(8) uint64_t bar_theta, bar_b_full[NB], bar_b_empty[NB], bar_d1_full[LB], bar_d1_empty[LB],
       bar_a2_full[NA], bar_a2_empty[NA], bar_d2_full[2], bar_d2_free[2], bar_drain;
   __shared__ uint32_t tmem_slot;
@@ -659,12 +674,13 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     // pixel row; the next tile's coordinates, log2 S and label are fetched
     // while the current tile is written.
     const int p = tid - kTcConsumers;
-    float xn[DIM], cn[DIM], dxn[DIM], lsn = INFINITY;
+    float xn[DIM], cn[DIM], dxn[DIM], lsn = INFINITY, nqn = 0.f;
     int labn = -1;
     auto fetch = [&](int t) {
       const int64_t j = tile_pixel_dx<DIM>(g, tm, tile_of(t), p, xn, cn, dxn);
       lsn = j >= 0 ? lse[j] : INFINITY;
       labn = j >= 0 ? labels[j] : -1;
+      nqn = j >= 0 ? -qin[j] : 0.f;
     };
     if (n_kept > 0) fetch(0);
     for (int t = 0; t < n_kept; ++t) {
@@ -676,7 +692,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
         cc[a] = cn[a];
         dxc[a] = dxn[a];
       }
-      const float lsc = lsn;
+      const float lsc = lsn, nqc = nqn;
       const int labc = labn;
       const int64_t tc = tile_of(t);
       if (t + 1 < n_kept) fetch(t + 1);
@@ -705,6 +721,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       }
       sLse[s * kTcPixTile + p] = lsc;
       sLab[s * kTcPixTile + p] = labc;
+      sNq[s * kTcPixTile + p] = nqc;
       fence_proxy_async();
       mbar_arrive(&bar_b_full[s]);
     }
@@ -753,18 +770,24 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       n_done = u + 1;
       return true;
     };
-    // c = delta - p for 32 pixels (columns q0 .. q0+31 of this thread's
-    // half), written as fp16 pairs, one 16-byte core-matrix row per 8
-    // pixels: c_hi = fl16(c) and, for PD_BF16X3, c_lo = fl16((c - c_hi) 2^12)
-    auto emit = [&](const uint32_t(&r)[32], const float* ls, const int* lab, float off, uint8_t* a2, int q0) {
+    // c = p - delta for 32 pixels (columns q0 .. q0+31 of this thread's
+    // half; the sign returns at the reduction), written as fp16 pairs, one
+    // 16-byte core-matrix row per 8 pixels: c_hi = fl16(c) and, for
+    // PD_BF16X3, c_lo = fl16((c - c_hi) 2^12).  The label's c = -(1 - p_G)
+    // comes from pass 1 (no cancellation when p_G is close to 1).
+    auto emit = [&](const uint32_t(&r)[32], const float* ls, const int* lab, const float* nq, float off,
+                    uint8_t* a2, int q0) {
 #pragma unroll
       for (int q8 = 0; q8 < 32; q8 += 8) {
         const float4 va = *reinterpret_cast<const float4*>(ls + q8);
         const float4 vb = *reinterpret_cast<const float4*>(ls + q8 + 4);
         const int4 la = *reinterpret_cast<const int4*>(lab + q8);
         const int4 lb = *reinterpret_cast<const int4*>(lab + q8 + 4);
+        const float4 na = *reinterpret_cast<const float4*>(nq + q8);
+        const float4 nb = *reinterpret_cast<const float4*>(nq + q8 + 4);
         const float lv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
         const int lg[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+        const float nv[8] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
@@ -772,10 +795,9 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           // operation throughout (each rounds as its scalar form would)
           const float2 t = __fadd2_rn(make_float2(off, off), make_float2(-lv[u], -lv[u + 1]));
           const float2 x = __fadd2_rn(make_float2(__uint_as_float(r[q8 + u]), __uint_as_float(r[q8 + u + 1])), t);
-          const float2 pe = make_float2(Arith<float>::ex(x.x), Arith<float>::ex(x.y));
-          // c = delta - p
-          const float2 c = __ffma2_rn(pe, make_float2(-1.f, -1.f),
-                                      make_float2(lg[u] == gi ? 1.f : 0.f, lg[u + 1] == gi ? 1.f : 0.f));
+          // c = p - delta
+          const float2 c = make_float2(lg[u] == gi ? nv[u] : Arith<float>::ex(x.x),
+                                       lg[u + 1] == gi ? nv[u + 1] : Arith<float>::ex(x.y));
           const __half2 h = __floats2half2_rn(c.x, c.y);
           hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
           if (CT == 2) {
@@ -800,7 +822,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
     for (int t = 0; t < n_kept; ++t) {
       const int s = t % NB, b1 = t % LB, a = t % NA;
       const uint32_t col = (uint32_t)(b1 * kTcPixTile + half * 64);
-      // sLse, sLab and sOffP of the stage were written by the producers
+      // sLse, sLab, sNq and sOffP of the stage were written by the producers
       if (!mbar_wait_warp(&bar_b_full[s], (uint32_t)((t / NB) & 1), &abort_flag, status)) { ok = false; break; }
       if (!pre) {
         if (!mbar_wait_warp(&bar_d1_full[b1], (uint32_t)((t / LB) & 1), &abort_flag, status)) {
@@ -820,8 +842,9 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
       }
       const float* ls = sLse + s * kTcPixTile + half * 64;
       const int* lb = sLab + s * kTcPixTile + half * 64;
+      const float* nq = sNq + s * kTcPixTile + half * 64;
       uint8_t* a2 = sA2 + a * L::kA2Bytes;
-      emit(RA, ls, lb, off, a2, half * 64);
+      emit(RA, ls, lb, nq, off, a2, half * 64);
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(&bar_d1_empty[b1]);  // the tile's logits are in registers: release its TMEM columns
@@ -834,7 +857,7 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
           pre = true;
         }
       }
-      emit(RB, ls + 32, lb + 32, off, a2, half * 64 + 32);
+      emit(RB, ls + 32, lb + 32, nq + 32, off, a2, half * 64 + 32);
       fence_proxy_async();
       mbar_arrive(&bar_a2_full[a]);
       // the first warpgroup writes the previous chunk's partial one tile
@@ -869,11 +892,14 @@ k_tc_pass2(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, int Np
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float* __restrict__ lg,
-               float* __restrict__ lse_out, double* __restrict__ obj_part, const int* __restrict__ status) {
+               float* __restrict__ lse_out, float* __restrict__ q_out, double* __restrict__ obj_part,
+               const int* __restrict__ status) {
   __shared__ double sred[8];
   const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
   double r = 0.0;
   if (j < P) {
+    // every group's max starts at the label logit lG and its sum leaves the
+    // label's own term out: the label joins here
     float m = -INFINITY;
     for (int q = 0; q < n_grp; ++q) m = fmaxf(m, ms[(int64_t)q * P + j].x);
     float sum = 0.f;
@@ -881,9 +907,10 @@ k_tc_merge_lse(const float2* __restrict__ ms, int n_grp, int64_t P, const float*
       const float2 v = ms[(int64_t)q * P + j];
       if (v.y > 0.f) sum = fmaf(v.y, Arith<float>::ex(v.x - m), sum);
     }
-    const float l = m + log2f(sum);
-    lse_out[j] = l;
-    r = (double)(lg[j] - l) * Arith<float>::to_nat;
+    const LabelLse t = label_lse(m, sum, lg[j]);
+    lse_out[j] = t.lse;
+    q_out[j] = t.q;
+    r = t.logp;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
@@ -1052,6 +1079,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
   float2* ecg = sc.get<float2>((size_t)n_tiles * K);  // centre features per tile
   float* offg = sc.get<float>((size_t)n_tiles * Npad);  // relative centre logits [tile][image row]
   float* lse = sc.get<float>((size_t)P);
+  float* qv = sc.get<float>((size_t)P);  // 1 - p_G per pixel
   double* objp = sc.get<double>((size_t)std::max(grid1, n_grp > 1 ? gridm : 1));
   float2* ms = n_grp > 1 ? sc.get<float2>((size_t)n_grp * P) : nullptr;
   float* lgb = n_grp > 1 ? sc.get<float>((size_t)P) : nullptr;
@@ -1120,13 +1148,13 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     PD_TIMED(st, KS == 1 ? "tc_bf16_lse_pass1" : "tc_bf16x3_lse_pass1",
              k1<<<grid1, kP1Threads, smem1_req, st>>>(c.g, tm, c.labels, N, Npad, g0, ng, p1_stages, img, th32t,
                                                       th_resident, offg, perm ? rank : nullptr,
-                                                      lse, objp, ms ? ms + (size_t)q * P : nullptr, lgb, masks, need,
+                                                      lse, qv, objp, ms ? ms + (size_t)q * P : nullptr, lgb, masks, need,
                                                       n_words, status));
   }
   // a launch that fails (resources, configuration) is an error of this call
   if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   if (n_grp > 1)
-    PD_TIMED(st, "tc_merge_lse", k_tc_merge_lse<<<gridm, 256, 0, st>>>(ms, n_grp, P, lgb, lse, objp, status));
+    PD_TIMED(st, "tc_merge_lse", k_tc_merge_lse<<<gridm, 256, 0, st>>>(ms, n_grp, P, lgb, lse, qv, objp, status));
   if (c.grad) {
     if (skip)
       PD_TIMED(st, "tc_kept_lists",
@@ -1135,8 +1163,8 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_req) != cudaSuccess)
       return PD_ECUDA;
     PD_TIMED(st, KS == 1 ? "tc_bf16_grad_pass2" : "tc_bf16x3_grad_pass2",
-             k2<<<n_cta2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, c.labels, N, Npad, img, offg, lse, kept, nkept,
-                                                        gblocks, perm, part, status));
+             k2<<<n_cta2, kP2ThreadsG, smem2_req, st>>>(c.g, tm, c.labels, N, Npad, img, offg, lse, qv, kept,
+                                                        nkept, gblocks, perm, part, status));
     if (cudaPeekAtLastError() != cudaSuccess) return PD_ECUDA;
   }
   if (c.obj || c.grad) {
@@ -1145,7 +1173,7 @@ int eval_tc_dd(const EvalCall& c, cudaStream_t st) {
     PD_TIMED(st, "reduce_eval",
              k_tc_reduce_eval<<<blocks, dim3(32, 8), 0, st>>>(
                  part, n_cta2, kept ? nkept : nullptr, gblocks, perm ? rank : nullptr, n_tiles, K, NK,
-                 (const unsigned long long*)nullptr, 1.0 / (double)fx, -1.0 / (c.eps * (double)P), c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P,
+                 (const unsigned long long*)nullptr, 1.0 / (double)fx, 1.0 / (c.eps * (double)P), c.grad, objp, n_grp > 1 ? gridm : grid1, 1.0 / (double)P,
                  c.obj));
   }
   if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;

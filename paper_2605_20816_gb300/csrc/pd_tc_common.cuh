@@ -462,8 +462,8 @@ struct Pass2Layout {
   static constexpr uint32_t kB2Bytes = ET * kB2Term;           // rows: eta_h features, then eta_l
   static constexpr uint32_t kA2Term = 128u * kTcPixTile * 2;     // one term of c: 128 grains x 128 pixels, fp16
   static constexpr uint32_t kA2Bytes = CT * kA2Term;
-  // + log2 S, centre logits of the block, labels of the pixels
-  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + 128 * 4 + kTcPixTile * 4;
+  // + log2 S, centre logits of the block, labels of the pixels, -(1 - p_G)
+  static constexpr uint32_t kPerB = kBBytes + kB2Bytes + kTcPixTile * 4 + 128 * 4 + kTcPixTile * 4 + kTcPixTile * 4;
   static constexpr size_t bytes(int nb, int na) { return kABytes + (size_t)nb * kPerB + (size_t)na * kA2Bytes; }
   // TMEM: the logit ring (128 columns a tile) and two gradient buffers of
   // CT x N2 columns; three logit buffers where they fit

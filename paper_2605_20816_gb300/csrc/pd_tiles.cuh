@@ -74,9 +74,13 @@ TileMap make_tiles(const Geom& g) {
 }
 
 // Integer position of row r of tile t and of the tile's centre pixel
-// (structured grids).  The centre pixel may lie outside the grid for a
-// ragged tile; its coordinate is then outside [-1, 1], which the
-// polynomials accept.
+// (structured grids).  The centre pixel is the middle of the tile, moved
+// back to the grid's last pixel along an axis where the middle lies outside
+// the grid (a ragged tile only): the centre then stays in [-1, 1], where
+// |P_m| <= 1.  Outside, P_m grows like x^m, and on a grid narrower than a
+// tile (a single pixel: x = 0 against a middle at 16) the centre logits and
+// the remainders would be large terms that cancel in float.  Full tiles,
+// the only ones the tile bounds are taken for, keep their middle.
 template <int DIM>
 __device__ __forceinline__ void tile_ints(const TileMap& tm, int64_t t, int r, int* k, int* kc) {
   using TS = TileShape<DIM>;
@@ -85,12 +89,12 @@ __device__ __forceinline__ void tile_ints(const TileMap& tm, int64_t t, int r, i
   const unsigned rest = tt / (unsigned)tm.ntx;
   const int ty = (int)(rest % (unsigned)tm.nty);
   const int tz = (int)(rest / (unsigned)tm.nty);
-  kc[0] = (int)tx * TS::X + TS::X / 2;
-  kc[1] = ty * TS::Y + TS::Y / 2;
+  kc[0] = min((int)tx * TS::X + TS::X / 2, tm.n0 - 1);
+  kc[1] = min(ty * TS::Y + TS::Y / 2, tm.n1 - 1);
   k[0] = (int)tx * TS::X + (r % TS::X);
   k[1] = ty * TS::Y + ((r / TS::X) % TS::Y);
   if (DIM == 3) {
-    kc[2] = tz * TS::Z + TS::Z / 2;
+    kc[2] = min(tz * TS::Z + TS::Z / 2, tm.n2 - 1);
     k[2] = tz * TS::Z + (r / (TS::X * TS::Y));
   }
 }

@@ -10,6 +10,8 @@ PD_BF16 rounds every operand to bf16 (8 significant bits): its logit error
 is about |theta| / eps * 2^-9, so it is checked at a loose bound scaled to
 that, and its error is reported by the benchmark.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -207,3 +209,73 @@ def test_config2_full_size_bf16x3():
     assert rel(grad, grad_o) <= 1e-5
     phi16, grad16 = run(shape, lab, N, th, d, eps, pd.PD_BF16)
     print("config2 bf16 rel err: phi %.3e grad %.3e" % (abs(phi16 - phi_o) / abs(phi_o), rel(grad16, grad_o)))
+
+
+SMALL_GRIDS = [((1, 1), 2, 2), ((1, 5), 3, 3), ((7, 3), 5, 4), ((3, 2, 1), 4, 2), ((2, 1, 1), 2, 3),
+               ((1, 3, 2), 3, 3)]
+
+
+def sharpness(g, d, eps, th, lab):
+    # max over the pixels of 1 - p_max(x) and of 1 - p_G(x), in double: the
+    # oracle forms these differences in double, so its own relative error
+    # is about P 2^-53 over them
+    eta = O.features(g, d)
+    L = -(eta @ th.T) / eps
+    L -= L.max(1, keepdims=True)
+    p = np.exp(L)
+    p /= p.sum(1, keepdims=True)
+    return (1.0 - p.max(1)).max(), (1.0 - p[np.arange(g.P), lab]).max()
+
+
+@pytest.mark.parametrize("shape,N,d", SMALL_GRIDS)
+def test_reduced_precision_on_grids_smaller_than_a_tile(shape, N, d):
+    # one ragged tile holding a handful of pixels (a single pixel included):
+    # the tile-relative logits, the pair skipping and the passes' padding
+    # rows must still give the oracle's Phi and gradient.  With |theta|/eps
+    # large, p_G(x) lies close to 1 at most pixels: the gradient is then
+    # small and must not lose its relative accuracy to 1 - p_G.  Phi is a
+    # mean of log p over the pixels and can lie near 0: its bound adds
+    # 2^-20, a few float roundings of one log S; a tile centre placed
+    # outside [-1, 1] (P_m(16) ~ 4e2 at d = 2) misses it by a factor of four
+    # on the single pixel.
+    g = O.Grid(shape)
+    K = O.K(len(shape), d)
+    lab = synth.random_labels(51, g.P, N)
+    th = synth.random_theta(52, N, K, 0.3)
+    eps = 2e-2
+    assert g.P * 2.0 ** -53 / sharpness(g, d, eps, th, lab)[1] < 1e-8  # the oracle's own error
+    phi_o, grad_o = O.objective_grad(g, lab, N, d, eps, th)
+    for prec in (pd.PD_FP32, pd.PD_BF16X3):
+        phi, grad = run(shape, lab, N, th, d, eps, prec)
+        assert abs(phi - phi_o) <= 1e-5 * abs(phi_o) + 2.0 ** -20, (prec, phi, phi_o)
+        assert rel(grad, grad_o) <= 1e-5, (prec, rel(grad, grad_o))
+        # theta = 0: every grain equally likely, Phi = -log N
+        phi0, _ = run(shape, lab, N, np.zeros_like(th), d, eps, prec)
+        assert abs(phi0 + math.log(N)) <= 1e-6 * math.log(N), (prec, phi0)
+
+
+@pytest.mark.parametrize("shape,N,d", [c for c in SMALL_GRIDS if c[0] != (2, 1, 1)])
+def test_reduced_precision_hvp_on_grids_smaller_than_a_tile(shape, N, d):
+    # the Hessian-vector product at the same sharp parameters: where one
+    # grain's p is close to 1, u_i - ubar of that grain is a small
+    # difference that must keep its relative accuracy.  FP32 leaves each
+    # pixel's arg-max grain out of its sums, with labels or without.  (The
+    # tensor cores form the plain difference, which loses about
+    # log2(1 / (1 - p_max)) of the float's 24 bits: they are checked at
+    # 2^-18 / max_x(1 - p_max(x)), 1e-5 at the least.  On the 2 x 1 x 1 grid
+    # every 1 - p_max(x) is below 1e-14: the oracle's double differences
+    # carry no digits there.)
+    g = O.Grid(shape)
+    K = O.K(len(shape), d)
+    lab = synth.random_labels(51, g.P, N)
+    th = synth.random_theta(52, N, K, 0.3)
+    v = synth.random_theta(53, N, K, 1.0)
+    eps = 2e-2
+    sharp = sharpness(g, d, eps, th, lab)[0]
+    assert g.P * 2.0 ** -53 / sharp < 1e-8  # the oracle's own error
+    hv_o = O.hvp(g, lab, N, d, eps, th, v)
+    for labels in (dev(lab), None):
+        hv = pd.pd_hvp(pd.Grid(shape), labels, N, dev(th), dev(v), d, eps, prec=pd.PD_FP32).cpu().numpy()
+        assert rel(hv, hv_o) <= 1e-5, rel(hv, hv_o)
+    hv = pd.pd_hvp(pd.Grid(shape), dev(lab), N, dev(th), dev(v), d, eps, prec=pd.PD_BF16X3).cpu().numpy()
+    assert rel(hv, hv_o) <= max(1e-5, 2.0 ** -18 / sharp), (rel(hv, hv_o), sharp)
