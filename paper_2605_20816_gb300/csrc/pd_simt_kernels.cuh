@@ -780,6 +780,19 @@ k_pass2_tiles(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, con
                                  blockIdx.x, blockIdx.y);
 }
 
+// The same held to four blocks per SM, for the longer feature vectors
+// (K > 15), where the compiler left free picks a slower schedule.
+template <int DIM, int D, bool HVP>
+__global__ void __launch_bounds__(kGradThreads, 4)
+k_pass2_tiles_4(Geom g, TileMap tm, const int32_t* __restrict__ labels, int N, const float* __restrict__ thH,
+              const float* __restrict__ thL, const float* __restrict__ vS, const float2* __restrict__ ecg,
+              const float2* __restrict__ refg, const float* __restrict__ lse, const float* __restrict__ qin,
+              const float* __restrict__ ubar, const float* __restrict__ dmin, const int* __restrict__ mxin,
+              int64_t tpc, double* __restrict__ part) {
+  pass2_tiles_block<DIM, D, HVP>(g, tm, labels, N, thH, thL, vS, ecg, refg, lse, qin, ubar, dmin, mxin, tpc, part,
+                                 blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Arg-min assignment in double, smallest index on ties (eq. Li_def).
 // ---------------------------------------------------------------------------
@@ -1108,11 +1121,13 @@ int launch_simt_tiles(const EvalCall& c, const TileMap& tm, float* thH, float* t
              (k1<<<(unsigned)blocks1, kLseThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, nullptr, ec, ref, lse,
                                                              want_grad ? qv : nullptr, nullptr, nullptr, nullptr,
                                                              objp)));
-    if (want_grad)
+    if (want_grad) {
+      auto k2 = k_pass2_tiles<DIM, D, false>;
+      if constexpr (K > 15) k2 = k_pass2_tiles_4<DIM, D, false>;
       PD_TIMED(st, "simt_grad_pass2",
-               (k_pass2_tiles<DIM, D, false><<<grid2, kGradThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, nullptr,
-                                                                            ec, ref, lse, qv, nullptr, nullptr,
-                                                                            nullptr, tpc, part)));
+               (k2<<<grid2, kGradThreads, 0, st>>>(c.g, tm, c.labels, N, thH, thL, nullptr, ec, ref, lse, qv,
+                                                    nullptr, nullptr, nullptr, tpc, part)));
+    }
   }
   if (c.obj && !hvp)
     PD_TIMED(st, "reduce_obj", k_reduce_obj<<<1, 1024, 0, st>>>(objp, (int)blocks1, 1.0 / (double)P, c.obj));
